@@ -1,0 +1,184 @@
+/*
+ * qs.h -- C interface of libqs, a state-vector kernel library for sm_103a (GB300).
+ *
+ * The library applies single-qubit 2x2 gates with any number of control qubits to a
+ * vector of 2^n complex amplitudes held in GPU memory, scheduling only the 2^(n-1-c)
+ * amplitude pairs whose control bits are satisfied (arXiv 2411.18354, Section III-B:
+ * "reduced iteration index set", Eqs. 3-4). Each pair index is formed on the device by
+ * inserting the target bit (value 0) and the control bits (their required values) into a
+ * compact counter, the bit-level form of Eq. 4 followed by ithCleared.
+ *
+ * Conventions shared by every call:
+ *  - Amplitude k of an n-qubit state is stored at element k; qubit 0 is the least
+ *    significant bit of k (Section III). Elements are interleaved (re, im): complex64 =
+ *    2 x float32 (8 bytes), complex128 = 2 x float64 (16 bytes).
+ *  - A gate matrix U[8] is G = [a b; c d] of Section III, Eq. 2, row-major, each entry as
+ *    (re, im) doubles: {re a, im a, re b, im b, re c, im c, re d, im d}. For complex64
+ *    states the entries are rounded to float32 once per call.
+ *  - Controls: bit q of ctrl_mask marks qubit q as a control; the gate acts on pairs whose
+ *    index bits under ctrl_mask equal ctrl_vals (bit set = control on |1>, Section III-B;
+ *    bit clear = control on |0>, Fig. 1 right). ctrl_vals must not have bits outside
+ *    ctrl_mask, and ctrl_mask must not contain the target or qubits >= n.
+ *  - Every call returns a qs_status. On an error nothing has been launched and
+ *    qs_last_error() holds a message for the calling thread. Calls never throw.
+ *  - Work is enqueued asynchronously on the state's CUDA stream (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream) unless a call says it synchronises.
+ *  - Device pointers are plain CUDA device addresses on the device that is current when
+ *    the state is created; the caller keeps that device current for later calls.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qs_status {
+    QS_OK = 0,
+    QS_EINVAL = 1,        /* bad argument: nothing was launched                     */
+    QS_ENOMEM = 2,        /* device allocation failed                               */
+    QS_ECUDA = 3,         /* a CUDA runtime call failed (message has the CUDA text)  */
+    QS_ETIMEOUT = 4,      /* a bounded device-side wait gave up (status word set)    */
+    QS_EUNSUPPORTED = 5   /* valid request this build does not handle               */
+} qs_status;
+
+typedef enum qs_dtype { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Gate kinds of qs_gate.kind. */
+enum {
+    QS_GATE_U = 0,   /* general 2x2 matrix in U                                     */
+    QS_GATE_X = 1,   /* exchange the two amplitudes of each selected pair (X, CNOT,
+                        Toffoli; Section II-A: X swaps the amplitudes). Bit-exact.  */
+    QS_GATE_RY = 2,  /* RY(theta[param]) = exp(-i theta Y/2) = [[cos, -sin],[sin, cos]]
+                        of theta/2; U ignored                                       */
+    QS_GATE_RZ = 3   /* RZ(theta[param]) = exp(-i theta Z/2) =
+                        diag(e^{-i theta/2}, e^{+i theta/2}); U ignored              */
+};
+
+/* Flags of qs_apply_circuit / qs_adjoint_grad / qs_batch_create. */
+enum {
+    QS_FLAG_FUSE = 1,        /* group runs of low-target gates into one tile pass      */
+    QS_FLAG_GRAPH = 2,       /* launch the whole sequence as one CUDA graph            */
+    QS_FLAG_OUT_DEVICE = 4   /* energy / grad / expectation outputs are device pointers */
+};
+
+/* One gate (96 bytes, naturally aligned). Section III-A: target t, controls, matrix. */
+typedef struct qs_gate {
+    int32_t target;      /* target qubit t, 0 <= t < n                              */
+    int32_t kind;        /* QS_GATE_*                                              */
+    uint64_t ctrl_mask;  /* control qubits                                          */
+    uint64_t ctrl_vals;  /* required values of the control qubits                   */
+    int32_t param;       /* RY/RZ: index into theta; ignored for other kinds        */
+    int32_t reserved;    /* must be 0                                               */
+    double U[8];         /* QS_GATE_U: row-major [a b; c d], (re, im) interleaved   */
+} qs_gate;
+
+typedef struct qs_state qs_state;  /* opaque */
+
+/* Message of the last failing call on this thread ("" if none). Valid until the next
+ * failing call on the same thread. */
+const char *qs_last_error(void);
+
+/* Number of SMs / library build string, for diagnostics. Never fails. */
+const char *qs_build_info(void);
+
+/* ------------------------------------------------------------------------------------ */
+/* State vectors (Section III: 2^n complex numbers in device memory)                     */
+/* ------------------------------------------------------------------------------------ */
+
+/* Allocate a state of n qubits (1 <= n <= 40) owned by the library, initialised to
+ * |0...0> (amplitude 0 = 1) on `stream`. EINVAL for n out of range or a bad dtype;
+ * ENOMEM if cudaMalloc fails. *out receives the handle. */
+qs_status qs_state_alloc(int n, qs_dtype dtype, void *stream, qs_state **out);
+
+/* Wrap caller-owned device memory of `bytes` bytes as an n-qubit state (contents are
+ * left as they are). The library never frees it. EINVAL if bytes < 2^n * element size or
+ * dev_ptr is not 256-byte aligned. */
+qs_status qs_state_wrap(void *dev_ptr, size_t bytes, int n, qs_dtype dtype, void *stream,
+                        qs_state **out);
+
+/* Release the handle, its library-owned buffers and, for qs_state_alloc states, the
+ * amplitude buffer. Synchronises the state's stream first. NULL is accepted. */
+qs_status qs_state_free(qs_state *s);
+
+/* Query n, dtype and the amplitude buffer's device address (any pointer may be NULL). */
+qs_status qs_state_info(const qs_state *s, int *n, qs_dtype *dtype, void **dev_ptr);
+
+/* Change the stream later calls enqueue on. */
+qs_status qs_state_set_stream(qs_state *s, void *stream);
+
+/* Set the state to the basis state |k> (k < 2^n). Asynchronous. */
+qs_status qs_state_set_basis(qs_state *s, uint64_t k);
+
+/* Copy all 2^n amplitudes to / from host memory (`bytes` must equal 2^n * element
+ * size). Synchronous: returns after the copy has finished. */
+qs_status qs_state_copy_to_host(const qs_state *s, void *dst, size_t bytes);
+qs_status qs_state_copy_from_host(qs_state *s, const void *src, size_t bytes);
+
+/* ------------------------------------------------------------------------------------ */
+/* Gates (Section III, Eq. 2 on the reduced iteration set of Section III-B)             */
+/* ------------------------------------------------------------------------------------ */
+
+/* Apply G = U to `target` on the pairs selected by (ctrl_mask, ctrl_vals); 2^(n-1-c)
+ * pairs are scheduled, c = popcount(ctrl_mask). U is not checked for unitarity. EINVAL if
+ * target is out of range, the mask holds the target or bits >= n, ctrl_vals has bits
+ * outside the mask, or U holds a NaN/Inf. Exact structure in U is used: [[0,1],[1,0]]
+ * runs the exchange path (bit-exact), b = c = 0 runs a diagonal path, and a diagonal with
+ * a == 1 (or d == 1) touches only the amplitudes it changes. */
+qs_status qs_apply_gate(qs_state *s, int target, uint64_t ctrl_mask, uint64_t ctrl_vals,
+                        const double U[8]);
+
+/* Exchange the amplitudes of each selected pair (X / CNOT / Toffoli): bit-exact. */
+qs_status qs_apply_x(qs_state *s, int target, uint64_t ctrl_mask, uint64_t ctrl_vals);
+
+/* Comparator for the paper's baseline scheduling (Section III-A pseudocode): launches
+ * all 2^(n-1) pair iterations and skips those whose controls fail. Same result as
+ * qs_apply_gate; exists to measure the difference. */
+qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
+                               uint64_t ctrl_vals, const double U[8]);
+
+/* Apply `count` gates in order (gates run serially, Section III). RY/RZ gates read
+ * theta[param] (theta may be NULL when no gate is parameterised; n_theta is its length).
+ * All gates are validated before anything is launched. flags: QS_FLAG_FUSE runs maximal
+ * runs of consecutive gates whose target and controls are below the tile size in one
+ * HBM round trip; QS_FLAG_GRAPH records the launches into a CUDA graph and launches it. */
+qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
+                           const double *theta, size_t n_theta, int flags);
+
+/* ------------------------------------------------------------------------------------ */
+/* Reductions (double-precision accumulation on the device)                             */
+/* ------------------------------------------------------------------------------------ */
+
+/* out[i] = <Z_i> = sum_k |psi_k|^2 (1 - 2 bit_i(k)) for i = 0..n-1, and, if out_norm2 is
+ * not NULL, *out_norm2 = sum_k |psi_k|^2 -- all in one pass over the state. Complex64
+ * states sum |psi_k|^2 in float32 over runs of at most 32 amplitudes per thread and 1024
+ * per warp, and in float64 above that; complex128 states sum in float64 throughout.
+ * With QS_FLAG_OUT_DEVICE in flags, out / out_norm2 are device pointers and the call is
+ * asynchronous; otherwise they are host pointers and the call synchronises the stream. */
+qs_status qs_expect_z(const qs_state *s, double *out, double *out_norm2, int flags);
+
+/* ------------------------------------------------------------------------------------ */
+/* Adjoint gradient (reverse sweep that un-applies gates; no checkpoints)               */
+/* ------------------------------------------------------------------------------------ */
+
+/* For E(theta) = <psi|O|psi>, O = sum_i Z_i, psi = C(theta)|psi_in>: on entry the state
+ * holds psi_in; the call applies the circuit, writes E to *energy and dE/dtheta[p] to
+ * grad[p] for p < n_theta (parameters that drive no gate get 0), running the reverse
+ * sweep psi <- U_g^dagger psi, lambda <- U_g^dagger lambda with
+ * grad += 2 Re <lambda| dU_g/dtheta psi> for every RY/RZ gate. On return the state holds
+ * psi_in recomputed by the sweep (up to rounding). A second vector (lambda) is allocated
+ * on first use and kept with the state. Inner products accumulate in float64.
+ * QS_FLAG_FUSE groups low-target gates into tile passes; QS_FLAG_OUT_DEVICE makes energy
+ * and grad device pointers (asynchronous); otherwise host pointers (synchronous). */
+qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count,
+                          const double *theta, size_t n_theta, double *energy,
+                          double *grad, int flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H */

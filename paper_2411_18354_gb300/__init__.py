@@ -1,0 +1,120 @@
+"""GB300 (sm_103a) state-vector kernels for controlled single-qubit gates.
+
+A gate on target t with c controls is applied by scheduling only the 2^(n-1-c) amplitude
+pairs whose controls hold, each pair index built by inserting the target and control bits
+into a compact counter (arXiv 2411.18354, Section III-B, Eqs. 3-4). Everything runs in the
+CUDA library ``libqs.so`` behind the C interface of ``include/qs.h``; this package is its
+ctypes binding (``_lib``: same names as the C calls), a small ``State`` wrapper, and a
+``torch.autograd.Function`` over the adjoint gradient. PyTorch is used only for streams and
+device memory.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401  (re-exported C-ABI names)
+    QS_C64, QS_C128, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_GATE_U,
+    QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate,
+    qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_last_error, qs_state_alloc,
+    qs_state_copy_from_host, qs_state_copy_to_host, qs_state_free, qs_state_info, qs_state_set_basis,
+    qs_state_set_stream, qs_state_wrap,
+)
+from .gates import GATE_DTYPE, as_gate_array  # noqa: F401
+
+_DT = {"c64": QS_C64, "complex64": QS_C64, "c128": QS_C128, "complex128": QS_C128}
+_NP = {QS_C64: np.complex64, QS_C128: np.complex128}
+
+
+def _current_stream() -> int:
+    import torch
+
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class State:
+    """An n-qubit state vector on the current CUDA device (owned by libqs unless wrapped)."""
+
+    def __init__(self, n: int, dtype="c64", stream: int | None = None, _handle: int | None = None):
+        self.dtype = _DT[dtype] if isinstance(dtype, str) else int(dtype)
+        self.n = int(n)
+        if _handle is not None:
+            self.h = _handle
+        else:
+            self.h = qs_state_alloc(self.n, self.dtype, _current_stream() if stream is None else stream)
+
+    @classmethod
+    def wrap(cls, tensor, n: int, stream: int | None = None) -> "State":
+        """Use a contiguous torch complex64/complex128 CUDA tensor of 2^n elements as the state."""
+        import torch
+
+        dt = QS_C64 if tensor.dtype == torch.complex64 else QS_C128 if tensor.dtype == torch.complex128 else None
+        if dt is None or not tensor.is_cuda or not tensor.is_contiguous():
+            raise ValueError("need a contiguous complex64/complex128 CUDA tensor")
+        h = qs_state_wrap(tensor.data_ptr(), tensor.numel() * tensor.element_size(), n, dt,
+                          _current_stream() if stream is None else stream)
+        st = cls(n, dt, _handle=h)
+        st._tensor = tensor  # keep the memory alive
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            qs_state_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def device_ptr(self) -> int:
+        return qs_state_info(self.h)[2]
+
+    def set_basis(self, k: int = 0):
+        qs_state_set_basis(self.h, k)
+
+    def set_stream(self, stream: int):
+        qs_state_set_stream(self.h, stream)
+
+    def apply_gate(self, target: int, U, ctrl_mask: int = 0, ctrl_vals: int | None = None):
+        qs_apply_gate(self.h, target, ctrl_mask, ctrl_mask if ctrl_vals is None else ctrl_vals, U)
+
+    def apply_x(self, target: int, ctrl_mask: int = 0, ctrl_vals: int | None = None):
+        qs_apply_x(self.h, target, ctrl_mask, ctrl_mask if ctrl_vals is None else ctrl_vals)
+
+    def apply_gate_masked(self, target: int, U, ctrl_mask: int = 0, ctrl_vals: int | None = None):
+        qs_apply_gate_masked(self.h, target, ctrl_mask, ctrl_mask if ctrl_vals is None else ctrl_vals, U)
+
+    def apply_circuit(self, gates, theta=None, flags: int = 0):
+        qs_apply_circuit(self.h, gates, theta, flags)
+
+    def expect_z(self):
+        return qs_expect_z(self.h)
+
+    def adjoint_grad(self, gates, theta, flags: int = 0):
+        return qs_adjoint_grad(self.h, gates, theta, flags)
+
+    def to_numpy(self) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=_NP[self.dtype])
+        qs_state_copy_to_host(self.h, out)
+        return out
+
+    def from_numpy(self, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=_NP[self.dtype])
+        if a.size != (1 << self.n):
+            raise ValueError("wrong number of amplitudes")
+        qs_state_copy_from_host(self.h, a)
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+
+    return _b(force=force)

@@ -1,0 +1,211 @@
+"""ctypes binding of libqs (``include/qs.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls, converts Python/numpy
+arguments to the C types, and raises ``QsError`` when the call returns a status other than
+QS_OK. No step of the computation runs in Python: if the shared library is missing, loading
+fails with an error instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
+QS_C64, QS_C128 = 0, 1
+QS_GATE_U, QS_GATE_X, QS_GATE_RY, QS_GATE_RZ = 0, 1, 2, 3
+QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE = 1, 2, 4
+
+STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EUNSUPPORTED"}
+
+
+class QsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_c_state_p = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+# (name, restype, argtypes) for every function declared in include/qs.h
+_SIGNATURES = [
+    ("qs_last_error", ctypes.c_char_p, []),
+    ("qs_build_info", ctypes.c_char_p, []),
+    ("qs_state_alloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_c_state_p)]),
+    ("qs_state_wrap", ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_c_state_p)]),
+    ("qs_state_free", ctypes.c_int, [_c_state_p]),
+    ("qs_state_info", ctypes.c_int, [_c_state_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(_vp)]),
+    ("qs_state_set_stream", ctypes.c_int, [_c_state_p, _vp]),
+    ("qs_state_set_basis", ctypes.c_int, [_c_state_p, _u64]),
+    ("qs_state_copy_to_host", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
+    ("qs_state_copy_from_host", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
+    ("qs_apply_gate", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
+    ("qs_apply_x", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64]),
+    ("qs_apply_gate_masked", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
+    ("qs_apply_circuit", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, ctypes.c_int]),
+    ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
+    ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libqs.so (built in-tree by ``paper_2411_18354_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libqs.so not found at {LIB_PATH}: build it with paper_2411_18354_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [name for name, _, _ in _SIGNATURES]
+
+
+def _check(status: int):
+    if status != QS_OK:
+        raise QsError(status, lib().qs_last_error().decode(errors="replace"))
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return ctypes.cast(ctypes.c_void_p(int(a)), _dp) if isinstance(a, int) else a.ctypes.data_as(_dp)
+
+
+def _u8(U) -> np.ndarray:
+    U = np.asarray(U)
+    if np.iscomplexobj(U) or U.shape == (2, 2):
+        U = np.asarray(U, dtype=np.complex128).reshape(4)
+        out = np.empty(8)
+        out[0::2] = U.real
+        out[1::2] = U.imag
+        return out
+    return np.ascontiguousarray(U, dtype=np.float64).reshape(8)
+
+
+def qs_last_error() -> str:
+    return lib().qs_last_error().decode(errors="replace")
+
+
+def qs_build_info() -> str:
+    return lib().qs_build_info().decode(errors="replace")
+
+
+def qs_state_alloc(n: int, dtype: int, stream: int = 0) -> int:
+    h = _c_state_p()
+    _check(lib().qs_state_alloc(n, dtype, _vp(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def qs_state_wrap(dev_ptr: int, nbytes: int, n: int, dtype: int, stream: int = 0) -> int:
+    h = _c_state_p()
+    _check(lib().qs_state_wrap(_vp(dev_ptr), nbytes, n, dtype, _vp(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def qs_state_free(h: int) -> None:
+    _check(lib().qs_state_free(_c_state_p(h)))
+
+
+def qs_state_info(h: int):
+    n = ctypes.c_int()
+    dt = ctypes.c_int()
+    p = _vp()
+    _check(lib().qs_state_info(_c_state_p(h), ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
+    return n.value, dt.value, p.value
+
+
+def qs_state_set_stream(h: int, stream: int) -> None:
+    _check(lib().qs_state_set_stream(_c_state_p(h), _vp(stream or None)))
+
+
+def qs_state_set_basis(h: int, k: int) -> None:
+    _check(lib().qs_state_set_basis(_c_state_p(h), k))
+
+
+def qs_state_copy_to_host(h: int, dst: np.ndarray) -> None:
+    if not dst.flags.c_contiguous:
+        raise ValueError("dst must be contiguous")
+    _check(lib().qs_state_copy_to_host(_c_state_p(h), _vp(dst.ctypes.data), dst.nbytes))
+
+
+def qs_state_copy_from_host(h: int, src: np.ndarray) -> None:
+    src = np.ascontiguousarray(src)
+    _check(lib().qs_state_copy_from_host(_c_state_p(h), _vp(src.ctypes.data), src.nbytes))
+
+
+def qs_apply_gate(h: int, target: int, ctrl_mask: int, ctrl_vals: int, U) -> None:
+    u = _u8(U)
+    _check(lib().qs_apply_gate(_c_state_p(h), target, ctrl_mask, ctrl_vals, u.ctypes.data_as(_dp)))
+
+
+def qs_apply_x(h: int, target: int, ctrl_mask: int = 0, ctrl_vals: int = 0) -> None:
+    _check(lib().qs_apply_x(_c_state_p(h), target, ctrl_mask, ctrl_vals))
+
+
+def qs_apply_gate_masked(h: int, target: int, ctrl_mask: int, ctrl_vals: int, U) -> None:
+    u = _u8(U)
+    _check(lib().qs_apply_gate_masked(_c_state_p(h), target, ctrl_mask, ctrl_vals, u.ctypes.data_as(_dp)))
+
+
+def _gates_arg(gates):
+    from .gates import as_gate_array
+
+    g = as_gate_array(gates)
+    return g, _vp(g.ctypes.data) if g.size else None
+
+
+def _theta_arg(theta):
+    if theta is None:
+        return None, None, 0
+    t = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    return t, t.ctypes.data_as(_dp), t.size
+
+
+def qs_apply_circuit(h: int, gates, theta=None, flags: int = 0) -> None:
+    g, gp = _gates_arg(gates)
+    t, tp, nt = _theta_arg(theta)
+    _check(lib().qs_apply_circuit(_c_state_p(h), gp, g.size, tp, nt, flags))
+
+
+def qs_expect_z(h: int, flags: int = 0, out=None, out_norm2=None):
+    """Host outputs (default): returns (z[n] numpy array, norm2). With QS_FLAG_OUT_DEVICE,
+    ``out`` / ``out_norm2`` are device addresses (ints) and nothing is returned."""
+    if flags & QS_FLAG_OUT_DEVICE:
+        _check(lib().qs_expect_z(_c_state_p(h), _dptr(out), _dptr(out_norm2), flags))
+        return None
+    n, _, _ = qs_state_info(h)
+    z = np.empty(n)
+    nrm = np.empty(1)
+    _check(lib().qs_expect_z(_c_state_p(h), z.ctypes.data_as(_dp), nrm.ctypes.data_as(_dp), flags))
+    return z, float(nrm[0])
+
+
+def qs_adjoint_grad(h: int, gates, theta, flags: int = 0, energy_out=None, grad_out=None):
+    """Host outputs (default): returns (energy, grad numpy array). With QS_FLAG_OUT_DEVICE,
+    ``energy_out`` / ``grad_out`` are device addresses (ints) and nothing is returned."""
+    g, gp = _gates_arg(gates)
+    t, tp, nt = _theta_arg(theta)
+    if flags & QS_FLAG_OUT_DEVICE:
+        _check(lib().qs_adjoint_grad(_c_state_p(h), gp, g.size, tp, nt, _dptr(energy_out), _dptr(grad_out), flags))
+        return None
+    e = np.empty(1)
+    gr = np.empty(max(nt, 1))
+    _check(lib().qs_adjoint_grad(_c_state_p(h), gp, g.size, tp, nt, e.ctypes.data_as(_dp),
+                                 gr.ctypes.data_as(_dp), flags))
+    return float(e[0]), gr[:nt]

@@ -1,0 +1,231 @@
+// k_reduce.cu -- one-pass <Z_i> for every qubit and the squared norm.
+//
+// <Z_i> = sum_k |psi_k|^2 (1 - 2 bit_i(k)) = T - 2 S_i with T = sum_k |psi_k|^2 and
+// S_i = sum over k with bit i set. One read of the state gives T and all S_i:
+//  - a block works on tiles of 2^TB consecutive amplitudes; inside a tile the amplitude
+//    offset is (j, thread, v) with v the element inside a 16-byte vector (complex64 only),
+//    the thread index (lane bits, then warp bits) and the unrolled load index j (4 bits);
+//  - each thread sums |psi|^2 over its 32 (complex64) or 16 (complex128) values, also per
+//    v bit and per j bit (those bits are compile-time constants of the unrolled loop);
+//  - warp shuffles reduce the per-thread sums and form the lane-bit sums;
+//  - warp totals give the warp-bit sums; bits at or above TB are constant per tile and
+//    take the tile total when set;
+//  - thread b of the block owns output b and accumulates it in float64 over the block's
+//    tiles; a final one-block pass adds the per-block results in a fixed order.
+// Complex64: per-thread and per-warp sums are float32 (at most 32 and 1024 terms),
+// everything above is float64. Complex128: float64 everywhere. The result does not depend
+// on scheduling (fixed tile-to-block assignment and fixed summation order).
+#include <algorithm>
+
+#include "qs_internal.cuh"
+
+namespace qs {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1024;
+constexpr int kJ = 16;  // unrolled loads per thread per tile
+
+template <typename Real> struct RedT;
+template <> struct RedT<float> {
+    using T2 = float2;
+    static constexpr int VB = 1;  // log2(amplitudes per 16-byte load)
+};
+template <> struct RedT<double> {
+    using T2 = double2;
+    static constexpr int VB = 0;
+};
+
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(kRedThreads)
+k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t ntiles, double *__restrict__ partials) {
+    using A = Real;  // per-thread / per-warp accumulator type
+    constexpr int VB = RedT<Real>::VB;
+    constexpr int TB = VB + 8 + 4;
+    // per-warp values: [0] total, [1..VB] v-bit, [1+VB .. 4+VB] j bits, [5+VB .. 9+VB] lane bits
+    constexpr int NV = 1 + VB + 4 + 5;
+    __shared__ A wpart[kRedThreads / 32][NV];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    double acc = 0.0;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        A tot = 0, sv = 0, sj[4] = {0, 0, 0, 0};
+        if (VB == 1) {
+            const float4 *base = reinterpret_cast<const float4 *>(psi) + (tile << (TB - 1));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float4 q[kJ / 2];
+#pragma unroll
+                for (int jj = 0; jj < kJ / 2; ++jj) q[jj] = base[(h * (kJ / 2) + jj) * kRedThreads + tid];
+#pragma unroll
+                for (int jj = 0; jj < kJ / 2; ++jj) {
+                    const int j = h * (kJ / 2) + jj;
+                    const A p0 = (A)fmaf(q[jj].x, q[jj].x, q[jj].y * q[jj].y);
+                    const A p1 = (A)fmaf(q[jj].z, q[jj].z, q[jj].w * q[jj].w);
+                    const A s = p0 + p1;
+                    tot += s;
+                    sv += p1;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if ((j >> b) & 1) sj[b] += s;
+                }
+            }
+        } else {
+            const double2 *base = reinterpret_cast<const double2 *>(psi) + (tile << TB);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                double2 q[kJ / 2];
+#pragma unroll
+                for (int jj = 0; jj < kJ / 2; ++jj) q[jj] = base[(h * (kJ / 2) + jj) * kRedThreads + tid];
+#pragma unroll
+                for (int jj = 0; jj < kJ / 2; ++jj) {
+                    const int j = h * (kJ / 2) + jj;
+                    const A s = (A)fma(q[jj].x, q[jj].x, q[jj].y * q[jj].y);
+                    tot += s;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if ((j >> b) & 1) sj[b] += s;
+                }
+            }
+        }
+        // lane-bit sums before the total is reduced
+        A sl[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) sl[b] = warp_sum<A>(((lane >> b) & 1) ? tot : (A)0);
+        tot = warp_sum<A>(tot);
+        if (VB) sv = warp_sum<A>(sv);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) sj[b] = warp_sum<A>(sj[b]);
+        if (lane == 0) {
+            wpart[warp][0] = tot;
+            if (VB) wpart[warp][1] = sv;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) wpart[warp][1 + VB + b] = sj[b];
+#pragma unroll
+            for (int b = 0; b < 5; ++b) wpart[warp][5 + VB + b] = sl[b];
+        }
+        __syncthreads();
+        if (tid <= n) {
+            // output tid: tid == n -> total; else S_tid (sum over amplitudes with bit tid set)
+            double v = 0.0;
+            const int b = tid;
+            if (b == n) {
+                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][0];
+            } else if (b < VB) {
+                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][1];
+            } else if (b < VB + 5) {
+                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][5 + VB + (b - VB)];
+            } else if (b < VB + 8) {
+                for (int w = 0; w < kRedThreads / 32; ++w)
+                    if ((w >> (b - VB - 5)) & 1) v += (double)wpart[w][0];
+            } else if (b < TB) {
+                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][1 + VB + (b - VB - 8)];
+            } else if ((tile >> (b - TB)) & 1ull) {
+                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][0];
+            }
+            acc += v;
+        }
+        __syncthreads();
+    }
+    if (tid <= n) partials[(size_t)blockIdx.x * (n + 1) + tid] = acc;
+}
+
+// Fixed-order sum of the per-block partials; one block.
+__global__ void k_expz_final(const double *__restrict__ partials, int nblocks, int n,
+                             double *__restrict__ out_z, double *__restrict__ out_norm2) {
+    __shared__ double tot;
+    const int b = threadIdx.x;
+    double s = 0.0;
+    if (b <= n)
+        for (int g = 0; g < nblocks; ++g) s += partials[(size_t)g * (n + 1) + b];
+    if (b == n) tot = s;
+    __syncthreads();
+    if (b < n && out_z) out_z[b] = tot - 2.0 * s;
+    if (b == n && out_norm2) *out_norm2 = s;
+}
+
+// Small states (fewer amplitudes than one tile): one block, float64 per amplitude.
+template <typename Real>
+__global__ void __launch_bounds__(kRedThreads)
+k_expz_small(const typename RedT<Real>::T2 *__restrict__ psi, int n, double *__restrict__ out_z,
+             double *__restrict__ out_norm2) {
+    constexpr int kMaxSmallBits = 13;
+    __shared__ double red[kRedThreads / 32][kMaxSmallBits + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t N = 1ull << n;
+    double tot = 0.0, s[kMaxSmallBits];
+#pragma unroll
+    for (int b = 0; b < kMaxSmallBits; ++b) s[b] = 0.0;
+    for (uint64_t k = tid; k < N; k += kRedThreads) {
+        const double re = (double)psi[k].x, im = (double)psi[k].y;
+        const double p = re * re + im * im;
+        tot += p;
+#pragma unroll
+        for (int b = 0; b < kMaxSmallBits; ++b)
+            if (b < n && ((k >> b) & 1ull)) s[b] += p;
+    }
+    tot = warp_sum<double>(tot);
+#pragma unroll
+    for (int b = 0; b < kMaxSmallBits; ++b) s[b] = warp_sum<double>(s[b]);
+    if (lane == 0) {
+        red[warp][kMaxSmallBits] = tot;
+#pragma unroll
+        for (int b = 0; b < kMaxSmallBits; ++b) red[warp][b] = s[b];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double T = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) T += red[w][kMaxSmallBits];
+        for (int b = 0; b < n; ++b) {
+            double S = 0.0;
+            for (int w = 0; w < kRedThreads / 32; ++w) S += red[w][b];
+            if (out_z) out_z[b] = T - 2.0 * S;
+        }
+        if (out_norm2) *out_norm2 = T;
+    }
+}
+
+template <typename Real>
+cudaError_t expect_z_impl(const void *psi, int n, double *scratch, double *out_z, double *out_norm2,
+                          cudaStream_t st) {
+    using T2 = typename RedT<Real>::T2;
+    constexpr int TB = RedT<Real>::VB + 8 + 4;
+    const T2 *p = reinterpret_cast<const T2 *>(psi);
+    if (n < TB) {
+        k_expz_small<Real><<<1, kRedThreads, 0, st>>>(p, n, out_z, out_norm2);
+        return cudaGetLastError();
+    }
+    static const int occ = [] {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_expz_tiles<Real>, kRedThreads, 0) != cudaSuccess || o < 1) o = 1;
+        return o;
+    }();
+    const uint64_t ntiles = 1ull << (n - TB);
+    const uint64_t cap = std::min<uint64_t>((uint64_t)kRedMaxBlocks, (uint64_t)device_sm_count() * occ);
+    const int grid = (int)std::min<uint64_t>(ntiles, cap);
+    k_expz_tiles<Real><<<grid, kRedThreads, 0, st>>>(p, n, ntiles, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_expz_final<<<1, 64, 0, st>>>(scratch, grid, n, out_z, out_norm2);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t reduce_scratch_doubles(int n) { return (size_t)kRedMaxBlocks * (size_t)(n + 1); }
+
+cudaError_t launch_expect_z(int dtype, const void *psi, int n, double *scratch, double *out_z,
+                            double *out_norm2, cudaStream_t st) {
+    return dtype == QS_C64 ? expect_z_impl<float>(psi, n, scratch, out_z, out_norm2, st)
+                           : expect_z_impl<double>(psi, n, scratch, out_z, out_norm2, st);
+}
+
+}  // namespace qs

@@ -1,0 +1,298 @@
+// qs_circuit.cu -- qs_apply_circuit and qs_adjoint_grad: whole gate lists, validated
+// up front, launched per gate (or per fused tile pass) on the state's stream, optionally
+// recorded once into a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "qs_internal.cuh"
+#include "qs_state.cuh"
+
+namespace qs {
+
+size_t adj_partials_per_slot();
+cudaError_t launch_adj_step(int dtype, void *psi, void *lam, const GatePlan &p, const double *dU, double *part,
+                            cudaStream_t st);
+cudaError_t launch_obs_sumz(int dtype, const void *psi, void *lam, int n, cudaStream_t st);
+cudaError_t launch_sum_vec(const double *z, int n, double *out, cudaStream_t st);
+cudaError_t launch_grad_final(const double *part, int nslots, double *slot_sum, const int *slot_param,
+                              double *grad, int nparams, cudaStream_t st);
+
+void release_state_buffers(qs_state *s) {
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
+    s->capture_stream = nullptr;
+    if (s->red_scratch) cudaFree(s->red_scratch);
+    s->red_scratch = nullptr;
+    s->red_scratch_n = 0;
+    if (s->lam) cudaFree(s->lam);
+    s->lam = nullptr;
+    if (s->grad_scratch) cudaFree(s->grad_scratch);
+    s->grad_scratch = nullptr;
+    s->grad_scratch_n = 0;
+}
+
+// RY(theta) = [[c, -s], [s, c]], RZ(theta) = diag(c - i s, c + i s), c = cos(theta/2),
+// s = sin(theta/2): exp(-i theta P / 2) for P = Y, Z.
+static void rot_matrix(int kind, double theta, double U[8]) {
+    const double c = std::cos(0.5 * theta), s = std::sin(0.5 * theta);
+    std::memset(U, 0, 8 * sizeof(double));
+    if (kind == QS_GATE_RY) {
+        U[0] = c; U[2] = -s; U[4] = s; U[6] = c;
+    } else {
+        U[0] = c; U[1] = -s; U[6] = c; U[7] = s;
+    }
+}
+
+// d/dtheta of the matrices above: dRY = 1/2 [[-s, -c], [c, -s]],
+// dRZ = diag(-i/2 (c - i s), i/2 (c + i s)) = diag((-s - i c)/2, (-s + i c)/2).
+static void rot_derivative(int kind, double theta, double D[8]) {
+    const double c = std::cos(0.5 * theta), s = std::sin(0.5 * theta);
+    std::memset(D, 0, 8 * sizeof(double));
+    if (kind == QS_GATE_RY) {
+        D[0] = -0.5 * s; D[2] = -0.5 * c; D[4] = 0.5 * c; D[6] = -0.5 * s;
+    } else {
+        D[0] = -0.5 * s; D[1] = -0.5 * c; D[6] = -0.5 * s; D[7] = 0.5 * c;
+    }
+}
+
+static void dagger(const double U[8], double D[8]) {
+    // [a b; c d]^dagger = [a* c*; b* d*]
+    D[0] = U[0]; D[1] = -U[1];
+    D[2] = U[4]; D[3] = -U[5];
+    D[4] = U[2]; D[5] = -U[3];
+    D[6] = U[6]; D[7] = -U[7];
+}
+
+// Resolve one gate record into a forward plan (validating it). `theta` may be NULL if
+// no gate is parameterised.
+static bool plan_record(const qs_state *s, const qs_gate &g, const double *theta, size_t n_theta, size_t index,
+                        GatePlan *p, char *err, size_t errlen) {
+    char e2[200];
+    if (g.reserved != 0) {
+        std::snprintf(err, errlen, "gate %zu: reserved field must be 0", index);
+        return false;
+    }
+    double U[8];
+    int kind = g.kind;
+    if (kind == QS_GATE_RY || kind == QS_GATE_RZ) {
+        if (!theta || g.param < 0 || (size_t)g.param >= n_theta) {
+            std::snprintf(err, errlen, "gate %zu: parameter index %d outside theta[%zu]", index, g.param, n_theta);
+            return false;
+        }
+        if (!std::isfinite(theta[g.param])) {
+            std::snprintf(err, errlen, "gate %zu: theta[%d] is not finite", index, g.param);
+            return false;
+        }
+        rot_matrix(kind, theta[g.param], U);
+        kind = QS_GATE_U;
+    } else if (kind == QS_GATE_U) {
+        std::memcpy(U, g.U, sizeof(U));
+    } else if (kind != QS_GATE_X) {
+        std::snprintf(err, errlen, "gate %zu: unknown kind %d", index, g.kind);
+        return false;
+    }
+    if (!plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, kind == QS_GATE_X ? nullptr : U, kind, -1, p,
+                   e2, sizeof(e2))) {
+        std::snprintf(err, errlen, "gate %zu: %s", index, e2);
+        return false;
+    }
+    return true;
+}
+
+static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, cudaStream_t st) {
+    for (size_t i = 0; i < plans.size(); ++i) {
+        cudaError_t e = launch_gate(s->dtype, s->psi, plans[i], st);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit launch");
+    }
+    return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
+                           int flags) {
+    if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
+    if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_apply_circuit: gates is NULL");
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH)) return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
+    if (flags & QS_FLAG_FUSE) return set_error(QS_EUNSUPPORTED, "qs_apply_circuit: QS_FLAG_FUSE not built yet");
+    std::vector<GatePlan> plans(count);
+    char err[256];
+    for (size_t i = 0; i < count; ++i)
+        if (!plan_record(s, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
+            return set_error(QS_EINVAL, err);
+    if (!(flags & QS_FLAG_GRAPH)) return launch_plans(s, plans, s->stream);
+
+    // CUDA graph: record once per distinct (gates, theta, flags), then replay.
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(key, gates, count * sizeof(qs_gate));
+    if (theta) key = fnv1a(key, theta, n_theta * sizeof(double));
+    key = fnv1a(key, &flags, sizeof(flags));
+    key = fnv1a(key, &s->psi, sizeof(s->psi));
+    cudaGraphExec_t exec = nullptr;
+    for (auto &g : s->graphs)
+        if (g.key == key) exec = g.exec;
+    if (!exec) {
+        cudaError_t e;
+        if (!s->capture_stream) {
+            e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+        }
+        e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        qs_status st = launch_plans(s, plans, s->capture_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s->capture_stream, &graph);
+        if (st != QS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (s->graphs.size() >= 16) {  // bounded cache: drop the oldest after the stream is idle
+            cudaStreamSynchronize(s->stream);
+            cudaGraphExecDestroy(s->graphs.front().exec);
+            s->graphs.erase(s->graphs.begin());
+        }
+        s->graphs.push_back({key, exec});
+    }
+    cudaError_t e = cudaGraphLaunch(exec, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return QS_OK;
+}
+
+qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
+                          double *energy, double *grad, int flags) {
+    if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
+    if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_adjoint_grad: gates is NULL");
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_OUT_DEVICE))
+        return set_error(QS_EINVAL, "qs_adjoint_grad: unknown flags");
+    if (flags & QS_FLAG_FUSE) return set_error(QS_EUNSUPPORTED, "qs_adjoint_grad: QS_FLAG_FUSE not built yet");
+    if (n_theta > 0 && !grad) return set_error(QS_EINVAL, "qs_adjoint_grad: grad is NULL");
+    if (n_theta > (size_t)(1 << 24)) return set_error(QS_EINVAL, "qs_adjoint_grad: n_theta too large");
+    const bool on_dev = (flags & QS_FLAG_OUT_DEVICE) != 0;
+
+    // Plans: forward, and for the sweep U^dagger (+ dU for parameterised gates).
+    std::vector<GatePlan> fwd(count), adj(count);
+    std::vector<int> slot_of(count, -1);
+    std::vector<int> slot_param;
+    std::vector<double> dus;  // 8 doubles per slot
+    char err[256], e2[200];
+    for (size_t i = 0; i < count; ++i) {
+        const qs_gate &g = gates[i];
+        if (!plan_record(s, g, theta, n_theta, i, &fwd[i], err, sizeof(err))) return set_error(QS_EINVAL, err);
+        double U[8], Ud[8];
+        int force = -1;
+        if (g.kind == QS_GATE_X) {
+            force = OP_SWAP;
+            std::memset(Ud, 0, sizeof(Ud));
+            Ud[2] = 1.0;
+            Ud[4] = 1.0;
+        } else {
+            if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) rot_matrix(g.kind, theta[g.param], U);
+            else std::memcpy(U, g.U, sizeof(U));
+            dagger(U, Ud);
+            if (g.kind == QS_GATE_RY) force = OP_GEN;
+            else if (g.kind == QS_GATE_RZ) force = OP_DIAG;
+        }
+        if (!plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, force, &adj[i], e2,
+                       sizeof(e2)))
+            return set_error(QS_EINVAL, e2);
+        if (adj[i].op == OP_SIDE) {  // the sweep kernels scale both sides
+            GatePlan q;
+            plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, OP_DIAG, &q, e2, sizeof(e2));
+            adj[i] = q;
+        }
+        if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) {
+            slot_of[i] = (int)slot_param.size();
+            slot_param.push_back(g.param);
+            double D[8];
+            rot_derivative(g.kind, theta[g.param], D);
+            dus.insert(dus.end(), D, D + 8);
+        }
+    }
+    const int nslots = (int)slot_param.size();
+
+    // Buffers: lambda, partials [nslots][P], slot sums, slot->param map, outputs.
+    cudaError_t e;
+    if (!s->lam) {
+        e = cudaMalloc(&s->lam, s->bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->lam = nullptr;
+            return set_error(QS_ENOMEM, "qs_adjoint_grad: cannot allocate the lambda vector");
+        }
+    }
+    const size_t P = adj_partials_per_slot();
+    const size_t need = (size_t)nslots * P + (size_t)nslots + (size_t)nslots + n_theta + 64 + 8;
+    if (s->grad_scratch_n < need) {
+        if (s->grad_scratch) cudaFree(s->grad_scratch);
+        s->grad_scratch = nullptr;
+        s->grad_scratch_n = 0;
+        e = cudaMalloc(&s->grad_scratch, need * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s->grad_scratch = nullptr;
+            return set_error(QS_ENOMEM, "qs_adjoint_grad: cannot allocate gradient scratch");
+        }
+        s->grad_scratch_n = need;
+    }
+    qs_status st = ensure_reduce_scratch(s);
+    if (st != QS_OK) return st;
+    double *part = s->grad_scratch;
+    double *slot_sum = part + (size_t)nslots * P;
+    int *slot_param_dev = reinterpret_cast<int *>(slot_sum + nslots);  // nslots ints fit in nslots doubles
+    double *grad_dev = slot_sum + 2 * (size_t)nslots;
+    double *energy_dev = grad_dev + n_theta;
+    cudaStream_t stm = s->stream;
+
+    // Forward pass.
+    st = launch_plans(s, fwd, stm);
+    if (st != QS_OK) return st;
+    // Energy and lambda = O psi.
+    double *z = s->red_scratch;
+    e = launch_expect_z(s->dtype, s->psi, s->n, s->red_scratch + 64, z, nullptr, stm);
+    if (e == cudaSuccess) e = launch_sum_vec(z, s->n, (on_dev && energy) ? energy : energy_dev, stm);
+    if (e == cudaSuccess) e = launch_obs_sumz(s->dtype, s->psi, s->lam, s->n, stm);
+    if (e == cudaSuccess && nslots > 0)
+        e = cudaMemsetAsync(part, 0, (size_t)nslots * P * sizeof(double), stm);
+    if (e == cudaSuccess && nslots > 0)
+        e = cudaMemcpyAsync(slot_param_dev, slot_param.data(), nslots * sizeof(int), cudaMemcpyHostToDevice, stm);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad setup");
+    // Reverse sweep.
+    for (size_t ii = count; ii-- > 0;) {
+        const int slot = slot_of[ii];
+        e = launch_adj_step(s->dtype, s->psi, s->lam, adj[ii], slot >= 0 ? &dus[8 * slot] : nullptr,
+                            slot >= 0 ? part + (size_t)slot * P : nullptr, stm);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad sweep launch");
+    }
+    e = launch_grad_final(part, nslots, slot_sum, slot_param_dev, on_dev ? grad : grad_dev, (int)n_theta, stm);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad final");
+    if (!on_dev) {
+        if (n_theta > 0) e = cudaMemcpyAsync(grad, grad_dev, n_theta * sizeof(double), cudaMemcpyDeviceToHost, stm);
+        if (e == cudaSuccess && energy)
+            e = cudaMemcpyAsync(energy, energy_dev, sizeof(double), cudaMemcpyDeviceToHost, stm);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stm);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad copy-out");
+    }
+    return QS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+"""GPU parity of the adjoint gradient: against the oracle's parameter-shift and
+finite-difference gradients, and properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2411_18354_gb300 as q
+
+    q.build()
+    return q
+
+
+def _adjoint(qs, n, dtype, gates, theta, psi0=None, flags=0):
+    st = qs.State(n, dtype)
+    try:
+        if psi0 is not None:
+            st.from_numpy(psi0)
+        e, g = st.adjoint_grad(gates, theta, flags)
+        back = st.to_numpy()
+    finally:
+        st.close()
+    return e, g, back
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 1e-4)])
+def test_hea_n10_against_parameter_shift(qs, dtype, tol):
+    """Hardware-efficient ansatz, n = 10, 20 layers (400 parameters) against the oracle's
+    parameter-shift gradient; complex64 within the stated 1e-4 gradient error."""
+    n, layers = 10, 20
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    e, g, back = _adjoint(qs, n, dtype, gates, th)
+    ps = oracle.param_shift_grad(n, gates, th)
+    e_ref = oracle.energy(n, gates, th)
+    assert abs(e - e_ref) <= tol
+    assert np.max(np.abs(g - ps)) <= tol
+    # the sweep un-applies every gate: the state is back to |0...0>
+    back = back.astype(np.complex128)
+    assert abs(back[0] - 1.0) <= (1e-10 if dtype == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-6), ("c64", 1e-4)])
+def test_controlled_rotations_against_finite_differences(qs, dtype, tol):
+    """Random circuit with controlled (also negatively controlled) RY/RZ, shared parameters
+    and fixed Haar gates, from a random start state, against central finite differences of
+    the oracle energy (h = 1e-4: truncation error O(h^2))."""
+    n = 7
+    rng = np.random.default_rng(17)
+    gl = []
+    for i in range(60):
+        t = int(rng.integers(0, n))
+        others = [q for q in range(n) if q != t]
+        c = int(rng.integers(0, 3))
+        ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+        vals = [int(b) for b in rng.integers(0, 2, size=c)]
+        r = rng.random()
+        if r < 0.35:
+            gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_RY, param=int(rng.integers(0, 12))))
+        elif r < 0.7:
+            gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_RZ, param=int(rng.integers(0, 12))))
+        elif r < 0.85:
+            gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_X))
+        else:
+            gl.append(W.make_gate(t, W.haar_2x2(rng), ctrls, vals))
+    gates = W.gate_list(gl)
+    th = rng.uniform(0, 2 * np.pi, size=14)  # parameters 12, 13 drive no gate
+    psi0 = W.random_state(n, 99, dtype=np.complex64 if dtype == "c64" else np.complex128)
+    e, g, _ = _adjoint(qs, n, dtype, gates, th, psi0)
+    fd = oracle.fd_grad(n, gates, th, h=1e-4, psi0=psi0.astype(np.complex128))
+    assert np.max(np.abs(g - fd)) <= tol
+    assert g[12] == 0.0 and g[13] == 0.0
+    assert abs(e - oracle.energy(n, gates, th, psi0.astype(np.complex128))) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_hea_n18_sampled_finite_differences(qs, dtype):
+    """n = 18, 20 layers: a few gradient entries against oracle finite differences."""
+    n, layers = 18, 20
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    e, g, _ = _adjoint(qs, n, dtype, gates, th)
+    h = 1e-4
+    for p in (0, 37, 401, 2 * n * layers - 1 - n):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (oracle.energy(n, gates, tp) - oracle.energy(n, gates, tm)) / (2 * h)
+        assert abs(g[p] - fd) <= (1e-6 if dtype == "c128" else 1e-4), p
+
+
+def test_hea_n24_properties(qs):
+    """The differentiation workload (n = 24, 20 layers, 960 parameters):
+    - the last layer's RZ angles do not change any Z probability (only a basis permutation
+      follows them), so their gradient entries are 0 up to rounding;
+    - the energy equals sum_i <Z_i> of the forward-only circuit;
+    - complex64 and complex128 gradients agree within 1e-4."""
+    n, layers = 24, 20
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    e64, g64, _ = _adjoint(qs, n, "c64", gates, th)
+    e128, g128, back = _adjoint(qs, n, "c128", gates, th)
+    last_rz = [2 * n * (layers - 1) + 2 * q + 1 for q in range(n)]
+    assert np.max(np.abs(g128[last_rz])) <= 1e-12
+    assert np.max(np.abs(g64[last_rz])) <= 1e-5
+    assert np.max(np.abs(g64 - g128)) <= 1e-4
+    st = qs.State(n, "c128")
+    try:
+        st.apply_circuit(gates, th)
+        z, _ = st.expect_z()
+    finally:
+        st.close()
+    assert abs(e128 - z.sum()) <= 1e-10
+    assert abs(back[0] - 1.0) <= 1e-10
+
+
+def test_device_outputs_and_autograd(qs):
+    import torch
+
+    from paper_2411_18354_gb300.autograd import AdjointEnergy
+
+    n, layers = 8, 3
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=5)
+    st = qs.State(n, "c128")
+    try:
+        e_host, g_host = st.adjoint_grad(gates, th)
+        st.set_basis(0)
+        de = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dg = torch.zeros(th.size, dtype=torch.float64, device="cuda")
+        qs.qs_adjoint_grad(st.h, gates, th, qs.QS_FLAG_OUT_DEVICE, de.data_ptr(), dg.data_ptr())
+        torch.cuda.synchronize()
+    finally:
+        st.close()
+    assert de.item() == e_host
+    assert np.array_equal(dg.cpu().numpy(), g_host)
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    E = AdjointEnergy.apply(theta, n, gates, "c128")
+    E.backward()
+    assert abs(E.item() - e_host) <= 1e-12
+    assert np.max(np.abs(theta.grad.cpu().numpy() - g_host)) <= 1e-12
