@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the controlled-gate path on GB300.
+
+Workload (the single-gate sweep at scale): an n = 30 complex64 state (8.6 GB, larger than
+L2) receives, per step, one Haar-random gate for every control count c = 0..8 and target
+t in {0, 15, 29} (27 gates), control sets rotating through 8 seeded sets per (c, t). The
+metric is algorithmic gate-apply bandwidth: 2 * 2^(n-c) amplitudes * 8 bytes per gate
+(read + write of the selected pairs), summed over the step, divided by the step's device
+time. Also reported: the same sweep end to end with host buffers, per-c bandwidth and
+fraction of the measured HBM peak, the complex128 sweep against the FP64 ALU bound, and
+the adjoint gradient (n = 24 hardware-efficient ansatz, 960 parameters) in complex64 vs
+the plain complex128 path.
+
+``--impl reference`` times the CPU oracle (plain loop over all 2^n indices with control
+checks) on the host cores instead, on a bounded sample of the same sweep.
+
+Multi-GPU: the path does not shard (every box has one GPU); under torchrun each rank runs
+an independent replica and rank 0 reports the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gate-apply GB/s & % HBM roofline at n=30, c=0..8; adjoint grads/s vs plain"
+CMAX = 8
+SETS = 8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--quick", action="store_true", help="headline sweep only (for profiler runs)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 ALU peak of GB300: 1.25 TFLOP/s dense (NVIDIA's published FP64 figure for the part;
+# 152 SMs at 2.07 GHz -> ~4 flops/clk/SM, i.e. 2 double FMA per clock per SM).
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    for name in ("k_gate.cuh", "k_gate_dispatch.cuh", "qs_plan.cu"):
+        with open(os.path.join(ROOT, "paper_2411_18354_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(n: int, dtype: str):
+    """DRAM bytes per gate launch from the committed ncu summary of this sweep, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"gate_sweep_n{n}_{dtype}.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch_mean:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def targets_for(n):
+    """Targets 0, 15, 29 at n = 30 (lowest, middle, highest qubit)."""
+    return (0, n // 2, n - 1)
+
+
+def sweep_schedule(n, seed=1):
+    import numpy as np
+
+    import workloads as W
+
+    sw = W.sweep_gates(n, CMAX, targets_for(n), sets=SETS, seed=seed)
+    sched = []  # per set index: list of (c, t, mask, vals, U8)
+    for s in range(SETS):
+        row = []
+        for t in targets_for(n):
+            for c in range(CMAX + 1):
+                g = sw[(c, t)][s]
+                row.append((c, t, int(g["ctrl_mask"]), int(g["ctrl_vals"]), np.ascontiguousarray(g["U"])))
+        sched.append(row)
+    return sched
+
+
+def alg_bytes(n, c, esize):
+    return 2 * (1 << (n - c)) * esize
+
+
+def run_sweep(qs, st, n, esize, sched, steps, warmup, per_launch=True):
+    """Device-timed sweep steps through qs_apply_gate. Returns per-launch ms and step ms."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    apply = qs._lib.qs_apply_gate
+    for w in range(warmup):
+        for (c, t, m, v, U) in sched[w % SETS]:
+            apply(st.h, t, m, v, U)
+    torch.cuda.synchronize()
+    launches = []  # (c, t, start_event, end_event)
+    step_ev = []
+    for k in range(steps):
+        row = sched[(warmup + k) % SETS]
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for (c, t, m, v, U) in row:
+            if per_launch:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                apply(st.h, t, m, v, U)
+                e1.record(stream)
+                launches.append((c, t, e0, e1))
+            else:
+                apply(st.h, t, m, v, U)
+        s1.record(stream)
+        step_ev.append((s0, s1))
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    per = [(c, t, a.elapsed_time(b)) for c, t, a, b in launches]
+    return step_ms, per
+
+
+def measure_adjoint(qs, W, reps=2):
+    """Differentiation workload: n = 24, 20 layers, 960 parameters. grads/s = parameters /
+    wall time of one full gradient (forward + energy + reverse sweep)."""
+    import numpy as np
+    import torch
+
+    n, layers = 24, 20
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    out = {}
+    grads = {}
+    for label, dtype, flags in (("c64", "c64", 0), ("c128_plain", "c128", 0)):
+        st = qs.State(n, dtype)
+        try:
+            st.adjoint_grad(gates, th, flags)  # warm-up (allocates lambda and scratch)
+            ts = []
+            for _ in range(reps):
+                st.set_basis(0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                e, g = st.adjoint_grad(gates, th, flags)
+                ts.append(time.perf_counter() - t0)
+            grads[label] = g
+            out[label] = {"s_per_gradient": min(ts), "grads_per_s": th.size / min(ts), "energy": e}
+        finally:
+            st.close()
+    out["max_abs_grad_diff_c64_vs_c128"] = float(np.max(np.abs(grads["c64"] - grads["c128_plain"])))
+    out["speedup_c64_vs_c128_plain"] = out["c128_plain"]["s_per_gradient"] / out["c64"]["s_per_gradient"]
+    out["workload"] = "HEA n=24, 20 layers (RY,RZ per qubit + CNOT ladder), 960 params, observable sum Z_i"
+    return out
+
+
+def cpu_oracle_sample(n_target: int, sched, max_gates=None):
+    """Time the CPU oracle (as it stands) on gates of the sweep; returns throughput in the
+    headline unit (algorithmic GB/s at 8 bytes per amplitude) and a description."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+
+    oracle.lib()
+    n = n_target
+    try:
+        psi = np.full(1 << n, 2.0 ** (-n / 2.0), dtype=np.complex128)
+    except MemoryError:
+        n = 26
+        psi = np.full(1 << n, 2.0 ** (-n / 2.0), dtype=np.complex128)
+    row = sched[0] if max_gates is None else sched[0][:max_gates]
+    total_bytes = 0
+    t0 = time.perf_counter()
+    for (c, t, m, v, U) in row:
+        oracle.apply_gate(psi, n, t, m, v, U)
+        total_bytes += alg_bytes(n, c, 8)
+    dt = time.perf_counter() - t0
+    return {"value": total_bytes / dt / 1e9, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(row)} sweep gates (c=0..8, t=0/15/29) on an n={n} state, float64 oracle loop over all "
+                      f"2^n indices; bytes counted as complex64 algorithmic bytes of the same gates",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle on the host cores, same metric/unit/config."""
+    if rank != 0:
+        return
+    sched = sweep_schedule(args.n)
+    import numpy as np
+
+    import oracle
+
+    oracle.lib()
+    n = args.n
+    psi = np.full(1 << n, 2.0 ** (-n / 2.0), dtype=np.complex128)
+    # bounded sample per step: 9 gates (one target, c = 0..8)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        row = sched[k % SETS][9 * (k % 3): 9 * (k % 3) + 9]
+        t0 = time.perf_counter()
+        byts = 0
+        for (c, t, m, v, U) in row:
+            oracle.apply_gate(psi, n, t, m, v, U)
+            byts += alg_bytes(n, c, 8)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            vals.append((byts, dt))
+    tot_b = sum(b for b, _ in vals)
+    tot_t = sum(t for _, t in vals)
+    value = tot_b / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"single-gate sweep n={n}, c=0..8, t=0/15/29 (one target per step)",
+                   "state": "uniform superposition", "l2": "state larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"per step 9 gates (one target, c=0..8) on an n={n} float64 state"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    torch.cuda.set_device(local_rank)
+    n = args.n
+    esize = 8
+    sched = sweep_schedule(n)
+    st = qs.State(n, "c64")
+    # input: uniform superposition (H on every qubit), built by the library
+    for q in range(n):
+        st.apply_gate(q, W.H_MATRIX)
+    torch.cuda.synchronize()
+    peak, peak_src = load_peaks()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    step_ms, per = run_sweep(qs, st, n, esize, sched, args.steps, args.warmup)
+    t_wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    step_bytes = sum(alg_bytes(n, c, esize) for (c, _, _, _, _) in sched[0])
+    value = world * args.steps * step_bytes / (total_ms * 1e-3) / 1e9
+
+    # per-launch roofline of the gate kernel (algorithmic bytes / CUDA-event launch time)
+    launch_bytes = sum(alg_bytes(n, c, esize) for c, _, _ in per)
+    launch_ms = sum(ms for _, _, ms in per)
+    achieved = launch_bytes / (launch_ms * 1e-3) / 1e9
+    per_c = {}
+    for c in range(CMAX + 1):
+        ms = [x for cc, _, x in per if cc == c]
+        b = alg_bytes(n, c, esize) * len(ms)
+        gbs = b / (sum(ms) * 1e-3) / 1e9
+        per_c[str(c)] = {"ms_per_gate": statistics.mean(ms), "GBps": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    traffic = profiled_traffic(n, "c64")
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic)", "data": "synthetic",
+        "config": {"workload": f"single-gate sweep: n={n} complex64 state, Haar gates with c=0..8 controls on random "
+                               f"qubits, targets 0/15/29, 8 rotating control sets (27 gates/step)",
+                   "n": n, "gates_per_step": len(sched[0]), "bytes_counted": "2*2^(n-c)*8 per gate",
+                   "l2": "inputs larger than L2 (8.6 GB state)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_gate (qs_apply_gate)"},
+        "per_c": per_c,
+        "gpu_launches": len(per),
+        "clocks": clocks,
+    }
+
+    if not args.quick:
+        # end to end: host (pinned) -> device, the 27 gates, device -> host, through the C-ABI
+        host = torch.empty(1 << n, dtype=torch.complex64).pin_memory()
+        hnp = host.numpy()
+        st.to_numpy()  # warm path
+        qs._lib.qs_state_copy_to_host(st.h, hnp)
+        e2e_steps = 2
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            qs._lib.qs_state_copy_from_host(st.h, hnp)
+            for (c, t, m, v, U) in sched[k % SETS]:
+                qs._lib.qs_apply_gate(st.h, t, m, v, U)
+            qs._lib.qs_state_copy_to_host(st.h, hnp)
+        e2e_s = time.perf_counter() - t0
+        result["e2e"] = {"value": round(world * e2e_steps * step_bytes / e2e_s / 1e9, 2), "unit": "GB/s",
+                         "h2d_bytes_per_step": int(hnp.nbytes), "d2h_bytes_per_step": int(hnp.nbytes)}
+        del host, hnp
+
+    st.close()
+    torch.cuda.empty_cache()
+
+    if not args.quick and rank == 0:
+        # complex128 sweep (one step): FP64 ALU roofline
+        st2 = qs.State(n, "c128")
+        for q in range(n):
+            st2.apply_gate(q, W.H_MATRIX)
+        sm2, per2 = run_sweep(qs, st2, n, 16, sched, 1, 1)
+        st2.close()
+        torch.cuda.empty_cache()
+        b2 = sum(alg_bytes(n, c, 16) for c, _, _ in per2)
+        ms2 = sum(x for _, _, x in per2)
+        pairs = sum(1 << (n - 1 - c) for c, _, _ in per2)
+        flops = 28.0 * pairs  # general 2x2 complex update: 12 FMA + 4 MUL per pair, FMA = 2 flops
+        result["c128_sweep"] = {
+            "GBps": round(b2 / (ms2 * 1e-3) / 1e9, 1), "frac_hbm": round(b2 / (ms2 * 1e-3) / 1e9 / peak, 3),
+            "roofline": {"bound": "alu", "achieved": round(flops / (ms2 * 1e-3) / 1e12, 3),
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                         "frac": round(flops / (ms2 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)},
+        }
+        result["adjoint"] = measure_adjoint(qs, W)
+        result["cpu_baseline"] = cpu_oracle_sample(n, sched)
+
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -72,6 +72,11 @@ def _check_state(psi: np.ndarray, n: int):
         raise ValueError("oracle state must be a contiguous complex128 array of 2^n amplitudes")
 
 
+def _check_gate(n: int, t: int, ctrl_mask: int, ctrl_vals: int):
+    if not (0 <= t < n) or ctrl_mask >> n or (ctrl_mask >> t) & 1 or ctrl_vals & ~ctrl_mask:
+        raise ValueError(f"invalid gate for n={n}: t={t}, mask={ctrl_mask:#x}, vals={ctrl_vals:#x}")
+
+
 def _u8(U) -> np.ndarray:
     U = np.asarray(U)
     if U.dtype == np.complex128 or U.shape == (2, 2):
@@ -99,6 +104,7 @@ def eq4_map(i_r: int, t: int, controls) -> int:
 def apply_gate(psi: np.ndarray, n: int, t: int, ctrl_mask: int, ctrl_vals: int, U) -> None:
     """In place: Eq. 2 on the pairs of target t whose bits under ctrl_mask equal ctrl_vals."""
     _check_state(psi, n)
+    _check_gate(n, t, ctrl_mask, ctrl_vals)
     u = _u8(U)
     lib().oracle_apply_gate(_ptr(psi.view(np.float64)), n, t, ctrl_mask, ctrl_vals, _ptr(u))
 
@@ -106,6 +112,7 @@ def apply_gate(psi: np.ndarray, n: int, t: int, ctrl_mask: int, ctrl_vals: int, 
 def apply_x(psi: np.ndarray, n: int, t: int, ctrl_mask: int = 0, ctrl_vals: int = 0) -> None:
     """In place: exchange the amplitudes of every selected pair (X, CNOT, Toffoli)."""
     _check_state(psi, n)
+    _check_gate(n, t, ctrl_mask, ctrl_vals)
     lib().oracle_apply_x(_ptr(psi.view(np.float64)), n, t, ctrl_mask, ctrl_vals)
 
 
