@@ -45,6 +45,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=30)
     ap.add_argument("--quick", action="store_true", help="headline sweep only (for profiler runs)")
+    ap.add_argument("--ncu-case", type=int, default=None, metavar="C",
+                    help="small profiling case: the 3 sweep gates with C controls (set 0) at --n, run twice "
+                         "(profile with -s 3 -c 3 to skip the first round)")
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"], help="state precision of --ncu-case")
     return ap.parse_args()
 
 
@@ -402,8 +406,28 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(result), flush=True)
 
 
+def run_ncu_case(args):
+    """Profiling case: no timing, no output besides one status line."""
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+
+    qs.build()
+    rows = [r for r in sweep_schedule(args.n)[0] if r[0] == args.ncu_case]
+    st = qs.State(args.n, args.dtype)
+    for _ in range(2):
+        for (c, t, m, v, U) in rows:
+            qs._lib.qs_apply_gate(st.h, t, m, v, U)
+    torch.cuda.synchronize()
+    st.close()
+    print(f"ncu case done: n={args.n} c={args.ncu_case} {args.dtype} targets={[r[1] for r in rows]}")
+
+
 def main():
     args = parse_args()
+    if args.ncu_case is not None:
+        run_ncu_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
