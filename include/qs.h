@@ -160,6 +160,26 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
  * asynchronous; otherwise they are host pointers and the call synchronises the stream. */
 qs_status qs_expect_z(const qs_state *s, double *out, double *out_norm2, int flags);
 
+/* Same results as qs_expect_z, for callers that cannot allocate device memory: code whose
+ * device memory belongs to another allocator (a framework pool or a fixed arena), code on a
+ * latency budget that cannot afford a cudaMalloc, code that must not run out of memory in
+ * the middle of a job. No device or host memory is allocated by this call. (The paper has
+ * no counterpart; this is an interface addition.)
+ *  - psi: device pointer to 2^n amplitudes of `dtype` (16-byte aligned), read only.
+ *  - out_z (n doubles) / out_norm2 (1 double): device pointers, either may be NULL (not both).
+ *  - Enqueued on `stream`; returns without waiting.
+ *  - The per-block partial sums go to one fixed device array inside the library
+ *    (1024 * 41 doubles = 335,872 bytes per device, held until the process exits), which
+ *    covers every n <= 40; larger requests are rejected with QS_EINVAL.
+ *  - The first call on a device looks up that array's device address (a runtime query,
+ *    done once per device with the device current); make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the array. Calls that may run at the same time on the GPU
+ *    (other streams, other host threads) overwrite each other's partial sums: serialise
+ *    them. Nothing needs clearing between calls: each call writes every slot it reads. */
+qs_status qs_expect_z_noalloc(const void *psi, int n, qs_dtype dtype, void *stream, double *out_z,
+                              double *out_norm2);
+
 /* ------------------------------------------------------------------------------------ */
 /* Adjoint gradient (reverse sweep that un-applies gates; no checkpoints)               */
 /* ------------------------------------------------------------------------------------ */

@@ -51,6 +51,7 @@ _SIGNATURES = [
     ("qs_apply_gate_masked", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
     ("qs_apply_circuit", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, ctypes.c_int]),
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
+    ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
 ]
 
@@ -194,6 +195,14 @@ def qs_expect_z(h: int, flags: int = 0, out=None, out_norm2=None):
     nrm = np.empty(1)
     _check(lib().qs_expect_z(_c_state_p(h), z.ctypes.data_as(_dp), nrm.ctypes.data_as(_dp), flags))
     return z, float(nrm[0])
+
+
+def qs_expect_z_noalloc(psi_dev: int, n: int, dtype: int, stream: int, out_z_dev: int, out_norm2_dev: int) -> None:
+    """<Z_i> and the squared norm of the 2^n amplitudes at device address ``psi_dev``, written
+    to device addresses (ints; 0 = not wanted), without allocating anything (see qs.h)."""
+    _check(lib().qs_expect_z_noalloc(_vp(psi_dev), n, dtype, _vp(stream or None),
+                                     _dptr(out_z_dev) if out_z_dev else None,
+                                     _dptr(out_norm2_dev) if out_norm2_dev else None))
 
 
 def qs_adjoint_grad(h: int, gates, theta, flags: int = 0, energy_out=None, grad_out=None):

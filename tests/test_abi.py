@@ -50,6 +50,11 @@ def test_binding_covers_every_declared_symbol():
         assert hasattr(L, name)
 
 
+def test_package_reexports_every_declared_symbol():
+    for name in _declared():
+        assert callable(getattr(qs, name, None)), name
+
+
 def test_gate_dtype_matches_struct_layout():
     g = qs.GATE_DTYPE
     assert g.itemsize == 96
