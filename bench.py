@@ -124,7 +124,7 @@ def kernel_source_hash() -> str:
 def profiled_traffic(n: int, dtype: str):
     """DRAM bytes per gate launch from the committed ncu summary of this sweep, if it was
     taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", f"gate_sweep_n{n}_{dtype}.md")
+    p = os.path.join(ROOT, "profiles", f"k_gate_sweep_n{n}_{dtype}_traffic.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
