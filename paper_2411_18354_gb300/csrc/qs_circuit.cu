@@ -1,11 +1,14 @@
 // qs_circuit.cu -- qs_apply_circuit and qs_adjoint_grad: whole gate lists, validated
 // up front, launched per gate (or per fused tile pass) on the state's stream, optionally
 // recorded once into a CUDA graph and replayed.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
+#include "qs_fuse.cuh"
 #include "qs_internal.cuh"
 #include "qs_state.cuh"
 
@@ -20,8 +23,14 @@ cudaError_t launch_grad_final(const double *part, int nslots, double *slot_sum, 
                               double *grad, int nparams, cudaStream_t st);
 
 void release_state_buffers(qs_state *s) {
-    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : s->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        if (g.table) cudaFree(g.table);
+    }
     s->graphs.clear();
+    if (s->tile_table) cudaFree(s->tile_table);
+    s->tile_table = nullptr;
+    s->tile_table_bytes = 0;
     if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     s->capture_stream = nullptr;
     if (s->red_scratch) cudaFree(s->red_scratch);
@@ -119,6 +128,59 @@ static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, c
     return QS_OK;
 }
 
+// Local qubits per tile of a fused pass (shared memory per CTA: 2^k amplitudes, twice that
+// for the adjoint's psi and lambda tiles).
+static int tile_bits(int dtype, bool adjoint) {
+    const char *env = std::getenv("QS_TILE_BITS");
+    if (env && *env) {
+        const int v = std::atoi(env);
+        if (v >= 2 && v <= kTileMaxBits) return v;
+    }
+    if (dtype == QS_C64) return adjoint ? 11 : 12;
+    return adjoint ? 10 : 11;
+}
+
+// Make sure `*buf` (device) holds `bytes`; grow-only. The old buffer may still be read by
+// work queued on `st`, so the stream is drained before it is freed.
+static qs_status ensure_device(void **buf, size_t *cap, size_t bytes, cudaStream_t st, const char *what) {
+    if (*buf && *cap >= bytes) return QS_OK;
+    if (*buf) {
+        cudaStreamSynchronize(st);
+        cudaFree(*buf);
+    }
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return set_error(QS_ENOMEM, what);
+    }
+    *cap = std::max<size_t>(bytes, 256);
+    return QS_OK;
+}
+
+// Launch a fused program. Forward: `lam` == nullptr. Adjoint: single gates use the sweep
+// kernel with dus[g] / part + slot * P, passes use the adjoint tile kernel.
+static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std::vector<GatePlan> &plans,
+                                const TileGate *dev_table, void *lam, const std::vector<const double *> *dus,
+                                const std::vector<int> *slots, double *part, size_t P, cudaStream_t st) {
+    for (const FusedOp &op : prog.ops) {
+        cudaError_t e;
+        if (op.pass >= 0) {
+            e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], dev_table, part, P, st);
+        } else if (!lam) {
+            e = launch_gate(s->dtype, s->psi, plans[op.gate], st);
+        } else {
+            const int slot = (*slots)[op.gate];
+            e = launch_adj_step(s->dtype, s->psi, lam, plans[op.gate], (*dus)[op.gate],
+                                slot >= 0 ? part + (size_t)slot * P : nullptr, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "fused program launch");
+    }
+    return QS_OK;
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -130,48 +192,96 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_apply_circuit: gates is NULL");
     if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH)) return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
-    if (flags & QS_FLAG_FUSE) return set_error(QS_EUNSUPPORTED, "qs_apply_circuit: QS_FLAG_FUSE not built yet");
     std::vector<GatePlan> plans(count);
     char err[256];
     for (size_t i = 0; i < count; ++i)
         if (!plan_record(s, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
-    if (!(flags & QS_FLAG_GRAPH)) return launch_plans(s, plans, s->stream);
+    const bool fuse = (flags & QS_FLAG_FUSE) != 0;
+    FusedProgram prog;
+    if (fuse) {
+        std::vector<int> seq(count);
+        for (size_t i = 0; i < count; ++i) seq[i] = (int)i;
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog);
+    }
+    const size_t table_bytes = prog.gates.size() * sizeof(TileGate);
 
-    // CUDA graph: record once per distinct (gates, theta, flags), then replay.
+    if (!(flags & QS_FLAG_GRAPH)) {
+        if (!fuse) return launch_plans(s, plans, s->stream);
+        qs_status st = ensure_device(&s->tile_table, &s->tile_table_bytes, table_bytes, s->stream,
+                                     "qs_apply_circuit: cannot allocate the fused gate table");
+        if (st != QS_OK) return st;
+        if (table_bytes) {
+            // stream-ordered: earlier passes on this stream have read the previous table
+            cudaError_t e = cudaMemcpyAsync(s->tile_table, prog.gates.data(), table_bytes, cudaMemcpyHostToDevice,
+                                            s->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit: gate table upload");
+        }
+        return launch_program(s, prog, plans, static_cast<const TileGate *>(s->tile_table), nullptr, nullptr,
+                              nullptr, nullptr, 0, s->stream);
+    }
+
+    // CUDA graph: record once per distinct (gates, theta, flags, buffer), then replay.
     uint64_t key = 1469598103934665603ull;
     key = fnv1a(key, gates, count * sizeof(qs_gate));
     if (theta) key = fnv1a(key, theta, n_theta * sizeof(double));
     key = fnv1a(key, &flags, sizeof(flags));
     key = fnv1a(key, &s->psi, sizeof(s->psi));
+    const int tb = tile_bits(s->dtype, false);
+    key = fnv1a(key, &tb, sizeof(tb));
     cudaGraphExec_t exec = nullptr;
     for (auto &g : s->graphs)
         if (g.key == key) exec = g.exec;
     if (!exec) {
         cudaError_t e;
+        void *table = nullptr;
+        if (table_bytes) {
+            e = cudaMalloc(&table, table_bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(QS_ENOMEM, "qs_apply_circuit: cannot allocate the graph's gate table");
+            }
+            e = cudaMemcpy(table, prog.gates.data(), table_bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(table);
+                return cuda_fail(e, "qs_apply_circuit: gate table upload");
+            }
+        }
         if (!s->capture_stream) {
             e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+            if (e != cudaSuccess) {
+                if (table) cudaFree(table);
+                return cuda_fail(e, "capture stream");
+            }
         }
         e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        qs_status st = launch_plans(s, plans, s->capture_stream);
+        if (e != cudaSuccess) {
+            if (table) cudaFree(table);
+            return cuda_fail(e, "cudaStreamBeginCapture");
+        }
+        qs_status st = fuse ? launch_program(s, prog, plans, static_cast<const TileGate *>(table), nullptr, nullptr,
+                                             nullptr, nullptr, 0, s->capture_stream)
+                            : launch_plans(s, plans, s->capture_stream);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(s->capture_stream, &graph);
-        if (st != QS_OK) {
+        if (st != QS_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return st;
+            if (table) cudaFree(table);
+            return st != QS_OK ? st : cuda_fail(e, "cudaStreamEndCapture");
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (e != cudaSuccess) {
+            if (table) cudaFree(table);
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
         if (s->graphs.size() >= 16) {  // bounded cache: drop the oldest after the stream is idle
             cudaStreamSynchronize(s->stream);
             cudaGraphExecDestroy(s->graphs.front().exec);
+            if (s->graphs.front().table) cudaFree(s->graphs.front().table);
             s->graphs.erase(s->graphs.begin());
         }
-        s->graphs.push_back({key, exec});
+        s->graphs.push_back({key, exec, table});
     }
     cudaError_t e = cudaGraphLaunch(exec, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
@@ -184,7 +294,6 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_adjoint_grad: gates is NULL");
     if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_OUT_DEVICE))
         return set_error(QS_EINVAL, "qs_adjoint_grad: unknown flags");
-    if (flags & QS_FLAG_FUSE) return set_error(QS_EUNSUPPORTED, "qs_adjoint_grad: QS_FLAG_FUSE not built yet");
     if (n_theta > 0 && !grad) return set_error(QS_EINVAL, "qs_adjoint_grad: grad is NULL");
     if (n_theta > (size_t)(1 << 24)) return set_error(QS_EINVAL, "qs_adjoint_grad: n_theta too large");
     const bool on_dev = (flags & QS_FLAG_OUT_DEVICE) != 0;
@@ -229,6 +338,19 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
         }
     }
     const int nslots = (int)slot_param.size();
+    const bool fuse = (flags & QS_FLAG_FUSE) != 0;
+    FusedProgram pf, pa;
+    std::vector<const double *> dusp(count, nullptr);
+    if (fuse) {
+        std::vector<int> seq(count);
+        for (size_t i = 0; i < count; ++i) seq[i] = (int)i;
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &pf);
+        for (size_t i = 0; i < count; ++i) {
+            seq[i] = (int)(count - 1 - i);
+            if (slot_of[i] >= 0) dusp[i] = &dus[8 * slot_of[i]];
+        }
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &dusp, &slot_of, &pa);
+    }
 
     // Buffers: lambda, partials [nslots][P], slot sums, slot->param map, outputs.
     cudaError_t e;
@@ -263,8 +385,22 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     double *energy_dev = grad_dev + n_theta;
     cudaStream_t stm = s->stream;
 
+    // Gate tables of the fused forward and sweep programs (one upload, stream-ordered).
+    const size_t nf = pf.gates.size(), na = pa.gates.size();
+    if (fuse && nf + na > 0) {
+        st = ensure_device(&s->tile_table, &s->tile_table_bytes, (nf + na) * sizeof(TileGate), stm,
+                           "qs_adjoint_grad: cannot allocate the fused gate table");
+        if (st != QS_OK) return st;
+        std::vector<TileGate> both(pf.gates);
+        both.insert(both.end(), pa.gates.begin(), pa.gates.end());
+        e = cudaMemcpyAsync(s->tile_table, both.data(), both.size() * sizeof(TileGate), cudaMemcpyHostToDevice, stm);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad: gate table upload");
+    }
+    const TileGate *tab_f = static_cast<const TileGate *>(s->tile_table);
+    const TileGate *tab_a = tab_f ? tab_f + nf : nullptr;
     // Forward pass.
-    st = launch_plans(s, fwd, stm);
+    st = fuse ? launch_program(s, pf, fwd, tab_f, nullptr, nullptr, nullptr, nullptr, 0, stm)
+              : launch_plans(s, fwd, stm);
     if (st != QS_OK) return st;
     // Energy and lambda = O psi.
     double *z = s->red_scratch;
@@ -277,11 +413,16 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
         e = cudaMemcpyAsync(slot_param_dev, slot_param.data(), nslots * sizeof(int), cudaMemcpyHostToDevice, stm);
     if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad setup");
     // Reverse sweep.
-    for (size_t ii = count; ii-- > 0;) {
-        const int slot = slot_of[ii];
-        e = launch_adj_step(s->dtype, s->psi, s->lam, adj[ii], slot >= 0 ? &dus[8 * slot] : nullptr,
-                            slot >= 0 ? part + (size_t)slot * P : nullptr, stm);
-        if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad sweep launch");
+    if (fuse) {
+        st = launch_program(s, pa, adj, tab_a, s->lam, &dusp, &slot_of, part, P, stm);
+        if (st != QS_OK) return st;
+    } else {
+        for (size_t ii = count; ii-- > 0;) {
+            const int slot = slot_of[ii];
+            e = launch_adj_step(s->dtype, s->psi, s->lam, adj[ii], slot >= 0 ? &dus[8 * slot] : nullptr,
+                                slot >= 0 ? part + (size_t)slot * P : nullptr, stm);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad sweep launch");
+        }
     }
     e = launch_grad_final(part, nslots, slot_sum, slot_param_dev, on_dev ? grad : grad_dev, (int)n_theta, stm);
     if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad final");

@@ -56,6 +56,9 @@ struct GatePlan {
     uint64_t units;     // number of work units
     IndexMap map;       // counter -> first amplitude of the unit
     double U[8];        // matrix (for OP_SIDE: U[0..1] = scalar)
+    uint64_t ctrl_mask; // the gate as given (for the fused tile pass)
+    uint64_t ctrl_vals;
+    double Ufull[8];    // full matrix (exchange: [[0,1],[1,0]])
 };
 
 // Host planning (qs_plan.cpp): builds the sorted insertion positions and picks op/layout.
@@ -63,6 +66,8 @@ struct GatePlan {
 // force_op >= 0 skips the structure analysis and uses that GateOp with the full U.
 bool plan_gate(int n, int dtype, int target, uint64_t ctrl_mask, uint64_t ctrl_vals,
                const double U[8], int kind, int force_op, GatePlan *out, char *err, size_t errlen);
+// Counter -> index segments for inserted positions pos[0..m-1] (ascending, values `ins`).
+void build_map(int n, const int *pos, int m, uint64_t ins, IndexMap *map);
 // Same plan with all 2^(n-1) pairs scheduled and masked (baseline comparator).
 void plan_masked(const GatePlan &compact, GatePlan *out);
 

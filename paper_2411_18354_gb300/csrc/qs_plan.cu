@@ -34,7 +34,7 @@ static int ctz64(uint64_t v) { return __builtin_ctzll(v); }
 // values `ins`. Segment s collects the free bits between pos[s-1] and pos[s]; each of
 // them comes from the counter bit s places lower (Eq. 4 applied for every inserted
 // position in ascending order, Section III-B).
-static void build_map(int n, const int *pos, int m, uint64_t ins, IndexMap *map) {
+void build_map(int n, const int *pos, int m, uint64_t ins, IndexMap *map) {
     std::memset(map, 0, sizeof(*map));
     map->ins = ins;
     int ns = 0;
@@ -90,6 +90,14 @@ bool plan_gate(int n, int dtype, int target, uint64_t ctrl_mask, uint64_t ctrl_v
     p->t = target;
     p->tbit = tbit;
     p->c = __builtin_popcountll(ctrl_mask);
+    p->ctrl_mask = ctrl_mask;
+    p->ctrl_vals = ctrl_vals;
+    if (kind == QS_GATE_X) {
+        p->Ufull[2] = 1.0;
+        p->Ufull[4] = 1.0;
+    } else if (U) {
+        std::memcpy(p->Ufull, U, sizeof(p->Ufull));
+    }
 
     // Operation class from the exact structure of U (exact zeros and ones only).
     if (force_op >= 0) {

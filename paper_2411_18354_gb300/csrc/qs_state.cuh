@@ -15,6 +15,7 @@ constexpr uint32_t kStateMagic = 0x51535354u;  // "QSST"
 struct GraphCacheEntry {
     uint64_t key;
     cudaGraphExec_t exec;
+    void *table;  // device gate table of the fused passes recorded in the graph (or null)
 };
 
 }  // namespace qs
@@ -34,6 +35,8 @@ struct qs_state {
     void *lam = nullptr;            // adjoint: second vector (lambda), same size as psi
     double *grad_scratch = nullptr; // adjoint: per-gate, per-block partial inner products
     size_t grad_scratch_n = 0;
+    void *tile_table = nullptr;     // fused passes: device copy of the tile gate table
+    size_t tile_table_bytes = 0;
     // CUDA graphs of circuits, keyed by a hash of the gate list, theta and flags
     cudaStream_t capture_stream = nullptr;
     std::vector<qs::GraphCacheEntry> graphs;

@@ -29,14 +29,15 @@ def _adjoint(qs, n, dtype, gates, theta, psi0=None, flags=0):
     return e, g, back
 
 
+@pytest.mark.parametrize("fuse", [0, 1])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 1e-4)])
-def test_hea_n10_against_parameter_shift(qs, dtype, tol):
+def test_hea_n10_against_parameter_shift(qs, dtype, tol, fuse):
     """Hardware-efficient ansatz, n = 10, 20 layers (400 parameters) against the oracle's
     parameter-shift gradient; complex64 within the stated 1e-4 gradient error."""
     n, layers = 10, 20
     gates = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
-    e, g, back = _adjoint(qs, n, dtype, gates, th)
+    e, g, back = _adjoint(qs, n, dtype, gates, th, flags=qs.QS_FLAG_FUSE if fuse else 0)
     ps = oracle.param_shift_grad(n, gates, th)
     e_ref = oracle.energy(n, gates, th)
     assert abs(e - e_ref) <= tol
@@ -46,8 +47,9 @@ def test_hea_n10_against_parameter_shift(qs, dtype, tol):
     assert abs(back[0] - 1.0) <= (1e-10 if dtype == "c128" else 1e-4)
 
 
+@pytest.mark.parametrize("tile_bits", [None, 3, 6])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-6), ("c64", 1e-4)])
-def test_controlled_rotations_against_finite_differences(qs, dtype, tol):
+def test_controlled_rotations_against_finite_differences(qs, dtype, tol, tile_bits, monkeypatch):
     """Random circuit with controlled (also negatively controlled) RY/RZ, shared parameters
     and fixed Haar gates, from a random start state, against central finite differences of
     the oracle energy (h = 1e-4: truncation error O(h^2))."""
@@ -72,7 +74,11 @@ def test_controlled_rotations_against_finite_differences(qs, dtype, tol):
     gates = W.gate_list(gl)
     th = rng.uniform(0, 2 * np.pi, size=14)  # parameters 12, 13 drive no gate
     psi0 = W.random_state(n, 99, dtype=np.complex64 if dtype == "c64" else np.complex128)
-    e, g, _ = _adjoint(qs, n, dtype, gates, th, psi0)
+    flags = 0
+    if tile_bits is not None:
+        monkeypatch.setenv("QS_TILE_BITS", str(tile_bits))
+        flags = qs.QS_FLAG_FUSE
+    e, g, _ = _adjoint(qs, n, dtype, gates, th, psi0, flags=flags)
     fd = oracle.fd_grad(n, gates, th, h=1e-4, psi0=psi0.astype(np.complex128))
     assert np.max(np.abs(g - fd)) <= tol
     assert g[12] == 0.0 and g[13] == 0.0
@@ -106,6 +112,10 @@ def test_hea_n24_properties(qs):
     th = W.hea_params(n, layers, seed=3)
     e64, g64, _ = _adjoint(qs, n, "c64", gates, th)
     e128, g128, back = _adjoint(qs, n, "c128", gates, th)
+    e64f, g64f, _ = _adjoint(qs, n, "c64", gates, th, flags=qs.QS_FLAG_FUSE)
+    e128f, g128f, _ = _adjoint(qs, n, "c128", gates, th, flags=qs.QS_FLAG_FUSE)
+    assert np.max(np.abs(g128f - g128)) <= 1e-10 and abs(e128f - e128) <= 1e-10
+    assert np.max(np.abs(g64f - g128)) <= 1e-4
     last_rz = [2 * n * (layers - 1) + 2 * q + 1 for q in range(n)]
     assert np.max(np.abs(g128[last_rz])) <= 1e-12
     assert np.max(np.abs(g64[last_rz])) <= 1e-5

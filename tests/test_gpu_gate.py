@@ -228,3 +228,60 @@ def test_full_size_sweep_sampled(qs, dtype):
         st.close()
         del buf
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("tile_bits", [2, 5, 9, 12])
+def test_fused_circuits_match_oracle(qs, dtype, tile_bits, monkeypatch):
+    """QS_FLAG_FUSE (and FUSE | GRAPH): runs of gates grouped into shared-memory tile passes
+    give the oracle's state, for several tile sizes, random controls (also negative, also
+    on non-local qubits), diagonal / one-sided / exchange gates and tile predicates."""
+    monkeypatch.setenv("QS_TILE_BITS", str(tile_bits))
+    rng = np.random.default_rng(tile_bits)
+    for n in (3, 9, 14, 17):
+        gl = []
+        for i in range(120):
+            t = int(rng.integers(0, n))
+            others = [q for q in range(n) if q != t]
+            c = int(rng.integers(0, min(3, n - 1) + 1))
+            ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+            vals = [int(b) for b in rng.integers(0, 2, size=c)]
+            r = rng.random()
+            if r < 0.15:
+                gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_X))
+            elif r < 0.3:
+                gl.append(W.make_gate(t, np.diag(np.exp(1j * rng.uniform(0, 6, 2))), ctrls, vals))
+            elif r < 0.4:
+                gl.append(W.make_gate(t, np.diag([1.0, np.exp(0.3j)]), ctrls, vals))
+            else:
+                gl.append(W.make_gate(t, W.haar_2x2(rng), ctrls, vals))
+        gates = W.gate_list(gl)
+        psi0 = random_state(n, dtype, n)
+        ref = _run_oracle(n, psi0, gates)
+        for flags in (qs.QS_FLAG_FUSE, qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH):
+            st = qs.State(n, dtype)
+            try:
+                st.from_numpy(psi0)
+                st.apply_circuit(gates, flags=flags)
+                got = c128_of(st.to_numpy())
+            finally:
+                st.close()
+            assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype], (n, flags)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fused_ansatz_matches_unfused(qs, dtype):
+    """The differentiation ansatz (n = 20, 4 layers) fused and unfused, against the oracle."""
+    n, layers = 20, 4
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    psi0 = W.basis_state(n, 0, NP[dtype])
+    ref = _run_oracle(n, psi0, gates, th)
+    for flags in (0, qs.QS_FLAG_FUSE):
+        st = qs.State(n, dtype)
+        try:
+            st.apply_circuit(gates, th, flags=flags)
+            got = c128_of(st.to_numpy())
+        finally:
+            st.close()
+        assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype], flags
