@@ -197,6 +197,44 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count,
                           const double *theta, size_t n_theta, double *energy,
                           double *grad, int flags);
 
+/* ------------------------------------------------------------------------------------ */
+/* Batched forward energy + adjoint gradient (one persistent launch in a CUDA graph)     */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct qs_batch qs_batch;  /* opaque */
+
+/* Plan a batch of independent states. State s has n_qubits[s] qubits (1..30), starts from
+ * |0...0>, runs gates[gate_offsets[s] .. gate_offsets[s+1]) (qs_gate records; RY/RZ
+ * parameter indices are relative to the state), and owns the parameters
+ * theta[param_offsets[s] .. param_offsets[s+1]) (at most 4096 per state). Both offset arrays
+ * have num_states + 1 entries and start at 0. The observable is sum_i Z_i for every state.
+ * Tuning (0 = library default): small_bits — states with n <= small_bits stay in shared memory
+ * for the whole computation; tile_bits (5..14) — local qubits of the tile passes of larger
+ * states; max_pass_gates — gates per tile pass (fusion depth). All arguments are host
+ * memory and copied; everything is validated before any device work. Allocates the device
+ * descriptors and, for states above small_bits, a per-CTA workspace of two vectors of the
+ * largest such state. ENOMEM / EINVAL / ECUDA on failure. */
+qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *gates,
+                          const uint64_t *gate_offsets, const uint64_t *param_offsets, qs_dtype dtype,
+                          int small_bits, int tile_bits, int max_pass_gates, void *stream,
+                          qs_batch **out);
+
+/* Run the batch: theta (device, param_offsets[num_states] doubles) -> energy[s] (device,
+ * num_states doubles) and grad (device, param_offsets[num_states] doubles), all in float64.
+ * One persistent kernel: each CTA takes states from a device work queue (largest first;
+ * nothing waits on anything, so no bounded wait is needed). With QS_FLAG_GRAPH the queue
+ * reset and the kernel are recorded once into a CUDA graph (re-recorded when the three
+ * pointers change) and launched as a graph; otherwise they are launched directly.
+ * Asynchronous on the batch's stream. */
+qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double *grad, int flags);
+
+/* Chosen launch configuration and memory of a batch (any pointer may be NULL). */
+qs_status qs_batch_info(const qs_batch *b, int *grid, int *small_bits, int *tile_bits,
+                        int *max_pass_gates, size_t *smem_bytes, size_t *workspace_bytes);
+
+/* Release a batch (synchronises its stream first). NULL is accepted. */
+qs_status qs_batch_free(qs_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

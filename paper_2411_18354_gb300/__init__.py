@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     QS_C64, QS_C128, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_GATE_U,
     QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
-    qs_state_alloc,
+    qs_state_alloc, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run,
     qs_state_copy_from_host, qs_state_copy_to_host, qs_state_free, qs_state_info, qs_state_set_basis,
     qs_state_set_stream, qs_state_wrap,
 )
@@ -113,6 +113,48 @@ class State:
         if a.size != (1 << self.n):
             raise ValueError("wrong number of amplitudes")
         qs_state_copy_from_host(self.h, a)
+
+
+class Batch:
+    """Many independent states (own qubit count, gate list and parameters) whose energies
+    <sum_i Z_i> and adjoint gradients are computed by one persistent, graph-launched kernel."""
+
+    def __init__(self, n_qubits, circuits, n_params, dtype="c64", small_bits=0, tile_bits=0, max_pass_gates=0,
+                 stream: int | None = None):
+        import numpy as _np
+
+        self.dtype = _DT[dtype] if isinstance(dtype, str) else int(dtype)
+        self.n_qubits = _np.asarray(n_qubits, dtype=_np.int32)
+        gl = [as_gate_array(c) for c in circuits]
+        self.gate_offsets = _np.concatenate([[0], _np.cumsum([len(g) for g in gl])]).astype(_np.uint64)
+        self.param_offsets = _np.concatenate([[0], _np.cumsum(n_params)]).astype(_np.uint64)
+        gates = _np.concatenate(gl) if gl else _np.zeros(0, dtype=GATE_DTYPE)
+        self.h = qs_batch_create(self.n_qubits, gates, self.gate_offsets, self.param_offsets, self.dtype,
+                                 small_bits, tile_bits, max_pass_gates,
+                                 _current_stream() if stream is None else stream)
+
+    @property
+    def num_params(self) -> int:
+        return int(self.param_offsets[-1])
+
+    def info(self) -> dict:
+        return qs_batch_info(self.h)
+
+    def run(self, theta, energy, grad, flags: int = QS_FLAG_GRAPH):
+        """theta / energy / grad: torch float64 CUDA tensors (or device addresses)."""
+        addr = lambda t: t if isinstance(t, int) else t.data_ptr()  # noqa: E731
+        qs_batch_run(self.h, addr(theta), addr(energy), addr(grad), flags)
+
+    def close(self):
+        if getattr(self, "h", None):
+            qs_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def build(force: bool = False) -> str:

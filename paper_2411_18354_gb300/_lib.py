@@ -53,6 +53,13 @@ _SIGNATURES = [
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
     ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
+    ("qs_batch_create", ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    ("qs_batch_run", ctypes.c_int, [_vp, _dp, _dp, _dp, ctypes.c_int]),
+    ("qs_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("qs_batch_free", ctypes.c_int, [_vp]),
 ]
 
 _lib = None
@@ -218,3 +225,39 @@ def qs_adjoint_grad(h: int, gates, theta, flags: int = 0, energy_out=None, grad_
     _check(lib().qs_adjoint_grad(_c_state_p(h), gp, g.size, tp, nt, e.ctypes.data_as(_dp),
                                  gr.ctypes.data_as(_dp), flags))
     return float(e[0]), gr[:nt]
+
+
+def qs_batch_create(n_qubits, gates, gate_offsets, param_offsets, dtype: int, small_bits: int = 0, tile_bits: int = 0,
+                    max_pass_gates: int = 0, stream: int = 0) -> int:
+    """Plan a batch (see qs.h). ``gates`` is one concatenated gate array; offsets have
+    len(n_qubits) + 1 entries."""
+    from .gates import as_gate_array
+
+    nq = np.ascontiguousarray(n_qubits, dtype=np.int32)
+    g = as_gate_array(gates)
+    go = np.ascontiguousarray(gate_offsets, dtype=np.uint64)
+    po = np.ascontiguousarray(param_offsets, dtype=np.uint64)
+    if go.size != nq.size + 1 or po.size != nq.size + 1:
+        raise ValueError("offset arrays need len(n_qubits) + 1 entries")
+    h = _vp()
+    _check(lib().qs_batch_create(int(nq.size), _vp(nq.ctypes.data), _vp(g.ctypes.data) if g.size else None,
+                                 _vp(go.ctypes.data), _vp(po.ctypes.data), dtype, small_bits, tile_bits,
+                                 max_pass_gates, _vp(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def qs_batch_run(b: int, theta_dev: int, energy_dev: int, grad_dev: int, flags: int = QS_FLAG_GRAPH) -> None:
+    _check(lib().qs_batch_run(_vp(b), _dptr(theta_dev), _dptr(energy_dev), _dptr(grad_dev), flags))
+
+
+def qs_batch_info(b: int) -> dict:
+    grid, sb, tb, mg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    smem, ws = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().qs_batch_info(_vp(b), ctypes.byref(grid), ctypes.byref(sb), ctypes.byref(tb), ctypes.byref(mg),
+                               ctypes.byref(smem), ctypes.byref(ws)))
+    return {"grid": grid.value, "small_bits": sb.value, "tile_bits": tb.value, "max_pass_gates": mg.value,
+            "smem_bytes": smem.value, "workspace_bytes": ws.value}
+
+
+def qs_batch_free(b: int) -> None:
+    _check(lib().qs_batch_free(_vp(b)))

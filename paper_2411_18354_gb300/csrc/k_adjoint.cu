@@ -29,7 +29,7 @@ k_adj_step(typename CxT<Real>::T *__restrict__ psi, typename CxT<Real>::T *__res
     using T2 = typename CxT<Real>::T;
     constexpr int r = Log2<R>::v;
     constexpr int A = (LAY == LAY_ADJ) ? 2 * R : R;
-    constexpr int DOP = (OP == OP_DIAG) ? OP_DIAG : OP_GEN;  // structure of dU
+    constexpr int DOP = (OP == OP_DIAG) ? OP_DIAG : (OP == OP_REAL) ? OP_REAL : OP_GEN;  // structure of dU
     Real acc = 0;
     const Idx step = (Idx)gridDim.x * kGateThreads;
     for (Idx u = (Idx)blockIdx.x * kGateThreads + threadIdx.x; u < units; u += step) {
@@ -164,7 +164,9 @@ cudaError_t by_shape(void *psi, void *lam, const GatePlan &p, const double *dU, 
     if (param) {                                                                                      \
         if (p.op == OP_GEN) return go<Real, Idx, NS, LAY, R, OP_GEN, true>(psi, lam, p, dU, part, st);   \
         if (p.op == OP_DIAG) return go<Real, Idx, NS, LAY, R, OP_DIAG, true>(psi, lam, p, dU, part, st); \
+        if (p.op == OP_REAL) return go<Real, Idx, NS, LAY, R, OP_REAL, true>(psi, lam, p, dU, part, st); \
     } else {                                                                                          \
+        if (p.op == OP_REAL) return go<Real, Idx, NS, LAY, R, OP_REAL, false>(psi, lam, p, dU, part, st); \
         if (p.op == OP_GEN) return go<Real, Idx, NS, LAY, R, OP_GEN, false>(psi, lam, p, dU, part, st);  \
         if (p.op == OP_DIAG) return go<Real, Idx, NS, LAY, R, OP_DIAG, false>(psi, lam, p, dU, part, st); \
         if (p.op == OP_SWAP) return go<Real, Idx, NS, LAY, R, OP_SWAP, false>(psi, lam, p, dU, part, st); \

@@ -101,6 +101,14 @@ __device__ __forceinline__ void pair_update(T2 &x, T2 &y, const Real *m) {
         T2 ny = cmac<T2, Real>(m[4], m[5], x, m[6], m[7], y);
         x = nx;
         y = ny;
+    } else if (OP == OP_REAL) {
+        T2 nx, ny;
+        nx.x = fma(m[0], x.x, m[2] * y.x);
+        nx.y = fma(m[0], x.y, m[2] * y.y);
+        ny.x = fma(m[4], x.x, m[6] * y.x);
+        ny.y = fma(m[4], x.y, m[6] * y.y);
+        x = nx;
+        y = ny;
     } else if (OP == OP_SWAP) {
         T2 tmp = x;
         x = y;

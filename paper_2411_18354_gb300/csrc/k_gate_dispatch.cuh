@@ -55,6 +55,7 @@ cudaError_t by_shape(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cval
 #define QS_OPS(LAY, R)                                                                        \
     switch (op) {                                                                             \
         case OP_GEN: return go<Real, Idx, NS, LAY, R, OP_GEN, MASKED>(psi, p, cmask, cvals, st); \
+        case OP_REAL: if (!MASKED) return go<Real, Idx, NS, LAY, R, OP_REAL, false>(psi, p, cmask, cvals, st); break; \
         case OP_SWAP: if (!MASKED) return go<Real, Idx, NS, LAY, R, OP_SWAP, false>(psi, p, cmask, cvals, st); break; \
         case OP_DIAG: if (!MASKED) return go<Real, Idx, NS, LAY, R, OP_DIAG, false>(psi, p, cmask, cvals, st); break; \
         case OP_SIDE: if (!MASKED && LAY == LAY_SPLIT) return go<Real, Idx, NS, LAY_SPLIT, R, OP_SIDE, false>(psi, p, cmask, cvals, st); break; \

@@ -31,10 +31,14 @@ struct TileGate {
     int32_t op;               // GateOp
     int32_t side;             // OP_SIDE: which side is scaled
     int32_t slot;             // adjoint: accumulator index inside the pass, -1 if no parameter
+    int32_t pkind;            // batch: QS_GATE_RY / QS_GATE_RZ -> matrices from theta[pidx]; 0 = fixed
+    int32_t pidx;             // batch: parameter index inside the state
     int32_t pad;
     uint64_t hmask, hvals;    // non-local controls: the tile predicate (global bits)
     double U[8];              // forward: U; adjoint: U^dagger
     double D[8];              // adjoint: dU/dtheta (parameterised gates)
+    float Uf[8];              // the same, rounded once to float32 for complex64 states
+    float Df[8];
 };
 
 struct TilePass {

@@ -1,0 +1,370 @@
+// qs_batch.cu -- qs_batch_create / qs_batch_run / qs_batch_free: forward energy and adjoint
+// gradient of many independent states in one persistent launch, recorded in a CUDA graph.
+//
+// Host side: every state's gate list is validated; states with identical (n, gate list) share
+// one program; a program is the forward gate sequence and the reverse sweep, each planned into
+// tile passes (the whole state is one tile when n <= small_bits, otherwise passes of
+// tile_bits local qubits). Parameterised gates keep their parameter index; the kernel builds
+// their matrices from theta. Tuning (small_bits, tile_bits, max_pass_gates) comes from the
+// caller, normally the autotuner; 0 selects the library defaults.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "k_batch.cuh"
+#include "qs_fuse.cuh"
+#include "qs_internal.cuh"
+#include "qs_state.cuh"
+
+namespace qs {
+size_t elem_bytes(int dtype);
+}  // namespace qs
+
+using namespace qs;
+
+namespace {
+constexpr uint32_t kBatchMagic = 0x51534254u;  // "QSBT"
+constexpr int kBatchMaxQubits = 30;
+constexpr int kBatchMaxParams = 4096;
+}  // namespace
+
+struct qs_batch {
+    uint32_t magic = kBatchMagic;
+    qs_dtype dtype = QS_C64;
+    int num_states = 0;
+    uint64_t num_params = 0;
+    cudaStream_t stream = nullptr;
+    BatchArgs args{};
+    int grid = 0;
+    size_t smem = 0;
+    int small_bits = 0, tile_bits = 0, max_pass_gates = 0;
+    // device buffers
+    void *d_states = nullptr, *d_order = nullptr, *d_progs = nullptr, *d_passes = nullptr, *d_gates = nullptr;
+    void *workspace = nullptr;
+    int *queue = nullptr;
+    // graph of (queue reset + kernel) for the last (theta, energy, grad) pointers
+    cudaGraphExec_t exec = nullptr;
+    const double *g_theta = nullptr;
+    double *g_energy = nullptr, *g_grad = nullptr;
+    cudaStream_t capture_stream = nullptr;
+};
+
+namespace {
+
+void free_batch(qs_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (void *p : {b->d_states, b->d_order, b->d_progs, b->d_passes, b->d_gates, b->workspace, (void *)b->queue})
+        if (p) cudaFree(p);
+    b->magic = 0;
+    delete b;
+}
+
+template <typename T>
+qs_status upload(const std::vector<T> &v, void **dst) {
+    const size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return set_error(QS_ENOMEM, "qs_batch_create: device allocation failed");
+    }
+    if (!v.empty()) {
+        e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_batch_create: upload");
+    }
+    return QS_OK;
+}
+
+void dagger8(const double U[8], double D[8]) {
+    D[0] = U[0]; D[1] = -U[1];
+    D[2] = U[4]; D[3] = -U[5];
+    D[4] = U[2]; D[5] = -U[3];
+    D[6] = U[6]; D[7] = -U[7];
+}
+
+// Plans of one gate for the forward program (fwd) and the sweep (adj).
+bool plan_pair(int n, int dtype, const qs_gate &g, int nparam, GatePlan *fwd, GatePlan *adj, char *err, size_t el) {
+    double U[8] = {0}, Ud[8] = {0};
+    if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) {
+        if (g.param < 0 || g.param >= nparam) {
+            std::snprintf(err, el, "parameter index %d outside the state's %d parameters", g.param, nparam);
+            return false;
+        }
+        // placeholder matrices (the kernel builds the real ones from theta); only the structure counts
+        const int op = g.kind == QS_GATE_RY ? OP_REAL : OP_DIAG;
+        U[0] = U[6] = 0.5;
+        if (g.kind == QS_GATE_RY) { U[2] = -0.5; U[4] = 0.5; }
+        dagger8(U, Ud);
+        return plan_gate(n, dtype, g.target, g.ctrl_mask, g.ctrl_vals, U, QS_GATE_U, op, fwd, err, el) &&
+               plan_gate(n, dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, op, adj, err, el);
+    }
+    if (g.kind == QS_GATE_X) {
+        if (!plan_gate(n, dtype, g.target, g.ctrl_mask, g.ctrl_vals, nullptr, QS_GATE_X, -1, fwd, err, el)) return false;
+        *adj = *fwd;
+        return true;
+    }
+    if (g.kind != QS_GATE_U) {
+        std::snprintf(err, el, "unknown gate kind %d", g.kind);
+        return false;
+    }
+    if (!plan_gate(n, dtype, g.target, g.ctrl_mask, g.ctrl_vals, g.U, QS_GATE_U, -1, fwd, err, el)) return false;
+    dagger8(g.U, Ud);
+    if (!plan_gate(n, dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, -1, adj, err, el)) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *gates, const uint64_t *gate_offsets,
+                          const uint64_t *param_offsets, qs_dtype dtype, int small_bits, int tile_bits,
+                          int max_pass_gates, void *stream, qs_batch **out) {
+    if (!out) return set_error(QS_EINVAL, "qs_batch_create: out is NULL");
+    *out = nullptr;
+    if (num_states < 1 || !n_qubits || !gate_offsets || !param_offsets)
+        return set_error(QS_EINVAL, "qs_batch_create: need num_states >= 1 and the size / offset arrays");
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_batch_create: bad dtype");
+    const int es = (int)elem_bytes(dtype);
+    if (small_bits <= 0) small_bits = dtype == QS_C64 ? 12 : 11;
+    if (tile_bits <= 0) tile_bits = dtype == QS_C64 ? 11 : 10;
+    if (max_pass_gates <= 0) max_pass_gates = kTileMaxGates;
+    if (small_bits > kTileMaxBits || tile_bits > kTileMaxBits || tile_bits < 5)
+        return set_error(QS_EINVAL, "qs_batch_create: small_bits / tile_bits out of range (tile_bits 5..14)");
+    if (gate_offsets[0] != 0 || param_offsets[0] != 0) return set_error(QS_EINVAL, "qs_batch_create: offsets must start at 0");
+    if (gate_offsets[num_states] > 0 && !gates) return set_error(QS_EINVAL, "qs_batch_create: gates is NULL");
+
+    std::vector<BatchState> states(num_states);
+    std::vector<BatchProg> progs;
+    std::vector<TilePass> passes;
+    std::vector<TileGate> tgates;
+    std::map<std::string, int> prog_of;
+    int max_params = 1, max_large_n = 0, max_small_n = 0, smem_bits = 5;
+    char err[256], e2[300];
+    for (int s = 0; s < num_states; ++s) {
+        const int n = n_qubits[s];
+        if (n < 1 || n > kBatchMaxQubits) {
+            std::snprintf(e2, sizeof(e2), "qs_batch_create: state %d has n=%d outside [1, %d]", s, n, kBatchMaxQubits);
+            return set_error(QS_EINVAL, e2);
+        }
+        if (gate_offsets[s + 1] < gate_offsets[s] || param_offsets[s + 1] < param_offsets[s])
+            return set_error(QS_EINVAL, "qs_batch_create: offsets must be non-decreasing");
+        const uint64_t np = param_offsets[s + 1] - param_offsets[s];
+        if (np > (uint64_t)kBatchMaxParams) return set_error(QS_EINVAL, "qs_batch_create: more than 4096 parameters in a state");
+        const qs_gate *gs = gates + gate_offsets[s];
+        const size_t gc = gate_offsets[s + 1] - gate_offsets[s];
+        std::string key((const char *)&n, sizeof(n));
+        key.append((const char *)&np, sizeof(np));
+        key.append((const char *)gs, gc * sizeof(qs_gate));
+        auto it = prog_of.find(key);
+        int pid;
+        if (it != prog_of.end()) {
+            pid = it->second;
+        } else {
+            std::vector<GatePlan> fwd(gc), adj(gc);
+            std::vector<const double *> dus(gc, nullptr);
+            std::vector<int> slots(gc, -1);
+            static const double kMarker[8] = {0};
+            for (size_t i = 0; i < gc; ++i) {
+                if (gs[i].reserved != 0) return set_error(QS_EINVAL, "qs_batch_create: reserved field must be 0");
+                if (!plan_pair(n, dtype, gs[i], (int)np, &fwd[i], &adj[i], err, sizeof(err))) {
+                    std::snprintf(e2, sizeof(e2), "qs_batch_create: state %d gate %zu: %s", s, i, err);
+                    return set_error(QS_EINVAL, e2);
+                }
+                if (adj[i].op == OP_SIDE) {  // both sides in the sweep (the sweep never skips a side)
+                    double Ud[8];
+                    dagger8(gs[i].U, Ud);
+                    plan_gate(n, dtype, gs[i].target, gs[i].ctrl_mask, gs[i].ctrl_vals, Ud, QS_GATE_U, OP_DIAG, &adj[i],
+                              err, sizeof(err));
+                }
+                if (gs[i].kind == QS_GATE_RY || gs[i].kind == QS_GATE_RZ) {
+                    dus[i] = kMarker;
+                    slots[i] = gs[i].param;
+                }
+            }
+            const bool small = n <= small_bits;
+            const int k = small ? n : tile_bits;
+            std::vector<int> seq(gc);
+            std::iota(seq.begin(), seq.end(), 0);
+            FusedProgram pf, pa;
+            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false);
+            std::reverse(seq.begin(), seq.end());
+            plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa, max_pass_gates, false);
+            BatchProg bp{};
+            bp.small = small;
+            bp.n = n;
+            for (int dir = 0; dir < 2; ++dir) {
+                FusedProgram &fp = dir ? pa : pf;
+                const int base = (int)tgates.size();
+                for (size_t gi = 0; gi < fp.gates.size(); ++gi) {
+                    TileGate G = fp.gates[gi];
+                    const qs_gate &src = gs[fp.gate_src[gi]];
+                    if (src.kind == QS_GATE_RY || src.kind == QS_GATE_RZ) {
+                        G.pkind = src.kind;
+                        G.pidx = src.param;
+                        G.slot = dir ? src.param : -1;
+                    } else {
+                        G.slot = -1;
+                    }
+                    tgates.push_back(G);
+                }
+                if (dir) bp.adj_begin = (int)passes.size();
+                else bp.fwd_begin = (int)passes.size();
+                for (TilePass P : fp.passes) {
+                    P.gate_begin += base;
+                    passes.push_back(P);
+                }
+                if (dir) bp.adj_count = (int)passes.size() - bp.adj_begin;
+                else bp.fwd_count = (int)passes.size() - bp.fwd_begin;
+            }
+            pid = (int)progs.size();
+            progs.push_back(bp);
+            prog_of.emplace(key, pid);
+        }
+        states[s].n = n;
+        states[s].prog = pid;
+        states[s].nparam = (int32_t)np;
+        states[s].param_off = param_offsets[s];
+        max_params = std::max<int>(max_params, (int)np);
+        if (n <= small_bits) max_small_n = std::max(max_small_n, n);
+        else max_large_n = std::max(max_large_n, n);
+    }
+    smem_bits = std::max(max_small_n, max_large_n > 0 ? std::min(tile_bits, max_large_n) : 0);
+    smem_bits = std::max(smem_bits, 1);
+    std::vector<int32_t> order(num_states);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return states[a].n > states[b].n; });
+
+    const size_t smem = batch_smem_bytes(dtype, smem_bits, max_params);
+    if (smem > 227 * 1024) return set_error(QS_EINVAL, "qs_batch_create: shared memory per CTA would exceed 227 KB");
+    const int grid = batch_grid(dtype, smem);
+    if (grid <= 0) return set_error(QS_ECUDA, "qs_batch_create: no resident CTA for this shared memory size");
+
+    qs_batch *b = new (std::nothrow) qs_batch();
+    if (!b) return set_error(QS_ENOMEM, "qs_batch_create: host allocation failed");
+    b->dtype = dtype;
+    b->num_states = num_states;
+    b->num_params = param_offsets[num_states];
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    b->grid = grid;
+    b->smem = smem;
+    b->small_bits = small_bits;
+    b->tile_bits = tile_bits;
+    b->max_pass_gates = max_pass_gates;
+    qs_status st;
+    if ((st = upload(states, &b->d_states)) != QS_OK || (st = upload(order, &b->d_order)) != QS_OK ||
+        (st = upload(progs, &b->d_progs)) != QS_OK || (st = upload(passes, &b->d_passes)) != QS_OK ||
+        (st = upload(tgates, &b->d_gates)) != QS_OK) {
+        free_batch(b);
+        return st;
+    }
+    const uint64_t ws_stride = max_large_n > 0 ? (1ull << max_large_n) : 0;
+    if (ws_stride) {
+        const size_t bytes = (size_t)grid * 2 * ws_stride * es;
+        cudaError_t e = cudaMalloc(&b->workspace, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b->workspace = nullptr;
+            free_batch(b);
+            return set_error(QS_ENOMEM, "qs_batch_create: cannot allocate the large-state workspace");
+        }
+    }
+    if (cudaMalloc(&b->queue, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        b->queue = nullptr;
+        free_batch(b);
+        return set_error(QS_ENOMEM, "qs_batch_create: cannot allocate the work queue");
+    }
+    BatchArgs &a = b->args;
+    a.states = static_cast<const BatchState *>(b->d_states);
+    a.order = static_cast<const int32_t *>(b->d_order);
+    a.progs = static_cast<const BatchProg *>(b->d_progs);
+    a.passes = static_cast<const TilePass *>(b->d_passes);
+    a.gates = static_cast<const TileGate *>(b->d_gates);
+    a.workspace = b->workspace;
+    a.ws_stride = ws_stride;
+    a.queue = b->queue;
+    a.num_states = num_states;
+    a.smem_bits = smem_bits;
+    a.max_params = max_params;
+    *out = b;
+    return QS_OK;
+}
+
+qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double *grad, int flags) {
+    if (!b || b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_run: batch is NULL or not valid");
+    if (!theta || !energy || (b->num_params > 0 && !grad))
+        return set_error(QS_EINVAL, "qs_batch_run: theta, energy and grad must be device pointers");
+    if (flags & ~QS_FLAG_GRAPH) return set_error(QS_EINVAL, "qs_batch_run: unknown flags");
+    BatchArgs a = b->args;
+    a.theta = theta;
+    a.energy = energy;
+    a.grad = grad;
+    cudaError_t e;
+    if (!(flags & QS_FLAG_GRAPH)) {
+        e = cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess) e = launch_batch(b->dtype, a, b->grid, b->smem, b->stream);
+        return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_batch_run launch");
+    }
+    if (!b->exec || b->g_theta != theta || b->g_energy != energy || b->g_grad != grad) {
+        if (b->exec) {
+            cudaStreamSynchronize(b->stream);
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        if (!b->capture_stream) {
+            e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "qs_batch_run: capture stream");
+        }
+        e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_batch_run: begin capture");
+        cudaError_t e1 = cudaMemsetAsync(b->queue, 0, sizeof(int), b->capture_stream);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_batch(b->dtype, a, b->grid, b->smem, b->capture_stream) : e1;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->capture_stream, &graph);
+        if (e2 != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e2 != cudaSuccess ? e2 : e, "qs_batch_run: capture");
+        }
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return cuda_fail(e, "qs_batch_run: instantiate");
+        }
+        b->g_theta = theta;
+        b->g_energy = energy;
+        b->g_grad = grad;
+    }
+    e = cudaGraphLaunch(b->exec, b->stream);
+    return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_batch_run: graph launch");
+}
+
+qs_status qs_batch_info(const qs_batch *b, int *grid, int *small_bits, int *tile_bits, int *max_pass_gates,
+                        size_t *smem_bytes, size_t *workspace_bytes) {
+    if (!b || b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_info: batch is NULL or not valid");
+    if (grid) *grid = b->grid;
+    if (small_bits) *small_bits = b->small_bits;
+    if (tile_bits) *tile_bits = b->tile_bits;
+    if (max_pass_gates) *max_pass_gates = b->max_pass_gates;
+    if (smem_bytes) *smem_bytes = b->smem;
+    if (workspace_bytes) *workspace_bytes = b->args.ws_stride * 2 * (size_t)b->grid * elem_bytes(b->dtype);
+    return QS_OK;
+}
+
+qs_status qs_batch_free(qs_batch *b) {
+    if (!b) return QS_OK;
+    if (b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_free: batch is not valid");
+    cudaStreamSynchronize(b->stream);
+    free_batch(b);
+    cudaGetLastError();
+    return QS_OK;
+}
+
+}  // extern "C"

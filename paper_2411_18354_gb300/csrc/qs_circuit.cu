@@ -318,7 +318,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
             if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) rot_matrix(g.kind, theta[g.param], U);
             else std::memcpy(U, g.U, sizeof(U));
             dagger(U, Ud);
-            if (g.kind == QS_GATE_RY) force = OP_GEN;
+            if (g.kind == QS_GATE_RY) force = OP_REAL;
             else if (g.kind == QS_GATE_RZ) force = OP_DIAG;
         }
         if (!plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, force, &adj[i], e2,

@@ -62,6 +62,7 @@ static void make_tile_gate(const GatePlan &p, uint64_t Lmask, int k, const int *
     G->side = p.side;
     G->slot = -1;
     std::memcpy(G->U, p.U, sizeof(G->U));
+    for (int i = 0; i < 8; ++i) G->Uf[i] = (float)p.U[i];
 }
 
 static void make_pass(int n, uint64_t Lmask, TilePass *P) {
@@ -97,12 +98,17 @@ static void make_pass(int n, uint64_t Lmask, TilePass *P) {
 }
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
-                const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog) {
+                const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
+                int max_gates, bool allow_single) {
     prog->ops.clear();
     prog->passes.clear();
     prog->gates.clear();
-    k = std::min(std::min(k, kTileMaxBits), n);
-    const int b = std::min(k, dtype == QS_C64 ? 4 : 3);
+    prog->gate_src.clear();
+    max_gates = std::max(1, std::min(max_gates, kTileMaxGates));
+    // k >= b0 + 1 so that any single target fits next to the b0 low qubits (n permitting)
+    const int b0 = dtype == QS_C64 ? 4 : 3;
+    k = std::min(std::min(std::max(k, b0 + 1), kTileMaxBits), n);
+    const int b = std::min(k, b0);
     const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
     const bool adjoint = dus != nullptr;
     size_t i = 0;
@@ -112,7 +118,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         int nparam = 0;
         std::vector<int> members;
         size_t j = i;
-        while (j < seq.size() && (int)members.size() < kTileMaxGates) {
+        while (j < seq.size() && (int)members.size() < max_gates) {
             const GatePlan &p = plans[seq[j]];
             const bool param = adjoint && (*dus)[seq[j]] != nullptr;
             if (p.units == 0 && !param) {  // identity: nothing to apply
@@ -136,7 +142,11 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         }
         int real = 0;
         for (int mbr : members) real += mbr >= 0;
-        if (real < 2) {  // not worth a pass: the first gate runs alone
+        if (real == 0) {  // only identity gates (j > i here: the first real gate always fits)
+            i = std::max(j, i + 1);
+            continue;
+        }
+        if (real < 2 && allow_single) {  // not worth a pass: the first gate runs alone
             const int g = seq[i];
             const bool param = adjoint && (*dus)[g] != nullptr;
             if (plans[g].units != 0 || param) prog->ops.push_back({-1, g});
@@ -155,12 +165,14 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             TileGate G;
             make_tile_gate(plans[mbr], L, P.k, local_of, &G);
             if (adjoint && (*dus)[mbr]) {
-                if (G.op != OP_GEN && G.op != OP_DIAG) G.op = OP_GEN;
+                if (G.op != OP_GEN && G.op != OP_DIAG && G.op != OP_REAL) G.op = OP_GEN;
                 std::memcpy(G.D, (*dus)[mbr], sizeof(G.D));
+                for (int q = 0; q < 8; ++q) G.Df[q] = (float)G.D[q];
                 G.slot = P.nparam;
                 P.param_gslot[P.nparam++] = (*gslots)[mbr];
             }
             prog->gates.push_back(G);
+            prog->gate_src.push_back(mbr);
         }
         P.gate_count = (int)prog->gates.size() - P.gate_begin;
         prog->ops.push_back({(int)prog->passes.size(), -1});

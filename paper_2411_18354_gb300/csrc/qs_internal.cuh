@@ -21,6 +21,7 @@ enum GateOp : int {
     OP_SWAP = 1,  // (x, y) -> (y, x), no arithmetic
     OP_DIAG = 2,  // (x, y) -> (a x, d y)
     OP_SIDE = 3,  // one side only: z -> s z on the amplitudes whose bit t equals `side`
+    OP_REAL = 4,  // general 2x2 with real entries (e.g. RY, H): half the multiplications
 };
 
 // Layout classes of one work unit (see k_gate.cu).

@@ -137,6 +137,8 @@ bool plan_gate(int n, int dtype, int target, uint64_t ctrl_mask, uint64_t ctrl_v
             }
         } else if (is_zero(a) && is_zero(d) && is_one(b) && is_one(c)) {
             p->op = OP_SWAP;
+        } else if (U[1] == 0.0 && U[3] == 0.0 && U[5] == 0.0 && U[7] == 0.0) {
+            p->op = OP_REAL;
         } else {
             p->op = OP_GEN;
         }
