@@ -148,6 +148,14 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
                            const double *theta, size_t n_theta, int flags);
 
+/* Tile size of the fused passes (QS_FLAG_FUSE) for one precision, forward (adjoint = 0) or
+ * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, 5..14, or 0 for the
+ * library default (complex64: 12; complex128: 11 forward, 10 adjoint). Process-wide; normally
+ * set from the autotuner's cache. The QS_TILE_BITS environment variable overrides it. */
+qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits);
+/* The tile size the next fused call will use. */
+int qs_get_tile_bits(qs_dtype dtype, int adjoint);
+
 /* ------------------------------------------------------------------------------------ */
 /* Reductions (double-precision accumulation on the device)                             */
 /* ------------------------------------------------------------------------------------ */

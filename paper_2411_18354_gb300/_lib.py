@@ -60,6 +60,8 @@ _SIGNATURES = [
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     ("qs_batch_free", ctypes.c_int, [_vp]),
+    ("qs_set_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("qs_get_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
 ]
 
 _lib = None
@@ -261,3 +263,11 @@ def qs_batch_info(b: int) -> dict:
 
 def qs_batch_free(b: int) -> None:
     _check(lib().qs_batch_free(_vp(b)))
+
+
+def qs_set_tile_bits(dtype: int, adjoint: int, bits: int) -> None:
+    _check(lib().qs_set_tile_bits(dtype, adjoint, bits))
+
+
+def qs_get_tile_bits(dtype: int, adjoint: int) -> int:
+    return int(lib().qs_get_tile_bits(dtype, adjoint))

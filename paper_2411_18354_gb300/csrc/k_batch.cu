@@ -36,22 +36,23 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // lambda = O psi and E = <psi|O|psi> over amplitudes [0, N) of `src`, written to `dst`
-// (both in shared or both in global memory). Partial sums: float over runs of at most 32
-// amplitudes per thread, float64 above.
+// (both in shared memory with the tile swizzle `sw`, or both in global memory, sw = 0).
+// Partial sums: float over runs of at most 32 amplitudes per thread, float64 above.
 template <typename Real>
 __device__ __forceinline__ double obs_pass(const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst, int n,
-                                           double *red) {
+                                           double *red, int sw) {
     const uint64_t N = 1ull << n;
     double acc = 0.0;
     Real run = 0;
     int cnt = 0;
     for (uint64_t k = threadIdx.x; k < N; k += blockDim.x) {
         const Real w = (Real)(n - 2 * __popcll(k));
-        typename TileT<Real>::T2 v = src[k];
+        const uint64_t pos = sw ? tile_swizzle((uint32_t)k, sw) : k;
+        typename TileT<Real>::T2 v = src[pos];
         run += w * (v.x * v.x + v.y * v.y);
         v.x *= w;
         v.y *= w;
-        dst[k] = v;
+        dst[pos] = v;
         if (++cnt == 32) {
             acc += (double)run;
             run = 0;
@@ -66,39 +67,33 @@ template <typename Real>
 __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool adjoint, typename TileT<Real>::T2 *psi,
                                    typename TileT<Real>::T2 *lam, typename TileT<Real>::T2 *tp,
                                    typename TileT<Real>::T2 *tl, const Real *cs, double *gacc) {
-    using V = typename TileT<Real>::V;
-    constexpr int VEC = TileT<Real>::VEC;
     const int begin = adjoint ? pg.adj_begin : pg.fwd_begin;
     const int count = adjoint ? pg.adj_count : pg.fwd_count;
     for (int pi = begin; pi < begin + count; ++pi) {
         const TilePass &P = a.passes[pi];
-        const TileGate *G0 = a.gates + P.gate_begin;
-        const uint32_t nvec = (1u << P.k) / VEC;
+        const RegGate *G0 = a.gates + P.gate_begin;
         for (uint64_t tau = 0; tau < P.ntiles; ++tau) {
             const uint64_t base = tile_base(P, tau);
             bool any = false;
             for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
             if (!any) continue;
-            for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-                const uint64_t gi = base | scatter_local(P, v * VEC);
-                reinterpret_cast<V *>(tp)[v] = *reinterpret_cast<const V *>(psi + gi);
-                if (adjoint) reinterpret_cast<V *>(tl)[v] = *reinterpret_cast<const V *>(lam + gi);
-            }
+            load_tile<Real>(P, base, psi, tp);
+            if (adjoint) load_tile<Real>(P, base, lam, tl);
             __syncthreads();
-            if (adjoint) apply_gates<Real, true>(tp, tl, base, G0, P.gate_count, cs, gacc);
-            else apply_gates<Real, false>(tp, nullptr, base, G0, P.gate_count, cs, nullptr);
-            for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-                const uint64_t gi = base | scatter_local(P, v * VEC);
-                *reinterpret_cast<V *>(psi + gi) = reinterpret_cast<const V *>(tp)[v];
-                if (adjoint) *reinterpret_cast<V *>(lam + gi) = reinterpret_cast<const V *>(tl)[v];
-            }
+            if (adjoint)
+                apply_groups<Real, true>(tp, tl, base, P.k, a.groups + P.group_begin, P.group_count, a.gates, cs, gacc);
+            else
+                apply_groups<Real, false>(tp, nullptr, base, P.k, a.groups + P.group_begin, P.group_count, a.gates, cs,
+                                          nullptr);
+            store_tile<Real>(P, base, tp, psi);
+            if (adjoint) store_tile<Real>(P, base, tl, lam);
             __syncthreads();
         }
     }
 }
 
 template <typename Real>
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_batch(const BatchArgs a) {
     using T2 = typename TileT<Real>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t T = 1u << a.smem_bits;
@@ -131,23 +126,25 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchArgs a) {
         double energy;
         if (pg.small) {
             const uint32_t N = 1u << n;
+            // |0...0>: element 0 sits at swizzled position 0, every other element is 0
             for (uint32_t k = tid; k < N; k += kBatchThreads) tp[k] = T2{(Real)(k == 0), (Real)0};
             __syncthreads();
             for (int pi = pg.fwd_begin; pi < pg.fwd_begin + pg.fwd_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                apply_gates<Real, false>(tp, nullptr, 0, a.gates + P.gate_begin, P.gate_count, cs, nullptr);
+                apply_groups<Real, false>(tp, nullptr, 0, n, a.groups + P.group_begin, P.group_count, a.gates, cs,
+                                          nullptr);
             }
-            energy = obs_pass<Real>(tp, tl, n, red);
+            energy = obs_pass<Real>(tp, tl, n, red, TileT<Real>::SW);
             for (int pi = pg.adj_begin; pi < pg.adj_begin + pg.adj_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                apply_gates<Real, true>(tp, tl, 0, a.gates + P.gate_begin, P.gate_count, cs, gacc);
+                apply_groups<Real, true>(tp, tl, 0, n, a.groups + P.group_begin, P.group_count, a.gates, cs, gacc);
             }
         } else {
             const uint64_t N = 1ull << n;
             for (uint64_t k = tid; k < N; k += kBatchThreads) ws_psi[k] = T2{(Real)(k == 0), (Real)0};
             __syncthreads();
             run_program_global<Real>(a, pg, false, ws_psi, ws_lam, tp, tl, cs, nullptr);
-            energy = obs_pass<Real>(ws_psi, ws_lam, n, red);
+            energy = obs_pass<Real>(ws_psi, ws_lam, n, red, 0);
             run_program_global<Real>(a, pg, true, ws_psi, ws_lam, tp, tl, cs, gacc);
         }
         __syncthreads();

@@ -27,7 +27,8 @@ struct BatchArgs {
     const int32_t *order;   // queue position -> state index (largest first)
     const BatchProg *progs;
     const TilePass *passes;
-    const TileGate *gates;
+    const TileGroup *groups;
+    const RegGate *gates;
     const double *theta;
     double *energy;
     double *grad;

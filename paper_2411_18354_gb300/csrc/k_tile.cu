@@ -9,12 +9,11 @@ namespace {
 using namespace tiledev;
 
 template <typename Real, bool ADJ>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, (ADJ && sizeof(Real) == 8) ? 1 : 2)
 k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2 *__restrict__ lam, const TilePass P,
-            const TileGate *__restrict__ gates, double *__restrict__ part, size_t part_stride) {
+            const TileGroup *__restrict__ groups, const RegGate *__restrict__ gates, double *__restrict__ part,
+            size_t part_stride) {
     using T2 = typename TileT<Real>::T2;
-    using V = typename TileT<Real>::V;
-    constexpr int VEC = TileT<Real>::VEC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const uint32_t T = 1u << P.k;
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
@@ -25,25 +24,18 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
         for (int i = tid; i < kTileMaxParam * (kTileThreads / 32); i += kTileThreads) acc[i] = 0.0;
         __syncthreads();
     }
-    const TileGate *G0 = gates + P.gate_begin;
-    const uint32_t nvec = T / VEC;
+    const RegGate *G0 = gates + P.gate_begin;
     for (uint64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
         const uint64_t base = tile_base(P, tau);
         bool any = false;
         for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
         if (!any) continue;  // no gate of the pass selects this tile
-        for (uint32_t v = tid; v < nvec; v += kTileThreads) {
-            const uint64_t gi = base | scatter_local(P, v * VEC);
-            reinterpret_cast<V *>(tp)[v] = *reinterpret_cast<const V *>(psi + gi);
-            if (ADJ) reinterpret_cast<V *>(tl)[v] = *reinterpret_cast<const V *>(lam + gi);
-        }
+        load_tile<Real>(P, base, psi, tp);
+        if (ADJ) load_tile<Real>(P, base, lam, tl);
         __syncthreads();
-        apply_gates<Real, ADJ>(tp, tl, base, G0, P.gate_count, nullptr, acc);
-        for (uint32_t v = tid; v < nvec; v += kTileThreads) {
-            const uint64_t gi = base | scatter_local(P, v * VEC);
-            *reinterpret_cast<V *>(psi + gi) = reinterpret_cast<const V *>(tp)[v];
-            if (ADJ) *reinterpret_cast<V *>(lam + gi) = reinterpret_cast<const V *>(tl)[v];
-        }
+        apply_groups<Real, ADJ>(tp, tl, base, P.k, groups + P.group_begin, P.group_count, gates, nullptr, acc);
+        store_tile<Real>(P, base, tp, psi);
+        if (ADJ) store_tile<Real>(P, base, tl, lam);
         __syncthreads();
     }
     if (ADJ) {
@@ -57,8 +49,8 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
 }
 
 template <typename Real, bool ADJ>
-cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGate *gates, double *part, size_t part_stride,
-               cudaStream_t st) {
+cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGroup *groups, const RegGate *gates, double *part,
+               size_t part_stride, cudaStream_t st) {
     auto kern = k_tile_pass<Real, ADJ>;
     const size_t smem = tile_smem_bytes(sizeof(Real) == 4 ? QS_C64 : QS_C128, p.k, ADJ);
     static size_t configured = 0;
@@ -73,8 +65,8 @@ cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGate *gates, d
     if (ADJ) cap = std::min<uint64_t>(cap, part_stride);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(p.ntiles, cap));
     using T2 = typename TileT<Real>::T2;
-    kern<<<grid, kTileThreads, smem, st>>>(reinterpret_cast<T2 *>(psi), reinterpret_cast<T2 *>(lam), p, gates, part,
-                                           part_stride);
+    kern<<<grid, kTileThreads, smem, st>>>(reinterpret_cast<T2 *>(psi), reinterpret_cast<T2 *>(lam), p, groups, gates,
+                                           part, part_stride);
     return cudaGetLastError();
 }
 
@@ -85,14 +77,14 @@ size_t tile_smem_bytes(int dtype, int k, bool adjoint) {
     return (adjoint ? 2 : 1) * (size_t(1) << k) * es + (adjoint ? kTileMaxParam * (kTileThreads / 32) * sizeof(double) : 0);
 }
 
-cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGate *gates, double *part,
-                             size_t part_stride, cudaStream_t st) {
+cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,
+                             const RegGate *gates, double *part, size_t part_stride, cudaStream_t st) {
     const bool adj = lam != nullptr;
     if (dtype == QS_C64)
-        return adj ? go<float, true>(psi, lam, p, gates, part, part_stride, st)
-                   : go<float, false>(psi, lam, p, gates, part, part_stride, st);
-    return adj ? go<double, true>(psi, lam, p, gates, part, part_stride, st)
-               : go<double, false>(psi, lam, p, gates, part, part_stride, st);
+        return adj ? go<float, true>(psi, lam, p, groups, gates, part, part_stride, st)
+                   : go<float, false>(psi, lam, p, groups, gates, part, part_stride, st);
+    return adj ? go<double, true>(psi, lam, p, groups, gates, part, part_stride, st)
+               : go<double, false>(psi, lam, p, groups, gates, part, part_stride, st);
 }
 
 }  // namespace qs

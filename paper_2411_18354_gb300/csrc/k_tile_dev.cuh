@@ -1,6 +1,6 @@
 // k_tile_dev.cuh -- device code shared by the fused tile pass and the batched kernel:
-// applying a list of TileGates to one shared-memory tile (and, for the adjoint sweep, to the
-// matching lambda tile with the gradient inner products).
+// applying register groups of gates to one shared-memory tile (and, for the adjoint sweep,
+// to the matching lambda tile, with the gradient inner products).
 #pragma once
 
 #include "k_gate.cuh"
@@ -12,25 +12,25 @@ namespace tiledev {
 template <typename Real> struct TileT;
 template <> struct TileT<float> {
     using T2 = float2;
-    using V = float4;  // 2 amplitudes per 16-byte vector
+    using V = float4;  // 2 amplitudes per 16-byte global vector
     static constexpr int VEC = 2;
-    __device__ static const float *U(const TileGate &G) { return G.Uf; }
-    __device__ static const float *D(const TileGate &G) { return G.Df; }
+    static constexpr int SW = 4;  // 16 amplitudes of 8 bytes per 128-byte bank row
+    __device__ static const float *U(const RegGate &G) { return G.Uf; }
+    __device__ static const float *D(const RegGate &G) { return G.Df; }
 };
 template <> struct TileT<double> {
     using T2 = double2;
-    using V = double2;  // 1 amplitude per 16-byte vector
+    using V = double2;
     static constexpr int VEC = 1;
-    __device__ static const double *U(const TileGate &G) { return G.U; }
-    __device__ static const double *D(const TileGate &G) { return G.D; }
+    static constexpr int SW = 3;  // 8 amplitudes of 16 bytes per bank row
+    __device__ static const double *U(const RegGate &G) { return G.U; }
+    __device__ static const double *D(const RegGate &G) { return G.D; }
 };
 
-// Gate fields a thread keeps in registers while it works through the gate's pairs.
+// Gate fields kept in registers while a row is processed.
 template <typename Real> struct GateRegs {
-    uint32_t mask[4];
-    uint32_t shift[4];
-    uint32_t ins, tbit, pairs;
-    int nseg, op, side, slot;
+    uint32_t crm, crv;
+    int p, cqm, cqv, op, side, slot;
     Real u[8], d[8];
 };
 
@@ -68,16 +68,12 @@ __device__ __forceinline__ void param_matrices(int kind, Real c, Real s, bool ad
 }
 
 template <typename Real>
-__device__ __forceinline__ void load_gate(const TileGate &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
-    r.nseg = G.nseg;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        r.mask[s] = s < r.nseg ? G.mask[s] : 0u;
-        r.shift[s] = s < r.nseg ? G.shift[s] : 0u;
-    }
-    r.ins = G.ins;
-    r.tbit = G.tbit;
-    r.pairs = 1u << G.log_pairs;
+__device__ __forceinline__ void load_gate(const RegGate &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
+    r.crm = G.crm;
+    r.crv = G.crv;
+    r.p = G.p;
+    r.cqm = G.cqm;
+    r.cqv = G.cqv;
     r.op = G.op;
     r.side = G.side;
     r.slot = G.slot;
@@ -94,16 +90,6 @@ __device__ __forceinline__ void load_gate(const TileGate &G, GateRegs<Real> &r, 
     }
 }
 
-// Local pair index: up to 4 counter segments from registers, the rest from the table.
-template <typename Real>
-__device__ __forceinline__ uint32_t local_pair(const GateRegs<Real> &r, const TileGate &G, uint32_t j) {
-    uint32_t lo = r.ins;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) lo |= (j << r.shift[s]) & r.mask[s];
-    for (int s = 4; s < r.nseg; ++s) lo |= (j << G.shift[s]) & G.mask[s];
-    return lo;
-}
-
 __device__ __forceinline__ uint64_t tile_base(const TilePass &P, uint64_t tau) {
     uint64_t b = 0;
     for (int s = 0; s < P.tnseg; ++s) b |= (tau << P.tshift[s]) & P.tmask[s];
@@ -117,68 +103,168 @@ __device__ __forceinline__ uint64_t scatter_local(const TilePass &P, uint32_t o)
     return g;
 }
 
-template <typename T2, typename Real>
-__device__ __forceinline__ void apply_pair(int op, int side, const Real *u, T2 &x, T2 &y) {
-    if (op == OP_GEN) {
-        T2 nx = cmac<T2, Real>(u[0], u[1], x, u[2], u[3], y);
-        T2 ny = cmac<T2, Real>(u[4], u[5], x, u[6], u[7], y);
-        x = nx;
-        y = ny;
-    } else if (op == OP_REAL) {
-        pair_update<OP_REAL, T2, Real>(x, y, u);
-    } else if (op == OP_SWAP) {
-        T2 t = x;
-        x = y;
-        y = t;
-    } else if (op == OP_DIAG) {
-        x = cmul<T2, Real>(u[0], u[1], x);
-        y = cmul<T2, Real>(u[6], u[7], y);
-    } else {  // OP_SIDE: scalar in u[0..1]
+template <int OP, typename T2, typename Real>
+__device__ __forceinline__ void op_pair(T2 &x, T2 &y, const Real *u, int side) {
+    if (OP == OP_SIDE) {
         if (side) y = cmul<T2, Real>(u[0], u[1], y);
         else x = cmul<T2, Real>(u[0], u[1], x);
+    } else {
+        pair_update<OP, T2, Real>(x, y, u);
     }
 }
 
-// Apply gates G0[0..count) to the tile tp (and, if ADJ, the lambda tile tl) whose global base
-// index is `base`. Adjoint: for a gate with slot >= 0, the warp partial of Re <lambda|dU psi>
-// is added to acc[slot * nwarps + warp] (float64). Ends with a block barrier.
-template <typename Real, bool ADJ>
-__device__ __forceinline__ void apply_gates(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
-                                            const TileGate *G0, int count, const Real *cs, double *acc) {
-    using T2 = typename TileT<Real>::T2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    for (int g = 0; g < count; ++g) {
-        const TileGate &G = G0[g];
-        if ((base & G.hmask) != G.hvals) continue;  // uniform over the block
-        GateRegs<Real> R;
-        load_gate<Real>(G, R, cs, ADJ);
-        const int dop = R.op == OP_DIAG ? OP_DIAG : R.op == OP_REAL ? OP_REAL : OP_GEN;
-        Real dot = 0;
-        for (uint32_t j = tid; j < R.pairs; j += blockDim.x) {
-            const uint32_t lo = local_pair<Real>(R, G, j), hi = lo | R.tbit;
-            T2 x = tp[lo], y = tp[hi];
-            apply_pair<T2, Real>(R.op, R.side, R.u, x, y);
-            tp[lo] = x;
-            tp[hi] = y;
+// All pairs (e, e | 2^P) of one row for one gate with operation OP.
+template <int P, int OP, bool ADJ, int GB, typename T2, typename Real>
+__device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+    constexpr int DOP = OP == OP_DIAG ? OP_DIAG : (OP == OP_REAL ? OP_REAL : OP_GEN);
+#pragma unroll
+    for (int e = 0; e < (1 << GB); ++e) {
+        if ((e >> P) & 1) continue;
+        const int e2 = e | (1 << P);
+        const bool ok = row_ok && ((e & R.cqm) == R.cqv) && (e2 < (1 << r));
+        if (ok) {
+            op_pair<OP, T2, Real>(v[e], v[e2], R.u, R.side);
             if (ADJ) {
-                T2 a = tl[lo], b = tl[hi];
                 if (R.slot >= 0) {
-                    T2 mx = x, my = y;
-                    apply_pair<T2, Real>(dop, 0, R.d, mx, my);
-                    dot += a.x * mx.x + a.y * mx.y + b.x * my.x + b.y * my.y;
+                    T2 mx = v[e], my = v[e2];
+                    pair_update<DOP, T2, Real>(mx, my, R.d);
+                    dot += w[e].x * mx.x + w[e].y * mx.y + w[e2].x * my.x + w[e2].y * my.y;
                 }
-                apply_pair<T2, Real>(R.op, R.side, R.u, a, b);
-                tl[lo] = a;
-                tl[hi] = b;
+                op_pair<OP, T2, Real>(w[e], w[e2], R.u, R.side);
             }
         }
-        if (ADJ && R.slot >= 0) {
-            double d = (double)dot;
+    }
+}
+
+template <int OP, bool ADJ, int GB, typename T2, typename Real>
+__device__ __forceinline__ void row_gate_op(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+    switch (R.p) {
+        case 0: row_pairs<0, OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case 1: if (GB > 1) row_pairs<(GB > 1 ? 1 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case 2: if (GB > 2) row_pairs<(GB > 2 ? 2 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        default: if (GB > 3) row_pairs<(GB > 3 ? 3 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+    }
+}
+
+template <bool ADJ, int GB, typename T2, typename Real>
+__device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+    switch (R.op) {
+        case OP_GEN: row_gate_op<OP_GEN, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case OP_REAL: row_gate_op<OP_REAL, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case OP_DIAG: row_gate_op<OP_DIAG, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case OP_SWAP: row_gate_op<OP_SWAP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        default: row_gate_op<OP_SIDE, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+    }
+}
+
+// Register qubits per group: 4 for forward passes, 3 for the adjoint sweep (psi and lambda
+// rows both live in registers there).
+template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
+
+// Apply the pass's register groups to the tile tp (and lambda tile tl if ADJ) whose global
+// base index is `base`. Adjoint: for a gate with slot >= 0 the warp partial of
+// Re <lambda| dU psi> is added to acc[slot * nwarps + warp] (float64). Every executed group
+// ends with a block barrier.
+template <typename Real, bool ADJ>
+__device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
+                                             int k, const TileGroup *groups, int group_count, const RegGate *gates,
+                                             const Real *cs, double *acc) {
+    using T2 = typename TileT<Real>::T2;
+    constexpr int SW = TileT<Real>::SW;
+    constexpr int GB = GroupBits<ADJ>::v;
+    constexpr int E = 1 << GB;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int gi = 0; gi < group_count; ++gi) {
+        const TileGroup &Gr = groups[gi];
+        bool any = false;
+        for (int g = 0; g < Gr.gate_count; ++g)
+            any |= (base & gates[Gr.gate_begin + g].hmask) == gates[Gr.gate_begin + g].hvals;
+        if (!any) continue;  // uniform: nothing of this group touches the tile
+        const int r = Gr.r;
+        uint32_t qb[4];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            if (lane == 0) acc[R.slot * nwarps + warp] += d;
+        for (int i = 0; i < 4; ++i) qb[i] = i < r ? (1u << Gr.q[i]) : 0u;
+        const uint32_t rows = 1u << (k - r);
+        for (uint32_t rb = 0; rb < rows; rb += blockDim.x) {
+            const uint32_t rho = rb + tid;
+            const bool active = rho < rows;
+            uint32_t ra = 0;
+            for (int s = 0; s < Gr.nrseg; ++s) ra |= (rho << Gr.rshift[s]) & Gr.rmask[s];
+            T2 v[E], w[ADJ ? E : 1];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint32_t a = ra | ((e & 1) ? qb[0] : 0u) | ((e & 2) ? qb[1] : 0u) | ((e & 4) ? qb[2] : 0u) |
+                                   ((e & 8) ? qb[3] : 0u);
+                if (active && e < (1 << r)) {
+                    const uint32_t s = tile_swizzle(a, SW);
+                    v[e] = tp[s];
+                    if (ADJ) w[e] = tl[s];
+                } else {
+                    v[e] = T2{0, 0};
+                    if (ADJ) w[e] = T2{0, 0};
+                }
+            }
+            for (int g = 0; g < Gr.gate_count; ++g) {
+                const RegGate &G = gates[Gr.gate_begin + g];
+                if ((base & G.hmask) != G.hvals) continue;  // uniform
+                GateRegs<Real> R;
+                load_gate<Real>(G, R, cs, ADJ);
+                const bool row_ok = active && ((ra & R.crm) == R.crv);
+                Real dot = 0;
+                row_gate<ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot);
+                if (ADJ && R.slot >= 0) {
+                    double d = (double)dot;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    if (lane == 0) acc[R.slot * nwarps + warp] += d;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint32_t a = ra | ((e & 1) ? qb[0] : 0u) | ((e & 2) ? qb[1] : 0u) | ((e & 4) ? qb[2] : 0u) |
+                                   ((e & 8) ? qb[3] : 0u);
+                if (active && e < (1 << r)) {
+                    const uint32_t s = tile_swizzle(a, SW);
+                    tp[s] = v[e];
+                    if (ADJ) tl[s] = w[e];
+                }
+            }
         }
         __syncthreads();
+    }
+}
+
+// Global <-> shared copies of one tile (swizzled in shared memory).
+template <typename Real>
+__device__ __forceinline__ void load_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
+                                          typename TileT<Real>::T2 *dst) {
+    using V = typename TileT<Real>::V;
+    using T2 = typename TileT<Real>::T2;
+    constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
+    const uint32_t nvec = (1u << P.k) / VEC;
+    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+        const uint32_t o = v * VEC;
+        const V x = *reinterpret_cast<const V *>(src + (base | scatter_local(P, o)));
+        const T2 *xs = reinterpret_cast<const T2 *>(&x);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) dst[tile_swizzle(o + i, SW)] = xs[i];
+    }
+}
+
+template <typename Real>
+__device__ __forceinline__ void store_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
+                                           typename TileT<Real>::T2 *dst) {
+    using V = typename TileT<Real>::V;
+    using T2 = typename TileT<Real>::T2;
+    constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
+    const uint32_t nvec = (1u << P.k) / VEC;
+    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+        const uint32_t o = v * VEC;
+        V x;
+        T2 *xs = reinterpret_cast<T2 *>(&x);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) xs[i] = src[tile_swizzle(o + i, SW)];
+        *reinterpret_cast<V *>(dst + (base | scatter_local(P, o))) = x;
     }
 }
 

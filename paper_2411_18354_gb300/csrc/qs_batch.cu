@@ -45,6 +45,7 @@ struct qs_batch {
     int small_bits = 0, tile_bits = 0, max_pass_gates = 0;
     // device buffers
     void *d_states = nullptr, *d_order = nullptr, *d_progs = nullptr, *d_passes = nullptr, *d_gates = nullptr;
+    void *d_groups = nullptr;
     void *workspace = nullptr;
     int *queue = nullptr;
     // graph of (queue reset + kernel) for the last (theta, energy, grad) pointers
@@ -59,7 +60,8 @@ namespace {
 void free_batch(qs_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-    for (void *p : {b->d_states, b->d_order, b->d_progs, b->d_passes, b->d_gates, b->workspace, (void *)b->queue})
+    for (void *p : {b->d_states, b->d_order, b->d_progs, b->d_passes, b->d_gates, b->d_groups, b->workspace,
+                    (void *)b->queue})
         if (p) cudaFree(p);
     b->magic = 0;
     delete b;
@@ -143,10 +145,11 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     std::vector<BatchState> states(num_states);
     std::vector<BatchProg> progs;
     std::vector<TilePass> passes;
-    std::vector<TileGate> tgates;
+    std::vector<RegGate> tgates;
+    std::vector<TileGroup> tgroups;
     std::map<std::string, int> prog_of;
     int max_params = 1, max_large_n = 0, max_small_n = 0, smem_bits = 5;
-    char err[256], e2[300];
+    char err[256], e2[512];
     for (int s = 0; s < num_states; ++s) {
         const int n = n_qubits[s];
         if (n < 1 || n > kBatchMaxQubits) {
@@ -202,8 +205,13 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
             for (int dir = 0; dir < 2; ++dir) {
                 FusedProgram &fp = dir ? pa : pf;
                 const int base = (int)tgates.size();
+                const int gbase = (int)tgroups.size();
+                for (TileGroup Gr : fp.groups) {
+                    Gr.gate_begin += base;
+                    tgroups.push_back(Gr);
+                }
                 for (size_t gi = 0; gi < fp.gates.size(); ++gi) {
-                    TileGate G = fp.gates[gi];
+                    RegGate G = fp.gates[gi];
                     const qs_gate &src = gs[fp.gate_src[gi]];
                     if (src.kind == QS_GATE_RY || src.kind == QS_GATE_RZ) {
                         G.pkind = src.kind;
@@ -218,6 +226,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
                 else bp.fwd_begin = (int)passes.size();
                 for (TilePass P : fp.passes) {
                     P.gate_begin += base;
+                    P.group_begin += gbase;
                     passes.push_back(P);
                 }
                 if (dir) bp.adj_count = (int)passes.size() - bp.adj_begin;
@@ -260,7 +269,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     qs_status st;
     if ((st = upload(states, &b->d_states)) != QS_OK || (st = upload(order, &b->d_order)) != QS_OK ||
         (st = upload(progs, &b->d_progs)) != QS_OK || (st = upload(passes, &b->d_passes)) != QS_OK ||
-        (st = upload(tgates, &b->d_gates)) != QS_OK) {
+        (st = upload(tgates, &b->d_gates)) != QS_OK || (st = upload(tgroups, &b->d_groups)) != QS_OK) {
         free_batch(b);
         return st;
     }
@@ -286,7 +295,8 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     a.order = static_cast<const int32_t *>(b->d_order);
     a.progs = static_cast<const BatchProg *>(b->d_progs);
     a.passes = static_cast<const TilePass *>(b->d_passes);
-    a.gates = static_cast<const TileGate *>(b->d_gates);
+    a.gates = static_cast<const RegGate *>(b->d_gates);
+    a.groups = static_cast<const TileGroup *>(b->d_groups);
     a.workspace = b->workspace;
     a.ws_stride = ws_stride;
     a.queue = b->queue;

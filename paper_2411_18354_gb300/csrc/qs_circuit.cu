@@ -2,6 +2,7 @@
 // up front, launched per gate (or per fused tile pass) on the state's stream, optionally
 // recorded once into a CUDA graph and replayed.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -128,16 +129,21 @@ static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, c
     return QS_OK;
 }
 
+// Tuned tile sizes per (dtype, adjoint), set by qs_set_tile_bits (0 = default).
+static std::atomic<int> g_tile_bits[2][2] = {{{0}, {0}}, {{0}, {0}}};
+
 // Local qubits per tile of a fused pass (shared memory per CTA: 2^k amplitudes, twice that
-// for the adjoint's psi and lambda tiles).
+// for the adjoint's psi and lambda tiles): QS_TILE_BITS if set, else the tuned value, else
+// the default.
 static int tile_bits(int dtype, bool adjoint) {
     const char *env = std::getenv("QS_TILE_BITS");
     if (env && *env) {
         const int v = std::atoi(env);
         if (v >= 2 && v <= kTileMaxBits) return v;
     }
-    if (dtype == QS_C64) return adjoint ? 11 : 12;
-    return adjoint ? 10 : 11;
+    const int tuned = g_tile_bits[dtype == QS_C64 ? 0 : 1][adjoint ? 1 : 0].load();
+    if (tuned > 0) return tuned;
+    return dtype == QS_C64 ? 12 : (adjoint ? 10 : 11);
 }
 
 // Make sure `*buf` (device) holds `bytes`; grow-only. The old buffer may still be read by
@@ -163,12 +169,14 @@ static qs_status ensure_device(void **buf, size_t *cap, size_t bytes, cudaStream
 // Launch a fused program. Forward: `lam` == nullptr. Adjoint: single gates use the sweep
 // kernel with dus[g] / part + slot * P, passes use the adjoint tile kernel.
 static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std::vector<GatePlan> &plans,
-                                const TileGate *dev_table, void *lam, const std::vector<const double *> *dus,
+                                const void *dev_table, void *lam, const std::vector<const double *> *dus,
                                 const std::vector<int> *slots, double *part, size_t P, cudaStream_t st) {
+    const TileGroup *groups = dev_table ? table_groups(prog, dev_table) : nullptr;
+    const RegGate *gates = dev_table ? table_gates(prog, dev_table) : nullptr;
     for (const FusedOp &op : prog.ops) {
         cudaError_t e;
         if (op.pass >= 0) {
-            e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], dev_table, part, P, st);
+            e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], groups, gates, part, P, st);
         } else if (!lam) {
             e = launch_gate(s->dtype, s->psi, plans[op.gate], st);
         } else {
@@ -187,6 +195,15 @@ using namespace qs;
 
 extern "C" {
 
+qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits) {
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_set_tile_bits: bad dtype");
+    if (bits != 0 && (bits < 5 || bits > kTileMaxBits)) return set_error(QS_EINVAL, "qs_set_tile_bits: bits must be 0 or 5..14");
+    g_tile_bits[dtype == QS_C64 ? 0 : 1][adjoint ? 1 : 0].store(bits);
+    return QS_OK;
+}
+
+int qs_get_tile_bits(qs_dtype dtype, int adjoint) { return tile_bits(dtype, adjoint != 0); }
+
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
                            int flags) {
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
@@ -204,7 +221,9 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         for (size_t i = 0; i < count; ++i) seq[i] = (int)i;
         plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog);
     }
-    const size_t table_bytes = prog.gates.size() * sizeof(TileGate);
+    const size_t table_bytes = fuse ? program_table_bytes(prog) : 0;
+    std::vector<char> table_host(table_bytes);
+    if (table_bytes) pack_program_table(prog, table_host.data());
 
     if (!(flags & QS_FLAG_GRAPH)) {
         if (!fuse) return launch_plans(s, plans, s->stream);
@@ -213,12 +232,11 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         if (st != QS_OK) return st;
         if (table_bytes) {
             // stream-ordered: earlier passes on this stream have read the previous table
-            cudaError_t e = cudaMemcpyAsync(s->tile_table, prog.gates.data(), table_bytes, cudaMemcpyHostToDevice,
+            cudaError_t e = cudaMemcpyAsync(s->tile_table, table_host.data(), table_bytes, cudaMemcpyHostToDevice,
                                             s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit: gate table upload");
         }
-        return launch_program(s, prog, plans, static_cast<const TileGate *>(s->tile_table), nullptr, nullptr,
-                              nullptr, nullptr, 0, s->stream);
+        return launch_program(s, prog, plans, s->tile_table, nullptr, nullptr, nullptr, nullptr, 0, s->stream);
     }
 
     // CUDA graph: record once per distinct (gates, theta, flags, buffer), then replay.
@@ -241,7 +259,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
                 cudaGetLastError();
                 return set_error(QS_ENOMEM, "qs_apply_circuit: cannot allocate the graph's gate table");
             }
-            e = cudaMemcpy(table, prog.gates.data(), table_bytes, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(table, table_host.data(), table_bytes, cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
                 cudaFree(table);
                 return cuda_fail(e, "qs_apply_circuit: gate table upload");
@@ -259,8 +277,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
             if (table) cudaFree(table);
             return cuda_fail(e, "cudaStreamBeginCapture");
         }
-        qs_status st = fuse ? launch_program(s, prog, plans, static_cast<const TileGate *>(table), nullptr, nullptr,
-                                             nullptr, nullptr, 0, s->capture_stream)
+        qs_status st = fuse ? launch_program(s, prog, plans, table, nullptr, nullptr, nullptr, nullptr, 0,
+                                             s->capture_stream)
                             : launch_plans(s, plans, s->capture_stream);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(s->capture_stream, &graph);
@@ -385,19 +403,21 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     double *energy_dev = grad_dev + n_theta;
     cudaStream_t stm = s->stream;
 
-    // Gate tables of the fused forward and sweep programs (one upload, stream-ordered).
-    const size_t nf = pf.gates.size(), na = pa.gates.size();
-    if (fuse && nf + na > 0) {
-        st = ensure_device(&s->tile_table, &s->tile_table_bytes, (nf + na) * sizeof(TileGate), stm,
+    // Tables of the fused forward and sweep programs (one upload, stream-ordered).
+    const size_t bf = fuse ? (program_table_bytes(pf) + 255) & ~size_t(255) : 0;
+    const size_t ba = fuse ? program_table_bytes(pa) : 0;
+    if (fuse && bf + ba > 0) {
+        st = ensure_device(&s->tile_table, &s->tile_table_bytes, bf + ba, stm,
                            "qs_adjoint_grad: cannot allocate the fused gate table");
         if (st != QS_OK) return st;
-        std::vector<TileGate> both(pf.gates);
-        both.insert(both.end(), pa.gates.begin(), pa.gates.end());
-        e = cudaMemcpyAsync(s->tile_table, both.data(), both.size() * sizeof(TileGate), cudaMemcpyHostToDevice, stm);
+        std::vector<char> both(bf + ba);
+        pack_program_table(pf, both.data());
+        pack_program_table(pa, both.data() + bf);
+        e = cudaMemcpyAsync(s->tile_table, both.data(), both.size(), cudaMemcpyHostToDevice, stm);
         if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad: gate table upload");
     }
-    const TileGate *tab_f = static_cast<const TileGate *>(s->tile_table);
-    const TileGate *tab_a = tab_f ? tab_f + nf : nullptr;
+    const void *tab_f = s->tile_table;
+    const void *tab_a = tab_f ? static_cast<const char *>(tab_f) + bf : nullptr;
     // Forward pass.
     st = fuse ? launch_program(s, pf, fwd, tab_f, nullptr, nullptr, nullptr, nullptr, 0, stm)
               : launch_plans(s, fwd, stm);

@@ -28,41 +28,156 @@ static double single_fraction(const GatePlan &p, int dtype) {
     return std::ldexp(1.0, -popc(high));
 }
 
-static void make_tile_gate(const GatePlan &p, uint64_t Lmask, int k, const int *local_of, TileGate *G) {
-    std::memset(G, 0, sizeof(*G));
-    const int t_loc = local_of[p.t];
-    uint32_t cm = 0, cv = 0;
+// A gate of a pass in local coordinates (before grouping).
+struct LocalGate {
+    int t;                 // local target position
+    uint32_t cm, cv;       // local controls (local index bits) and their values
+    uint64_t hmask, hvals; // non-local controls
+    int op, side;
+    double U[8];
+};
+
+static LocalGate make_local_gate(const GatePlan &p, uint64_t Lmask, const int *local_of) {
+    LocalGate g;
+    std::memset(&g, 0, sizeof(g));
+    g.t = local_of[p.t];
     uint64_t lc = p.ctrl_mask & Lmask;
     while (lc) {
         const int q = __builtin_ctzll(lc);
         lc &= lc - 1;
-        cm |= 1u << local_of[q];
-        if ((p.ctrl_vals >> q) & 1ull) cv |= 1u << local_of[q];
+        g.cm |= 1u << local_of[q];
+        if ((p.ctrl_vals >> q) & 1ull) g.cv |= 1u << local_of[q];
     }
-    int pos[kTileMaxBits];
-    int m = 0;
-    uint32_t all = cm | (1u << t_loc);
-    while (all) {
-        pos[m++] = __builtin_ctz(all);
-        all &= all - 1;
+    g.hmask = p.ctrl_mask & ~Lmask;
+    g.hvals = p.ctrl_vals & g.hmask;
+    g.op = p.op;
+    g.side = p.side;
+    std::memcpy(g.U, p.U, sizeof(g.U));
+    return g;
+}
+
+// Choose the group qubits Q (r of them, containing the targets S): the rows of a warp vary
+// the lowest local qubits outside Q, and for shared-memory accesses without bank conflicts
+// the lowest `sw` of those must land on distinct low bits after the swizzle (qubit b lands on
+// b mod sw). Pads S with the lowest positions that keep that property, else with the best
+// found.
+static uint32_t choose_group(uint32_t S, int k, int r, int sw) {
+    auto score = [&](uint32_t Q) {
+        int seen = 0, distinct = 0, taken = 0;
+        for (int b = 0; b < k && taken < sw; ++b) {
+            if ((Q >> b) & 1u) continue;
+            ++taken;
+            const int res = b % sw;
+            if (!((seen >> res) & 1)) {
+                seen |= 1 << res;
+                ++distinct;
+            }
+        }
+        return (taken - distinct);  // colliding lanes; 0 = conflict-free
+    };
+    const int need = r - __builtin_popcount(S);
+    if (need <= 0) return S;
+    std::vector<int> free_pos;
+    for (int b = 0; b < k; ++b)
+        if (!((S >> b) & 1u)) free_pos.push_back(b);
+    uint32_t best = 0;
+    int best_score = 1 << 30;
+    // combinations of `need` free positions, lexicographic (lowest first)
+    std::vector<int> idx(need);
+    for (int i = 0; i < need; ++i) idx[i] = i;
+    const int m = (int)free_pos.size();
+    while (true) {
+        uint32_t Q = S;
+        for (int i = 0; i < need; ++i) Q |= 1u << free_pos[idx[i]];
+        const int sc = score(Q);
+        if (sc < best_score) {
+            best_score = sc;
+            best = Q;
+            if (sc == 0) break;
+        }
+        int i = need - 1;
+        while (i >= 0 && idx[i] == m - need + i) --i;
+        if (i < 0) break;
+        ++idx[i];
+        for (int j = i + 1; j < need; ++j) idx[j] = idx[j - 1] + 1;
     }
-    IndexMap map;
-    build_map(k, pos, m, cv, &map);
-    G->nseg = (uint8_t)map.nseg;
-    for (int s = 0; s < map.nseg; ++s) {
-        G->mask[s] = (uint32_t)map.mask[s];
-        G->shift[s] = (uint8_t)map.shift[s];
+    return best;
+}
+
+// Split a pass's gates into register groups and append them to the program.
+static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> &slots, const std::vector<const double *> &ds,
+                       const std::vector<int> &src, int k, int dtype, int group_bits, FusedProgram *prog, TilePass *P) {
+    const int r = std::min(group_bits, k);
+    const int sw = dtype == QS_C64 ? 4 : 3;
+    P->group_begin = (int)prog->groups.size();
+    P->gate_begin = (int)prog->gates.size();
+    size_t i = 0;
+    while (i < lg.size()) {
+        uint32_t S = 0;
+        size_t j = i;
+        while (j < lg.size()) {
+            const uint32_t S2 = S | (1u << lg[j].t);
+            if (__builtin_popcount(S2) > r) break;
+            S = S2;
+            ++j;
+        }
+        const uint32_t Q = choose_group(S, k, r, sw);
+        TileGroup Gr;
+        std::memset(&Gr, 0, sizeof(Gr));
+        Gr.r = (uint8_t)r;
+        int pos[kGroupBits], m = 0, place[kTileMaxBits];
+        for (int b = 0; b < k; ++b) {
+            place[b] = -1;
+            if ((Q >> b) & 1u) {
+                place[b] = m;
+                pos[m++] = b;
+                Gr.q[m - 1] = (uint8_t)b;
+            }
+        }
+        IndexMap map;
+        build_map(k, pos, m, 0, &map);
+        Gr.nrseg = (uint8_t)map.nseg;
+        for (int s = 0; s < map.nseg; ++s) {
+            Gr.rmask[s] = (uint32_t)map.mask[s];
+            Gr.rshift[s] = (uint8_t)map.shift[s];
+        }
+        Gr.gate_begin = (int)prog->gates.size();
+        for (size_t g = i; g < j; ++g) {
+            const LocalGate &L = lg[g];
+            RegGate R;
+            std::memset(&R, 0, sizeof(R));
+            R.p = (uint8_t)place[L.t];
+            for (int b = 0; b < k; ++b) {
+                if (!((L.cm >> b) & 1u)) continue;
+                const int val = (L.cv >> b) & 1u;
+                if (place[b] >= 0) {
+                    R.cqm |= (uint8_t)(1u << place[b]);
+                    R.cqv |= (uint8_t)(val << place[b]);
+                } else {
+                    R.crm |= 1u << b;
+                    R.crv |= (uint32_t)val << b;
+                }
+            }
+            R.hmask = L.hmask;
+            R.hvals = L.hvals;
+            R.op = L.op;
+            R.side = L.side;
+            R.slot = slots[g];
+            std::memcpy(R.U, L.U, sizeof(R.U));
+            for (int q = 0; q < 8; ++q) R.Uf[q] = (float)R.U[q];
+            if (ds[g]) {
+                std::memcpy(R.D, ds[g], sizeof(R.D));
+                for (int q = 0; q < 8; ++q) R.Df[q] = (float)R.D[q];
+            }
+            prog->gates.push_back(R);
+            prog->gate_src.push_back(src[g]);
+        }
+        Gr.gate_count = (int)prog->gates.size() - Gr.gate_begin;
+        prog->groups.push_back(Gr);
+        i = j;
     }
-    G->ins = cv;
-    G->tbit = 1u << t_loc;
-    G->log_pairs = (uint32_t)(k - m);
-    G->hmask = p.ctrl_mask & ~Lmask;
-    G->hvals = p.ctrl_vals & G->hmask;
-    G->op = p.op;
-    G->side = p.side;
-    G->slot = -1;
-    std::memcpy(G->U, p.U, sizeof(G->U));
-    for (int i = 0; i < 8; ++i) G->Uf[i] = (float)p.U[i];
+    P->group_count = (int)prog->groups.size() - P->group_begin;
+    P->gate_count = (int)prog->gates.size() - P->gate_begin;
 }
 
 static void make_pass(int n, uint64_t Lmask, TilePass *P) {
@@ -103,6 +218,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     prog->ops.clear();
     prog->passes.clear();
     prog->gates.clear();
+    prog->groups.clear();
     prog->gate_src.clear();
     max_gates = std::max(1, std::min(max_gates, kTileMaxGates));
     // k >= b0 + 1 so that any single target fits next to the b0 low qubits (n permitting)
@@ -159,27 +275,53 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         for (int q = 0, l = 0; q < n; ++q) local_of[q] = ((L >> q) & 1ull) ? l++ : -1;
         TilePass P;
         make_pass(n, L, &P);
-        P.gate_begin = (int)prog->gates.size();
+        std::vector<LocalGate> lg;
+        std::vector<int> slots, src;
+        std::vector<const double *> ds;
         for (int mbr : members) {
             if (mbr < 0) continue;
-            TileGate G;
-            make_tile_gate(plans[mbr], L, P.k, local_of, &G);
+            LocalGate g = make_local_gate(plans[mbr], L, local_of);
+            const double *d = nullptr;
+            int slot = -1;
             if (adjoint && (*dus)[mbr]) {
-                if (G.op != OP_GEN && G.op != OP_DIAG && G.op != OP_REAL) G.op = OP_GEN;
-                std::memcpy(G.D, (*dus)[mbr], sizeof(G.D));
-                for (int q = 0; q < 8; ++q) G.Df[q] = (float)G.D[q];
-                G.slot = P.nparam;
+                if (g.op != OP_GEN && g.op != OP_DIAG && g.op != OP_REAL) g.op = OP_GEN;
+                d = (*dus)[mbr];
+                slot = P.nparam;
                 P.param_gslot[P.nparam++] = (*gslots)[mbr];
             }
-            prog->gates.push_back(G);
-            prog->gate_src.push_back(mbr);
+            lg.push_back(g);
+            slots.push_back(slot);
+            ds.push_back(d);
+            src.push_back(mbr);
         }
-        P.gate_count = (int)prog->gates.size() - P.gate_begin;
+        add_groups(lg, slots, ds, src, P.k, dtype, adjoint ? kGroupBitsAdjoint : kGroupBits, prog, &P);
         prog->ops.push_back({(int)prog->passes.size(), -1});
         prog->passes.push_back(P);
         i = j;
     }
     return true;
+}
+
+static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+size_t program_table_bytes(const FusedProgram &p) {
+    return align16(p.groups.size() * sizeof(TileGroup)) + p.gates.size() * sizeof(RegGate);
+}
+
+void pack_program_table(const FusedProgram &p, void *host_dst) {
+    char *d = static_cast<char *>(host_dst);
+    if (!p.groups.empty()) std::memcpy(d, p.groups.data(), p.groups.size() * sizeof(TileGroup));
+    if (!p.gates.empty())
+        std::memcpy(d + align16(p.groups.size() * sizeof(TileGroup)), p.gates.data(), p.gates.size() * sizeof(RegGate));
+}
+
+const TileGroup *table_groups(const FusedProgram &, const void *dev_base) {
+    return static_cast<const TileGroup *>(dev_base);
+}
+
+const RegGate *table_gates(const FusedProgram &p, const void *dev_base) {
+    return reinterpret_cast<const RegGate *>(static_cast<const char *>(dev_base) +
+                                             align16(p.groups.size() * sizeof(TileGroup)));
 }
 
 }  // namespace qs

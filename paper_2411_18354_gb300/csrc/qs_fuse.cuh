@@ -15,9 +15,17 @@ struct FusedOp {
 struct FusedProgram {
     std::vector<FusedOp> ops;
     std::vector<TilePass> passes;
-    std::vector<TileGate> gates;  // all passes' gates, uploaded to the device once
-    std::vector<int> gate_src;    // plan index each TileGate came from
+    std::vector<TileGroup> groups;  // all passes' register groups
+    std::vector<RegGate> gates;     // all groups' gates
+    std::vector<int> gate_src;      // plan index each RegGate came from
 };
+
+// Byte size and packing of a program's device table: groups first, then gates (16-byte aligned).
+size_t program_table_bytes(const FusedProgram &p);
+void pack_program_table(const FusedProgram &p, void *host_dst);
+// Device pointers of the two parts, given the table's device base address.
+const TileGroup *table_groups(const FusedProgram &p, const void *dev_base);
+const RegGate *table_gates(const FusedProgram &p, const void *dev_base);
 
 // Plan the gates plans[seq[0]], plans[seq[1]], ... (execution order). For the adjoint
 // sweep, `dus[g]` is dU/dtheta of gate g (nullptr when g has no parameter) and `gslots[g]` its
@@ -27,5 +35,6 @@ struct FusedProgram {
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
                 int max_gates = kTileMaxGates, bool allow_single = true);
+// (the group size is kGroupBits for forward programs, kGroupBitsAdjoint when dus != nullptr)
 
 }  // namespace qs

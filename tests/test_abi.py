@@ -132,3 +132,23 @@ def test_wrapped_state_validates_gates_on_host():
             qs.qs_apply_circuit(h, gates, np.zeros(1), flags=1 << 10)
     finally:
         qs.qs_state_free(h)  # wrapped memory is not freed by the library
+
+
+def test_tile_bits_setting_is_validated_on_host():
+    for bad in (1, 4, 15, -2):
+        with pytest.raises(qs.QsError):
+            qs.qs_set_tile_bits(qs.QS_C64, 0, bad)
+    qs.qs_set_tile_bits(qs.QS_C64, 1, 9)
+    assert qs.qs_get_tile_bits(qs.QS_C64, 1) == 9
+    qs.qs_set_tile_bits(qs.QS_C64, 1, 0)
+    assert qs.qs_get_tile_bits(qs.QS_C64, 1) == 12
+
+
+def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
+    from paper_2411_18354_gb300 import autotune
+
+    monkeypatch.setenv("QS_AUTOTUNE_CACHE", str(tmp_path / "c.json"))
+    assert autotune._load() == {}
+    autotune._save({"k": {"tile_bits": 11}})
+    assert autotune._load() == {"k": {"tile_bits": 11}}
+    assert autotune._sig(np.arange(3)) == autotune._sig(np.arange(3)) != autotune._sig(np.arange(4))
