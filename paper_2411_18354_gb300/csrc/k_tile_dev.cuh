@@ -234,21 +234,36 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
     }
 }
 
-// Global <-> shared copies of one tile (swizzled in shared memory).
+// Global <-> shared copies of one tile (swizzled in shared memory). Loads are asynchronous
+// copies (cp.async, one per amplitude: 8 bytes for complex64, 16 for complex128) that need no
+// registers, so every thread has all its copies of the tile in flight at once; the caller's
+// block barrier follows the final wait.
+__device__ __forceinline__ void cp_async_8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <typename Real>
 __device__ __forceinline__ void load_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
                                           typename TileT<Real>::T2 *dst) {
-    using V = typename TileT<Real>::V;
-    using T2 = typename TileT<Real>::T2;
     constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
     const uint32_t nvec = (1u << P.k) / VEC;
     for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-        const uint32_t o = v * VEC;
-        const V x = *reinterpret_cast<const V *>(src + (base | scatter_local(P, o)));
-        const T2 *xs = reinterpret_cast<const T2 *>(&x);
+        const typename TileT<Real>::T2 *g = src + (base | scatter_local(P, v * VEC));
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) dst[tile_swizzle(o + i, SW)] = xs[i];
+        for (int i = 0; i < VEC; ++i) {
+            if (sizeof(Real) == 4) cp_async_8(dst + tile_swizzle(v * VEC + i, SW), g + i);
+            else cp_async_16(dst + tile_swizzle(v * VEC + i, SW), g + i);
+        }
     }
+    cp_async_wait_all();
 }
 
 template <typename Real>
@@ -259,12 +274,11 @@ __device__ __forceinline__ void store_tile(const TilePass &P, uint64_t base, con
     constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
     const uint32_t nvec = (1u << P.k) / VEC;
     for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-        const uint32_t o = v * VEC;
         V x;
         T2 *xs = reinterpret_cast<T2 *>(&x);
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) xs[i] = src[tile_swizzle(o + i, SW)];
-        *reinterpret_cast<V *>(dst + (base | scatter_local(P, o))) = x;
+        for (int i = 0; i < VEC; ++i) xs[i] = src[tile_swizzle(v * VEC + i, SW)];
+        *reinterpret_cast<V *>(dst + (base | scatter_local(P, v * VEC))) = x;
     }
 }
 
