@@ -49,6 +49,10 @@ def parse_args():
                     help="small profiling case: the 3 sweep gates with C controls (set 0) at --n, run twice "
                          "(profile with -s 3 -c 3 to skip the first round)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"], help="state precision of --ncu-case")
+    ap.add_argument("--ncu-fused", action="store_true",
+                    help="small profiling case: 2 layers of the ansatz at n=24, fused forward then fused gradient")
+    ap.add_argument("--ncu-batch", action="store_true",
+                    help="small profiling case: one batch launch of 304 states (n=16, 2 layers of the ansatz)")
     return ap.parse_args()
 
 
@@ -423,10 +427,53 @@ def run_ncu_case(args):
     print(f"ncu case done: n={args.n} c={args.ncu_case} {args.dtype} targets={[r[1] for r in rows]}")
 
 
+def run_ncu_fused(args):
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    n, layers = 24, 2
+    g = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    with qs.State(n, args.dtype) as st:
+        st.apply_circuit(g, th, qs.QS_FLAG_FUSE)
+        st.adjoint_grad(g, th, qs.QS_FLAG_FUSE)
+        torch.cuda.synchronize()
+    print("ncu fused case done")
+
+
+def run_ncu_batch(args):
+    import numpy as np
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    ns = [16] * 304
+    circ = W.hea_circuit(16, 2)
+    th = torch.tensor(np.random.default_rng(1).uniform(0, 6.28, size=304 * 64), dtype=torch.float64, device="cuda")
+    b = qs.Batch(ns, [circ] * 304, [64] * 304, "c64")
+    en = torch.zeros(304, dtype=torch.float64, device="cuda")
+    gr = torch.zeros(304 * 64, dtype=torch.float64, device="cuda")
+    b.run(th, en, gr, 0)
+    torch.cuda.synchronize()
+    b.close()
+    print("ncu batch case done")
+
+
 def main():
     args = parse_args()
     if args.ncu_case is not None:
         run_ncu_case(args)
+        return
+    if args.ncu_fused:
+        run_ncu_fused(args)
+        return
+    if args.ncu_batch:
+        run_ncu_batch(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

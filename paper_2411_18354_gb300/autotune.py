@@ -22,10 +22,10 @@ from . import _lib
 
 FUSED_CANDIDATES = (10, 11, 12, 13)
 BATCH_CANDIDATES = (
-    {"small_bits": 12, "tile_bits": 12, "max_pass_gates": 96},
-    {"small_bits": 12, "tile_bits": 11, "max_pass_gates": 96},
-    {"small_bits": 11, "tile_bits": 11, "max_pass_gates": 96},
-    {"small_bits": 13, "tile_bits": 13, "max_pass_gates": 96},
+    {"small_bits": 12, "tile_bits": 12, "max_pass_gates": 64},
+    {"small_bits": 12, "tile_bits": 11, "max_pass_gates": 64},
+    {"small_bits": 11, "tile_bits": 11, "max_pass_gates": 64},
+    {"small_bits": 13, "tile_bits": 13, "max_pass_gates": 64},
     {"small_bits": 12, "tile_bits": 12, "max_pass_gates": 32},
 )
 

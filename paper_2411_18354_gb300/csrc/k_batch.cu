@@ -41,37 +41,47 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 template <typename Real>
 __device__ __forceinline__ double obs_pass(const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst, int n,
                                            double *red, int sw) {
+    using T2 = typename TileT<Real>::T2;
+    constexpr int U = 4;  // independent loads in flight per thread
     const uint64_t N = 1ull << n;
     double acc = 0.0;
-    Real run = 0;
-    int cnt = 0;
-    for (uint64_t k = threadIdx.x; k < N; k += blockDim.x) {
-        const Real w = (Real)(n - 2 * __popcll(k));
-        const uint64_t pos = sw ? tile_swizzle((uint32_t)k, sw) : k;
-        typename TileT<Real>::T2 v = src[pos];
-        run += w * (v.x * v.x + v.y * v.y);
-        v.x *= w;
-        v.y *= w;
-        dst[pos] = v;
-        if (++cnt == 32) {
-            acc += (double)run;
-            run = 0;
-            cnt = 0;
+    for (uint64_t k0 = threadIdx.x; k0 < N; k0 += (uint64_t)U * blockDim.x) {
+        T2 v[U];
+        uint64_t pos[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.x;
+            pos[u] = k < N ? (sw ? tile_swizzle((uint32_t)k, sw) : k) : 0;
+            if (k < N) v[u] = src[pos[u]];
         }
+        Real run = 0;  // float over U terms, float64 above
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t k = k0 + (uint64_t)u * blockDim.x;
+            if (k < N) {
+                const Real w = (Real)(n - 2 * __popcll(k));
+                run += w * (v[u].x * v[u].x + v[u].y * v[u].y);
+                v[u].x *= w;
+                v[u].y *= w;
+                dst[pos[u]] = v[u];
+            }
+        }
+        acc += (double)run;
     }
-    acc += (double)run;
     return block_sum<Real>(acc, red);
 }
 
 template <typename Real>
 __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool adjoint, typename TileT<Real>::T2 *psi,
                                    typename TileT<Real>::T2 *lam, typename TileT<Real>::T2 *tp,
-                                   typename TileT<Real>::T2 *tl, const Real *cs, double *gacc) {
+                                   typename TileT<Real>::T2 *tl, const Real *cs, double *gacc, TileGroup *sgroups,
+                                   SGate<Real> *sgates) {
     const int begin = adjoint ? pg.adj_begin : pg.fwd_begin;
     const int count = adjoint ? pg.adj_count : pg.fwd_count;
     for (int pi = begin; pi < begin + count; ++pi) {
         const TilePass &P = a.passes[pi];
-        const RegGate *G0 = a.gates + P.gate_begin;
+        stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+        const SGate<Real> *G0 = sgates;
         for (uint64_t tau = 0; tau < P.ntiles; ++tau) {
             const uint64_t base = tile_base(P, tau);
             bool any = false;
@@ -81,14 +91,14 @@ __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool
             if (adjoint) load_tile<Real>(P, base, lam, tl);
             __syncthreads();
             if (adjoint)
-                apply_groups<Real, true>(tp, tl, base, P.k, a.groups + P.group_begin, P.group_count, a.gates, cs, gacc);
+                apply_groups<Real, true>(tp, tl, base, P.k, sgroups, P.group_count, sgates, cs, gacc);
             else
-                apply_groups<Real, false>(tp, nullptr, base, P.k, a.groups + P.group_begin, P.group_count, a.gates, cs,
-                                          nullptr);
+                apply_groups<Real, false>(tp, nullptr, base, P.k, sgroups, P.group_count, sgates, cs, nullptr);
             store_tile<Real>(P, base, tp, psi);
             if (adjoint) store_tile<Real>(P, base, tl, lam);
             __syncthreads();
         }
+        __syncthreads();  // the next pass restages the gate table
     }
 }
 
@@ -102,7 +112,9 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
     Real *cs = reinterpret_cast<Real *>(tl + T);                                   // [2 * max_params]
     double *gacc = reinterpret_cast<double *>(cs + 2 * ((a.max_params + 1) & ~1));  // [max_params * nwarps]
     double *red = gacc + (size_t)a.max_params * (kBatchThreads / 32);              // [nwarps]
-    int *next = reinterpret_cast<int *>(red + kBatchThreads / 32);
+    TileGroup *sgroups = reinterpret_cast<TileGroup *>(red + kBatchThreads / 32);
+    SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
+    int *next = reinterpret_cast<int *>(sgates + kTileMaxGates);
     const int tid = threadIdx.x;
     const int nwarps = kBatchThreads / 32;
     T2 *ws_psi = reinterpret_cast<T2 *>(a.workspace) + (size_t)blockIdx.x * 2 * a.ws_stride;
@@ -131,21 +143,24 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
             __syncthreads();
             for (int pi = pg.fwd_begin; pi < pg.fwd_begin + pg.fwd_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                apply_groups<Real, false>(tp, nullptr, 0, n, a.groups + P.group_begin, P.group_count, a.gates, cs,
-                                          nullptr);
+                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+                apply_groups<Real, false>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
+                __syncthreads();
             }
             energy = obs_pass<Real>(tp, tl, n, red, TileT<Real>::SW);
             for (int pi = pg.adj_begin; pi < pg.adj_begin + pg.adj_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                apply_groups<Real, true>(tp, tl, 0, n, a.groups + P.group_begin, P.group_count, a.gates, cs, gacc);
+                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+                apply_groups<Real, true>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
+                __syncthreads();
             }
         } else {
             const uint64_t N = 1ull << n;
             for (uint64_t k = tid; k < N; k += kBatchThreads) ws_psi[k] = T2{(Real)(k == 0), (Real)0};
             __syncthreads();
-            run_program_global<Real>(a, pg, false, ws_psi, ws_lam, tp, tl, cs, nullptr);
+            run_program_global<Real>(a, pg, false, ws_psi, ws_lam, tp, tl, cs, nullptr, sgroups, sgates);
             energy = obs_pass<Real>(ws_psi, ws_lam, n, red, 0);
-            run_program_global<Real>(a, pg, true, ws_psi, ws_lam, tp, tl, cs, gacc);
+            run_program_global<Real>(a, pg, true, ws_psi, ws_lam, tp, tl, cs, gacc, sgroups, sgates);
         }
         __syncthreads();
         if (tid == 0) a.energy[a.order[qi]] = energy;
@@ -163,8 +178,10 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
 size_t batch_smem_bytes(int dtype, int smem_bits, int max_params) {
     const size_t es = dtype == QS_C64 ? 8 : 16;
     const size_t rs = dtype == QS_C64 ? 4 : 8;
+    const size_t sg = dtype == QS_C64 ? sizeof(SGate<float>) : sizeof(SGate<double>);
     return 2 * (size_t(1) << smem_bits) * es + 2 * (size_t)((max_params + 1) & ~1) * rs +
-           (size_t)max_params * (kBatchThreads / 32) * sizeof(double) + (kBatchThreads / 32) * sizeof(double) + 16;
+           (size_t)max_params * (kBatchThreads / 32) * sizeof(double) + (kBatchThreads / 32) * sizeof(double) +
+           kTileMaxGates * (sizeof(TileGroup) + sg) + 16;
 }
 
 int batch_grid(int dtype, size_t smem) {

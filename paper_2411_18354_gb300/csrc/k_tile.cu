@@ -19,12 +19,13 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
     T2 *tl = tp + T;  // adjoint: lambda tile
     double *acc = reinterpret_cast<double *>(smem_raw + (ADJ ? 2 : 1) * (size_t)T * sizeof(T2));  // [kTileMaxParam][8]
+    TileGroup *sgroups = reinterpret_cast<TileGroup *>(acc + (ADJ ? kTileMaxParam * (kTileThreads / 32) : 0));
+    SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
     const int tid = threadIdx.x;
-    if (ADJ) {
+    if (ADJ)
         for (int i = tid; i < kTileMaxParam * (kTileThreads / 32); i += kTileThreads) acc[i] = 0.0;
-        __syncthreads();
-    }
-    const RegGate *G0 = gates + P.gate_begin;
+    stage_pass<Real>(P, groups, gates, sgroups, sgates);
+    const SGate<Real> *G0 = sgates;
     for (uint64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
         const uint64_t base = tile_base(P, tau);
         bool any = false;
@@ -33,7 +34,7 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
         load_tile<Real>(P, base, psi, tp);
         if (ADJ) load_tile<Real>(P, base, lam, tl);
         __syncthreads();
-        apply_groups<Real, ADJ>(tp, tl, base, P.k, groups + P.group_begin, P.group_count, gates, nullptr, acc);
+        apply_groups<Real, ADJ>(tp, tl, base, P.k, sgroups, P.group_count, sgates, nullptr, acc);
         store_tile<Real>(P, base, tp, psi);
         if (ADJ) store_tile<Real>(P, base, tl, lam);
         __syncthreads();
@@ -74,7 +75,9 @@ cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGroup *groups,
 
 size_t tile_smem_bytes(int dtype, int k, bool adjoint) {
     const size_t es = dtype == QS_C64 ? 8 : 16;
-    return (adjoint ? 2 : 1) * (size_t(1) << k) * es + (adjoint ? kTileMaxParam * (kTileThreads / 32) * sizeof(double) : 0);
+    const size_t sg = dtype == QS_C64 ? sizeof(SGate<float>) : sizeof(SGate<double>);
+    return (adjoint ? 2 : 1) * (size_t(1) << k) * es + (adjoint ? kTileMaxParam * (kTileThreads / 32) * sizeof(double) : 0) +
+           kTileMaxGates * (sizeof(TileGroup) + sg);
 }
 
 cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,

@@ -24,7 +24,7 @@ constexpr int kTileMaxBits = 14;
 constexpr int kGroupBits = 4;      // register qubits per group, at most (16 amplitudes per row)
 constexpr int kGroupBitsAdjoint = 3;  // in the adjoint sweep (psi and lambda rows in registers)
 constexpr int kTileMaxParam = 64;  // parameterised gates per adjoint pass
-constexpr int kTileMaxGates = 96;  // gates per pass
+constexpr int kTileMaxGates = 64;  // gates (and so at most as many groups) per pass
 constexpr int kTileThreads = 256;
 
 // One gate inside a register group.

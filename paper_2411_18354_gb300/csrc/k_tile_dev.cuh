@@ -27,6 +27,54 @@ template <> struct TileT<double> {
     __device__ static const double *D(const RegGate &G) { return G.D; }
 };
 
+// Compact copy of a RegGate in shared memory (matrices in the state's precision), staged once
+// per pass so that every row reads its gates with broadcast shared-memory loads.
+template <typename Real> struct SGate {
+    uint64_t hmask, hvals;
+    uint32_t crm, crv;
+    int8_t p, cqm, cqv, op, side, pkind;
+    int16_t slot;
+    int32_t pidx;
+    Real u[8], d[8];
+};
+
+template <typename Real>
+__device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S) {
+    S.hmask = G.hmask;
+    S.hvals = G.hvals;
+    S.crm = G.crm;
+    S.crv = G.crv;
+    S.p = (int8_t)G.p;
+    S.cqm = (int8_t)G.cqm;
+    S.cqv = (int8_t)G.cqv;
+    S.op = (int8_t)G.op;
+    S.side = (int8_t)G.side;
+    S.pkind = (int8_t)G.pkind;
+    S.slot = (int16_t)G.slot;
+    S.pidx = G.pidx;
+    const Real *u = TileT<Real>::U(G);
+    const Real *d = TileT<Real>::D(G);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        S.u[i] = u[i];
+        S.d[i] = d[i];
+    }
+}
+
+// Copy a pass's groups and gates to shared memory (group gate indices become pass-relative).
+// Ends with a block barrier.
+template <typename Real>
+__device__ __forceinline__ void stage_pass(const TilePass &P, const TileGroup *groups, const RegGate *gates,
+                                           TileGroup *sgroups, SGate<Real> *sgates) {
+    for (int i = threadIdx.x; i < P.group_count; i += blockDim.x) {
+        TileGroup g = groups[P.group_begin + i];
+        g.gate_begin -= P.gate_begin;
+        sgroups[i] = g;
+    }
+    for (int i = threadIdx.x; i < P.gate_count; i += blockDim.x) stage_gate<Real>(gates[P.gate_begin + i], sgates[i]);
+    __syncthreads();
+}
+
 // Gate fields kept in registers while a row is processed.
 template <typename Real> struct GateRegs {
     uint32_t crm, crv;
@@ -68,7 +116,7 @@ __device__ __forceinline__ void param_matrices(int kind, Real c, Real s, bool ad
 }
 
 template <typename Real>
-__device__ __forceinline__ void load_gate(const RegGate &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
+__device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
     r.crm = G.crm;
     r.crv = G.crv;
     r.p = G.p;
@@ -80,12 +128,10 @@ __device__ __forceinline__ void load_gate(const RegGate &G, GateRegs<Real> &r, c
     if (G.pkind != 0 && cs) {
         param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, r.u, r.d);
     } else {
-        const Real *u = TileT<Real>::U(G);
-        const Real *d = TileT<Real>::D(G);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            r.u[i] = u[i];
-            r.d[i] = d[i];
+            r.u[i] = G.u[i];
+            r.d[i] = G.d[i];
         }
     }
 }
@@ -167,7 +213,7 @@ template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
 // ends with a block barrier.
 template <typename Real, bool ADJ>
 __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
-                                             int k, const TileGroup *groups, int group_count, const RegGate *gates,
+                                             int k, const TileGroup *groups, int group_count, const SGate<Real> *gates,
                                              const Real *cs, double *acc) {
     using T2 = typename TileT<Real>::T2;
     constexpr int SW = TileT<Real>::SW;
@@ -205,7 +251,7 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                 }
             }
             for (int g = 0; g < Gr.gate_count; ++g) {
-                const RegGate &G = gates[Gr.gate_begin + g];
+                const SGate<Real> &G = gates[Gr.gate_begin + g];
                 if ((base & G.hmask) != G.hvals) continue;  // uniform
                 GateRegs<Real> R;
                 load_gate<Real>(G, R, cs, ADJ);
