@@ -129,9 +129,10 @@ __device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &
         param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, r.u, r.d);
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            r.u[i] = G.u[i];
-            r.d[i] = G.d[i];
+        for (int i = 0; i < 8; ++i) r.u[i] = G.u[i];
+        if (adjoint && r.slot >= 0) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) r.d[i] = G.d[i];
         }
     }
 }
@@ -159,16 +160,19 @@ __device__ __forceinline__ void op_pair(T2 &x, T2 &y, const Real *u, int side) {
     }
 }
 
-// All pairs (e, e | 2^P) of one row for one gate with operation OP.
-template <int P, int OP, bool ADJ, int GB, typename T2, typename Real>
-__device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+// All pairs (e, e | 2^P) of one row for one gate with operation OP; CQ: the gate has
+// controls on group qubits (else every pair of a selected row is updated). Rows of tiles with
+// fewer than GB qubits are padded with zero elements that pair only with each other, so they
+// stay zero and add nothing to the inner products.
+template <int P, int OP, bool ADJ, int GB, bool CQ, typename T2, typename Real>
+__device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
     constexpr int DOP = OP == OP_DIAG ? OP_DIAG : (OP == OP_REAL ? OP_REAL : OP_GEN);
+    if (!row_ok) return;
 #pragma unroll
     for (int e = 0; e < (1 << GB); ++e) {
         if ((e >> P) & 1) continue;
         const int e2 = e | (1 << P);
-        const bool ok = row_ok && ((e & R.cqm) == R.cqv) && (e2 < (1 << r));
-        if (ok) {
+        if (!CQ || ((e & R.cqm) == R.cqv)) {
             op_pair<OP, T2, Real>(v[e], v[e2], R.u, R.side);
             if (ADJ) {
                 if (R.slot >= 0) {
@@ -182,24 +186,30 @@ __device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R,
     }
 }
 
-template <int OP, bool ADJ, int GB, typename T2, typename Real>
-__device__ __forceinline__ void row_gate_op(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+template <int OP, bool ADJ, int GB, bool CQ, typename T2, typename Real>
+__device__ __forceinline__ void row_gate_p(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
     switch (R.p) {
-        case 0: row_pairs<0, OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        case 1: if (GB > 1) row_pairs<(GB > 1 ? 1 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        case 2: if (GB > 2) row_pairs<(GB > 2 ? 2 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        default: if (GB > 3) row_pairs<(GB > 3 ? 3 : 0), OP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case 0: row_pairs<0, OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
+        case 1: if (GB > 1) row_pairs<(GB > 1 ? 1 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
+        case 2: if (GB > 2) row_pairs<(GB > 2 ? 2 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
+        default: if (GB > 3) row_pairs<(GB > 3 ? 3 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
     }
 }
 
+template <int OP, bool ADJ, int GB, typename T2, typename Real>
+__device__ __forceinline__ void row_gate_op(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
+    if (R.cqm) row_gate_p<OP, ADJ, GB, true, T2, Real>(v, w, R, row_ok, dot);
+    else row_gate_p<OP, ADJ, GB, false, T2, Real>(v, w, R, row_ok, dot);
+}
+
 template <bool ADJ, int GB, typename T2, typename Real>
-__device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, int r, bool row_ok, Real &dot) {
+__device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
     switch (R.op) {
-        case OP_GEN: row_gate_op<OP_GEN, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        case OP_REAL: row_gate_op<OP_REAL, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        case OP_DIAG: row_gate_op<OP_DIAG, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        case OP_SWAP: row_gate_op<OP_SWAP, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
-        default: row_gate_op<OP_SIDE, ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot); break;
+        case OP_GEN: row_gate_op<OP_GEN, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
+        case OP_REAL: row_gate_op<OP_REAL, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
+        case OP_DIAG: row_gate_op<OP_DIAG, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
+        case OP_SWAP: row_gate_op<OP_SWAP, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
+        default: row_gate_op<OP_SIDE, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
     }
 }
 
@@ -227,24 +237,26 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
             any |= (base & gates[Gr.gate_begin + g].hmask) == gates[Gr.gate_begin + g].hvals;
         if (!any) continue;  // uniform: nothing of this group touches the tile
         const int r = Gr.r;
-        uint32_t qb[4];
+        // The swizzle is linear over XOR (a ^ f(a) with f built from shifts and XORs), so the
+        // position of (row bits | element bits) is swz(row) ^ swz(element bits).
+        uint32_t qs_[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) qb[i] = i < r ? (1u << Gr.q[i]) : 0u;
+        for (int i = 0; i < 4; ++i) qs_[i] = i < r ? tile_swizzle(1u << Gr.q[i], SW) : 0u;
         const uint32_t rows = 1u << (k - r);
         for (uint32_t rb = 0; rb < rows; rb += blockDim.x) {
             const uint32_t rho = rb + tid;
             const bool active = rho < rows;
             uint32_t ra = 0;
             for (int s = 0; s < Gr.nrseg; ++s) ra |= (rho << Gr.rshift[s]) & Gr.rmask[s];
+            const uint32_t rs = tile_swizzle(ra, SW);
             T2 v[E], w[ADJ ? E : 1];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const uint32_t a = ra | ((e & 1) ? qb[0] : 0u) | ((e & 2) ? qb[1] : 0u) | ((e & 4) ? qb[2] : 0u) |
-                                   ((e & 8) ? qb[3] : 0u);
+                const uint32_t ps = rs ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^ ((e & 4) ? qs_[2] : 0u) ^
+                                    ((e & 8) ? qs_[3] : 0u);
                 if (active && e < (1 << r)) {
-                    const uint32_t s = tile_swizzle(a, SW);
-                    v[e] = tp[s];
-                    if (ADJ) w[e] = tl[s];
+                    v[e] = tp[ps];
+                    if (ADJ) w[e] = tl[ps];
                 } else {
                     v[e] = T2{0, 0};
                     if (ADJ) w[e] = T2{0, 0};
@@ -257,7 +269,7 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                 load_gate<Real>(G, R, cs, ADJ);
                 const bool row_ok = active && ((ra & R.crm) == R.crv);
                 Real dot = 0;
-                row_gate<ADJ, GB, T2, Real>(v, w, R, r, row_ok, dot);
+                row_gate<ADJ, GB, T2, Real>(v, w, R, row_ok, dot);
                 if (ADJ && R.slot >= 0) {
                     double d = (double)dot;
 #pragma unroll
@@ -267,12 +279,11 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
             }
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const uint32_t a = ra | ((e & 1) ? qb[0] : 0u) | ((e & 2) ? qb[1] : 0u) | ((e & 4) ? qb[2] : 0u) |
-                                   ((e & 8) ? qb[3] : 0u);
+                const uint32_t ps = rs ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^ ((e & 4) ? qs_[2] : 0u) ^
+                                    ((e & 8) ? qs_[3] : 0u);
                 if (active && e < (1 << r)) {
-                    const uint32_t s = tile_swizzle(a, SW);
-                    tp[s] = v[e];
-                    if (ADJ) tl[s] = w[e];
+                    tp[ps] = v[e];
+                    if (ADJ) tl[ps] = w[e];
                 }
             }
         }
@@ -296,17 +307,26 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Element o = VEC * (tid + j * blockDim) + i of a tile: both its global offset (a bit deposit)
+// and its shared-memory position (the swizzle) are XOR-linear over disjoint bit fields, so
+// they split into a per-thread part, a per-step part and a per-element part.
 template <typename Real>
 __device__ __forceinline__ void load_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
                                           typename TileT<Real>::T2 *dst) {
     constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
     const uint32_t nvec = (1u << P.k) / VEC;
-    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
-        const typename TileT<Real>::T2 *g = src + (base | scatter_local(P, v * VEC));
+    const uint32_t o_t = threadIdx.x * VEC;
+    const uint64_t g_t = base | scatter_local(P, o_t);
+    const uint32_t s_t = tile_swizzle(o_t, SW);
+    const uint32_t s_1 = tile_swizzle(1u, SW);
+    for (uint32_t v0 = 0; v0 + threadIdx.x < nvec; v0 += blockDim.x) {
+        const uint32_t o_j = v0 * VEC;  // disjoint from o_t: blockDim * VEC is a power of two
+        const typename TileT<Real>::T2 *g = src + (g_t | scatter_local(P, o_j));
+        const uint32_t s = s_t ^ tile_swizzle(o_j, SW);
 #pragma unroll
         for (int i = 0; i < VEC; ++i) {
-            if (sizeof(Real) == 4) cp_async_8(dst + tile_swizzle(v * VEC + i, SW), g + i);
-            else cp_async_16(dst + tile_swizzle(v * VEC + i, SW), g + i);
+            if (sizeof(Real) == 4) cp_async_8(dst + (i ? (s ^ s_1) : s), g + i);
+            else cp_async_16(dst + s, g);
         }
     }
     cp_async_wait_all();
@@ -319,12 +339,18 @@ __device__ __forceinline__ void store_tile(const TilePass &P, uint64_t base, con
     using T2 = typename TileT<Real>::T2;
     constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
     const uint32_t nvec = (1u << P.k) / VEC;
-    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+    const uint32_t o_t = threadIdx.x * VEC;
+    const uint64_t g_t = base | scatter_local(P, o_t);
+    const uint32_t s_t = tile_swizzle(o_t, SW);
+    const uint32_t s_1 = tile_swizzle(1u, SW);
+    for (uint32_t v0 = 0; v0 + threadIdx.x < nvec; v0 += blockDim.x) {
+        const uint32_t o_j = v0 * VEC;
+        const uint32_t s = s_t ^ tile_swizzle(o_j, SW);
         V x;
         T2 *xs = reinterpret_cast<T2 *>(&x);
 #pragma unroll
-        for (int i = 0; i < VEC; ++i) xs[i] = src[tile_swizzle(v * VEC + i, SW)];
-        *reinterpret_cast<V *>(dst + (base | scatter_local(P, v * VEC))) = x;
+        for (int i = 0; i < VEC; ++i) xs[i] = src[i ? (s ^ s_1) : s];
+        *reinterpret_cast<V *>(dst + (g_t | scatter_local(P, o_j))) = x;
     }
 }
 
