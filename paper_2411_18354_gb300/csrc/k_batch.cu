@@ -84,9 +84,11 @@ __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool
         const SGate<Real> *G0 = sgates;
         for (uint64_t tau = 0; tau < P.ntiles; ++tau) {
             const uint64_t base = tile_base(P, tau);
-            bool any = false;
-            for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
-            if (!any) continue;
+            if (P.hctrl) {
+                bool any = false;
+                for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
+                if (!any) continue;
+            }
             load_tile<Real>(P, base, psi, tp);
             if (adjoint) load_tile<Real>(P, base, lam, tl);
             __syncthreads();

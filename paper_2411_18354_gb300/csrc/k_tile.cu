@@ -28,9 +28,11 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
     const SGate<Real> *G0 = sgates;
     for (uint64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
         const uint64_t base = tile_base(P, tau);
-        bool any = false;
-        for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
-        if (!any) continue;  // no gate of the pass selects this tile
+        if (P.hctrl) {
+            bool any = false;
+            for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
+            if (!any) continue;  // no gate of the pass selects this tile
+        }
         load_tile<Real>(P, base, psi, tp);
         if (ADJ) load_tile<Real>(P, base, lam, tl);
         __syncthreads();

@@ -54,7 +54,9 @@ struct TileGroup {
     uint8_t nrseg;            // row -> local index segments
     uint8_t rshift[kGroupBits + 1];
     uint32_t rmask[kGroupBits + 1];
+    uint32_t qsw[kGroupBits];  // shared-memory offset (swizzled) of each group qubit's bit
     int32_t gate_begin, gate_count;  // into the RegGate table
+    int32_t hctrl;             // some gate of the group has a non-local control
 };
 
 struct TilePass {
@@ -67,6 +69,7 @@ struct TilePass {
     uint64_t ntiles;
     int32_t gate_begin, gate_count;    // all RegGates of the pass
     int32_t group_begin, group_count;  // its register groups
+    int32_t hctrl;                     // some gate of the pass has a non-local control
     int32_t nparam;            // adjoint: parameterised gates of this pass
     int32_t param_gslot[kTileMaxParam];  // adjoint: global gradient slot of each accumulator
 };

@@ -232,16 +232,19 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int gi = 0; gi < group_count; ++gi) {
         const TileGroup &Gr = groups[gi];
-        bool any = false;
-        for (int g = 0; g < Gr.gate_count; ++g)
-            any |= (base & gates[Gr.gate_begin + g].hmask) == gates[Gr.gate_begin + g].hvals;
-        if (!any) continue;  // uniform: nothing of this group touches the tile
+        if (Gr.hctrl) {
+            bool any = false;
+            for (int g = 0; g < Gr.gate_count; ++g)
+                any |= (base & gates[Gr.gate_begin + g].hmask) == gates[Gr.gate_begin + g].hvals;
+            if (!any) continue;  // uniform: nothing of this group touches the tile
+        }
         const int r = Gr.r;
         // The swizzle is linear over XOR (a ^ f(a) with f built from shifts and XORs), so the
-        // position of (row bits | element bits) is swz(row) ^ swz(element bits).
+        // position of (row bits | element bits) is swz(row) ^ swz(element bits); the group
+        // qubits' offsets come precomputed.
         uint32_t qs_[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) qs_[i] = i < r ? tile_swizzle(1u << Gr.q[i], SW) : 0u;
+        for (int i = 0; i < 4; ++i) qs_[i] = Gr.qsw[i];
         const uint32_t rows = 1u << (k - r);
         for (uint32_t rb = 0; rb < rows; rb += blockDim.x) {
             const uint32_t rho = rb + tid;
@@ -264,7 +267,7 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
             }
             for (int g = 0; g < Gr.gate_count; ++g) {
                 const SGate<Real> &G = gates[Gr.gate_begin + g];
-                if ((base & G.hmask) != G.hvals) continue;  // uniform
+                if (Gr.hctrl && (base & G.hmask) != G.hvals) continue;  // uniform
                 GateRegs<Real> R;
                 load_gate<Real>(G, R, cs, ADJ);
                 const bool row_ok = active && ((ra & R.crm) == R.crv);

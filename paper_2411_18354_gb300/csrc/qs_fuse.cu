@@ -173,6 +173,9 @@ static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> 
             prog->gate_src.push_back(src[g]);
         }
         Gr.gate_count = (int)prog->gates.size() - Gr.gate_begin;
+        for (int q = 0; q < kGroupBits; ++q) Gr.qsw[q] = q < m ? tile_swizzle(1u << Gr.q[q], sw) : 0u;
+        for (int g = Gr.gate_begin; g < Gr.gate_begin + Gr.gate_count; ++g) Gr.hctrl |= prog->gates[g].hmask != 0;
+        P->hctrl |= Gr.hctrl;
         prog->groups.push_back(Gr);
         i = j;
     }
