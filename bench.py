@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"], help="state precision of --ncu-case")
     ap.add_argument("--ncu-fused", action="store_true",
                     help="small profiling case: 2 layers of the ansatz at n=24, fused forward then fused gradient")
+    ap.add_argument("--ncu-reduce", action="store_true",
+                    help="small profiling case: <Z_i> + norm of an n=27 state, twice")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="small profiling case: one batch launch of 304 states (n=16, 2 layers of the ansatz)")
     return ap.parse_args()
@@ -165,6 +167,14 @@ def alg_bytes(n, c, esize):
     return 2 * (1 << (n - c)) * esize
 
 
+def sector_bytes(n, mask, esize):
+    """Bytes of the 64-byte DRAM units that hold a selected amplitude (read + write): controls
+    on the qubits inside one unit (0-2 for complex64, 0-1 for complex128) do not reduce it."""
+    unit_bits = 3 if esize == 8 else 2
+    c_hi = bin(mask >> unit_bits).count("1")
+    return 2 * (1 << (n - c_hi)) * esize
+
+
 def run_sweep(qs, st, n, esize, sched, steps, warmup, per_launch=True):
     """Device-timed sweep steps through qs_apply_gate. Returns per-launch ms and step ms."""
     import torch
@@ -189,29 +199,50 @@ def run_sweep(qs, st, n, esize, sched, steps, warmup, per_launch=True):
                 e0.record(stream)
                 apply(st.h, t, m, v, U)
                 e1.record(stream)
-                launches.append((c, t, e0, e1))
+                launches.append((c, t, m, e0, e1))
             else:
                 apply(st.h, t, m, v, U)
         s1.record(stream)
         step_ev.append((s0, s1))
     torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
-    per = [(c, t, a.elapsed_time(b)) for c, t, a, b in launches]
+    per = [(c, t, a.elapsed_time(b), m) for c, t, m, a, b in launches]
     return step_ms, per
 
 
-def measure_adjoint(qs, W, reps=2):
+def _events_ms(fn, reps):
+    """Average device time of fn() over reps runs (CUDA events on the current stream)."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_adjoint(qs, W, reps=3):
     """Differentiation workload: n = 24, 20 layers, 960 parameters. grads/s = parameters /
-    wall time of one full gradient (forward + energy + reverse sweep)."""
+    time of one full gradient (forward + energy + reverse sweep, host outputs)."""
     import numpy as np
     import torch
+
+    from paper_2411_18354_gb300 import autotune
 
     n, layers = 24, 20
     gates = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
-    out = {}
+    tuned = {"fwd": autotune.tune_fused(n, "c64", gates, th, adjoint=False, use_cache=False, reps=1),
+             "adj": autotune.tune_fused(n, "c64", gates, th, adjoint=True, use_cache=False, reps=1)}
+    out = {"tile_bits_c64": {"forward": tuned["fwd"]["tile_bits"], "adjoint": tuned["adj"]["tile_bits"]}}
     grads = {}
-    for label, dtype, flags in (("c64", "c64", 0), ("c128_plain", "c128", 0)):
+    for label, dtype, flags in (("c64_fused", "c64", qs.QS_FLAG_FUSE), ("c64_unfused", "c64", 0),
+                                ("c128_plain", "c128", 0)):
         st = qs.State(n, dtype)
         try:
             st.adjoint_grad(gates, th, flags)  # warm-up (allocates lambda and scratch)
@@ -223,13 +254,122 @@ def measure_adjoint(qs, W, reps=2):
                 e, g = st.adjoint_grad(gates, th, flags)
                 ts.append(time.perf_counter() - t0)
             grads[label] = g
-            out[label] = {"s_per_gradient": min(ts), "grads_per_s": th.size / min(ts), "energy": e}
+            out[label] = {"s_per_gradient": round(min(ts), 5), "grads_per_s": round(th.size / min(ts), 1),
+                          "energy": e}
         finally:
             st.close()
-    out["max_abs_grad_diff_c64_vs_c128"] = float(np.max(np.abs(grads["c64"] - grads["c128_plain"])))
-    out["speedup_c64_vs_c128_plain"] = out["c128_plain"]["s_per_gradient"] / out["c64"]["s_per_gradient"]
+    for label in ("c64_fused", "c64_unfused"):
+        out[f"max_abs_grad_err_{label}_vs_c128"] = float(np.max(np.abs(grads[label] - grads["c128_plain"])))
+    out["speedup_c64_fused_vs_c128_plain"] = round(out["c128_plain"]["s_per_gradient"] /
+                                                   out["c64_fused"]["s_per_gradient"], 2)
     out["workload"] = "HEA n=24, 20 layers (RY,RZ per qubit + CNOT ladder), 960 params, observable sum Z_i"
     return out
+
+
+def measure_fused(qs, W):
+    """Fused tile passes: the 1000-gate scale circuit at n = 30 (complex64) and the ansatz at
+    n = 24, unfused vs fused (tile size from the autotuner), gates/s."""
+    import torch
+
+    from paper_2411_18354_gb300 import autotune
+
+    out = {}
+    n = 30
+    gates = W.scale_circuit(n, 1000, seed=1)
+    st = qs.State(n, "c64")
+    try:
+        t_unf = _events_ms(lambda: st.apply_circuit(gates, flags=qs.QS_FLAG_GRAPH), 1)
+        tb = autotune.tune_fused(n, "c64", gates, adjoint=False, candidates=(12, 13), use_cache=False, reps=1)
+        t_fus = _events_ms(lambda: st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH), 1)
+    finally:
+        st.close()
+        torch.cuda.empty_cache()
+    out["scale_circuit_n30_c64"] = {"gates": 1000, "unfused_gates_per_s": round(1000 / (t_unf * 1e-3), 1),
+                                    "fused_gates_per_s": round(1000 / (t_fus * 1e-3), 1),
+                                    "tile_bits": tb["tile_bits"]}
+    n, layers = 24, 20
+    g = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    st = qs.State(n, "c64")
+    try:
+        t_unf = _events_ms(lambda: st.apply_circuit(g, th), 3)
+        t_fus = _events_ms(lambda: st.apply_circuit(g, th, qs.QS_FLAG_FUSE), 3)
+    finally:
+        st.close()
+    out["ansatz_n24_c64"] = {"gates": int(len(g)), "unfused_ms": round(t_unf, 3), "fused_ms": round(t_fus, 3),
+                             "fused_gates_per_s": round(len(g) / (t_fus * 1e-3), 1)}
+    return out
+
+
+def measure_reduce(qs, W, peak):
+    """One-pass <Z_i> + norm at n = 30: read bytes / time."""
+    import torch
+
+    out = {}
+    for dtype, es in (("c64", 8), ("c128", 16)):
+        st = qs.State(30, dtype)
+        try:
+            st.apply_gate(0, W.H_MATRIX)
+            dz = torch.empty(30, dtype=torch.float64, device="cuda")
+            dn = torch.empty(1, dtype=torch.float64, device="cuda")
+            ms = _events_ms(lambda: qs.qs_expect_z(st.h, qs.QS_FLAG_OUT_DEVICE, dz.data_ptr(), dn.data_ptr()), 5)
+        finally:
+            st.close()
+            torch.cuda.empty_cache()
+        gbs = (1 << 30) * es / (ms * 1e-3) / 1e9
+        out[dtype] = {"ms": round(ms, 4), "GBps": round(gbs, 1), "frac_hbm": round(gbs / peak, 3)}
+    return out
+
+
+def measure_masked(qs, n, sched):
+    """The baseline schedule (all 2^(n-1) pairs, controls tested per pair) against the
+    reduced schedule, per control count: time ratio masked / reduced."""
+    import torch
+
+    st = qs.State(n, "c64")
+    out = {}
+    try:
+        for (c, t, m, v, U) in sched[0]:
+            tr = _events_ms(lambda: qs._lib.qs_apply_gate(st.h, t, m, v, U), 2)
+            tm = _events_ms(lambda: qs._lib.qs_apply_gate_masked(st.h, t, m, v, U), 2)
+            out.setdefault(str(c), []).append(tm / tr)
+    finally:
+        st.close()
+        torch.cuda.empty_cache()
+    return {c: round(sum(v) / len(v), 2) for c, v in out.items()}
+
+
+def measure_batch(qs, W):
+    """Batching workload: 4096 states, n uniform in 10..20, 8 ansatz layers, complex64: one
+    graph-launched persistent kernel for energies and gradients; settings from the autotuner."""
+    import numpy as np
+    import torch
+
+    from paper_2411_18354_gb300 import autotune
+
+    ns, thetas = W.batch_workload(4096, 10, 20, 8, seed=4)
+    ns = [int(v) for v in ns]
+    circ = {k: W.hea_circuit(k, 8) for k in set(ns)}
+    circuits = [circ[k] for k in ns]
+    nparams = [16 * k for k in ns]
+    cands = ({"small_bits": 12, "tile_bits": 12, "max_pass_gates": 64},
+             {"small_bits": 12, "tile_bits": 13, "max_pass_gates": 64},
+             {"small_bits": 11, "tile_bits": 12, "max_pass_gates": 64})
+    tuned = autotune.tune_batch(ns, circuits, nparams, thetas, "c64", candidates=cands, reps=1, use_cache=False)
+    cfg = {k: tuned[k] for k in ("small_bits", "tile_bits", "max_pass_gates")}
+    b = qs.Batch(ns, circuits, nparams, "c64", **cfg)
+    try:
+        th = torch.tensor(np.concatenate(thetas), dtype=torch.float64, device="cuda")
+        en = torch.empty(len(ns), dtype=torch.float64, device="cuda")
+        gr = torch.empty(b.num_params, dtype=torch.float64, device="cuda")
+        ms = _events_ms(lambda: b.run(th, en, gr, qs.QS_FLAG_GRAPH), 2)
+        info = b.info()
+    finally:
+        b.close()
+    return {"states": len(ns), "ms_per_launch": round(ms, 2), "states_per_s": round(len(ns) / (ms * 1e-3), 1),
+            "gradient_entries_per_s": round(sum(nparams) / (ms * 1e-3), 1), "config": cfg,
+            "grid": info["grid"], "smem_bytes": info["smem_bytes"],
+            "workload": "4096 states, n~U{10..20} (seed 4), HEA 8 layers, energies + adjoint gradients, complex64"}
 
 
 def cpu_oracle_sample(n_target: int, sched, max_gates=None):
@@ -337,15 +477,19 @@ def run_ours(args, rank, world, local_rank):
     value = world * args.steps * step_bytes / (total_ms * 1e-3) / 1e9
 
     # per-launch roofline of the gate kernel (algorithmic bytes / CUDA-event launch time)
-    launch_bytes = sum(alg_bytes(n, c, esize) for c, _, _ in per)
-    launch_ms = sum(ms for _, _, ms in per)
+    launch_bytes = sum(alg_bytes(n, c, esize) for c, _, _, _ in per)
+    launch_ms = sum(ms for _, _, ms, _ in per)
     achieved = launch_bytes / (launch_ms * 1e-3) / 1e9
+    sect_bytes = sum(sector_bytes(n, m, esize) for _, _, _, m in per)
     per_c = {}
     for c in range(CMAX + 1):
-        ms = [x for cc, _, x in per if cc == c]
+        rows = [(x, m) for cc, _, x, m in per if cc == c]
+        ms = [x for x, _ in rows]
         b = alg_bytes(n, c, esize) * len(ms)
+        sb = sum(sector_bytes(n, m, esize) for _, m in rows)
         gbs = b / (sum(ms) * 1e-3) / 1e9
-        per_c[str(c)] = {"ms_per_gate": statistics.mean(ms), "GBps": round(gbs, 1), "frac": round(gbs / peak, 3)}
+        per_c[str(c)] = {"ms_per_gate": round(statistics.mean(ms), 5), "GBps": round(gbs, 1), "frac": round(gbs / peak, 3),
+                         "frac_sector_adjusted": round(sb / (sum(ms) * 1e-3) / 1e9 / peak, 3)}
     traffic = profiled_traffic(n, "c64")
 
     result = {
@@ -358,7 +502,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (8.6 GB state)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_gate (qs_apply_gate)"},
+                     "kernel": "k_gate (qs_apply_gate)",
+                     "frac_sector_adjusted": round(sect_bytes / (launch_ms * 1e-3) / 1e9 / peak, 4)},
         "per_c": per_c,
         "gpu_launches": len(per),
         "clocks": clocks,
@@ -393,9 +538,9 @@ def run_ours(args, rank, world, local_rank):
         sm2, per2 = run_sweep(qs, st2, n, 16, sched, 1, 1)
         st2.close()
         torch.cuda.empty_cache()
-        b2 = sum(alg_bytes(n, c, 16) for c, _, _ in per2)
-        ms2 = sum(x for _, _, x in per2)
-        pairs = sum(1 << (n - 1 - c) for c, _, _ in per2)
+        b2 = sum(alg_bytes(n, c, 16) for c, _, _, _ in per2)
+        ms2 = sum(x for _, _, x, _ in per2)
+        pairs = sum(1 << (n - 1 - c) for c, _, _, _ in per2)
         flops = 28.0 * pairs  # general 2x2 complex update: 12 FMA + 4 MUL per pair, FMA = 2 flops
         result["c128_sweep"] = {
             "GBps": round(b2 / (ms2 * 1e-3) / 1e9, 1), "frac_hbm": round(b2 / (ms2 * 1e-3) / 1e9 / peak, 3),
@@ -404,6 +549,10 @@ def run_ours(args, rank, world, local_rank):
                          "frac": round(flops / (ms2 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)},
         }
         result["adjoint"] = measure_adjoint(qs, W)
+        result["fused"] = measure_fused(qs, W)
+        result["reduce_expect_z_n30"] = measure_reduce(qs, W, peak)
+        result["masked_over_reduced_time_by_c"] = measure_masked(qs, n, sched)
+        result["batch"] = measure_batch(qs, W)
         result["cpu_baseline"] = cpu_oracle_sample(n, sched)
 
     if rank == 0:
@@ -444,6 +593,19 @@ def run_ncu_fused(args):
     print("ncu fused case done")
 
 
+def run_ncu_reduce(args):
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+
+    qs.build()
+    with qs.State(27, args.dtype) as st:
+        st.expect_z()
+        st.expect_z()
+        torch.cuda.synchronize()
+    print("ncu reduce case done")
+
+
 def run_ncu_batch(args):
     import numpy as np
     import torch
@@ -474,6 +636,9 @@ def main():
         return
     if args.ncu_batch:
         run_ncu_batch(args)
+        return
+    if args.ncu_reduce:
+        run_ncu_reduce(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -3,11 +3,14 @@
 // Greedy, in execution order: a pass starts with the lowest b qubits local (b = 4 for
 // complex64, 3 for complex128, so that tile rows are 128 or 128 bytes of contiguous memory)
 // and takes the following gates while their targets fit in k local qubits. A gate's controls
-// need not be local: non-local controls become the gate's tile predicate. A gate joins only if
-// the pass's estimated traffic grows by less than the gate's own traffic as a separate
-// launch (fraction of tiles touched, union bound over the gates' tile predicates, against the
-// fraction of 64-byte DRAM units a separate launch touches). Runs of one gate stay separate
-// launches. The local set is finally padded with the lowest free qubits up to k.
+// need not be local: non-local controls become the gate's tile predicate. Costs are in units
+// of one full read + write of the state: a separate launch of a gate costs the fraction of
+// 64-byte DRAM units it touches; a pass costs the fraction of tiles it touches (union bound
+// over its gates' tile predicates) plus a per-gate compute cost inside the tile (measured:
+// about 0.15 for complex64, whose gates are memory-bound, and 0.6 for complex128, whose gates
+// are FP64-bound either way). A gate joins a pass only if that is cheaper than running it
+// alone, and a pass is kept only if it is cheaper than its gates run alone (unless every gate
+// must go into a pass). The local set is finally padded with the lowest free qubits up to k.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -215,6 +218,8 @@ static void make_pass(int n, uint64_t Lmask, TilePass *P) {
     P->ntiles = 1ull << (n - P->k);
 }
 
+static double pass_gate_cost(int dtype) { return dtype == QS_C64 ? 0.15 : 0.6; }
+
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
                 int max_gates, bool allow_single) {
@@ -233,7 +238,8 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     size_t i = 0;
     while (i < seq.size()) {
         uint64_t L = low;
-        double frac = 0.0;
+        double frac = 0.0, singles = 0.0;
+        const double cc = pass_gate_cost(dtype);
         int nparam = 0;
         std::vector<int> members;
         size_t j = i;
@@ -252,8 +258,9 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             const double frac2 = std::min(1.0, frac + f);
             int real = 0;
             for (int mbr : members) real += mbr >= 0;
-            if (real > 0 && frac2 > frac + single_fraction(p, dtype)) break;
+            if (real > 0 && allow_single && frac2 + cc > frac + single_fraction(p, dtype)) break;
             frac = frac2;
+            singles += single_fraction(p, dtype);
             L = L2;
             members.push_back(seq[j]);
             nparam += param;
@@ -265,7 +272,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             i = std::max(j, i + 1);
             continue;
         }
-        if (real < 2 && allow_single) {  // not worth a pass: the first gate runs alone
+        if (allow_single && (real < 2 || frac + cc * real >= singles)) {  // not worth a pass: the first gate runs alone
             const int g = seq[i];
             const bool param = adjoint && (*dus)[g] != nullptr;
             if (plans[g].units != 0 || param) prog->ops.push_back({-1, g});
