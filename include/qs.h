@@ -162,8 +162,9 @@ int qs_get_tile_bits(qs_dtype dtype, int adjoint);
 
 /* out[i] = <Z_i> = sum_k |psi_k|^2 (1 - 2 bit_i(k)) for i = 0..n-1, and, if out_norm2 is
  * not NULL, *out_norm2 = sum_k |psi_k|^2 -- all in one pass over the state. Complex64
- * states sum |psi_k|^2 in float32 over runs of at most 32 amplitudes per thread and 1024
- * per warp, and in float64 above that; complex128 states sum in float64 throughout.
+ * states sum |psi_k|^2 in float32 within a tile of 8192 amplitudes, with a compensated
+ * (Kahan) float32 running sum over a block's tiles and float64 across blocks; complex128
+ * states sum in float64 throughout. Deterministic (fixed summation order).
  * With QS_FLAG_OUT_DEVICE in flags, out / out_norm2 are device pointers and the call is
  * asynchronous; otherwise they are host pointers and the call synchronises the stream. */
 qs_status qs_expect_z(const qs_state *s, double *out, double *out_norm2, int flags);

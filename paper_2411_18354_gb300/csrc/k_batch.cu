@@ -37,14 +37,15 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 
 // lambda = O psi and E = <psi|O|psi> over amplitudes [0, N) of `src`, written to `dst`
 // (both in shared memory with the tile swizzle `sw`, or both in global memory, sw = 0).
-// Partial sums: float over runs of at most 32 amplitudes per thread, float64 above.
+// Partial sums: per thread in the state's precision (compensated for complex64), float64
+// across threads.
 template <typename Real>
 __device__ __forceinline__ double obs_pass(const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst, int n,
                                            double *red, int sw) {
     using T2 = typename TileT<Real>::T2;
     constexpr int U = 4;  // independent loads in flight per thread
     const uint64_t N = 1ull << n;
-    double acc = 0.0;
+    Acc<Real> acc{};
     for (uint64_t k0 = threadIdx.x; k0 < N; k0 += (uint64_t)U * blockDim.x) {
         T2 v[U];
         uint64_t pos[U];
@@ -66,15 +67,15 @@ __device__ __forceinline__ double obs_pass(const typename TileT<Real>::T2 *src, 
                 dst[pos[u]] = v[u];
             }
         }
-        acc += (double)run;
+        acc.add(run);
     }
-    return block_sum<Real>(acc, red);
+    return block_sum<Real>(acc.value(), red);
 }
 
 template <typename Real>
 __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool adjoint, typename TileT<Real>::T2 *psi,
                                    typename TileT<Real>::T2 *lam, typename TileT<Real>::T2 *tp,
-                                   typename TileT<Real>::T2 *tl, const Real *cs, double *gacc, TileGroup *sgroups,
+                                   typename TileT<Real>::T2 *tl, const Real *cs, Acc<Real> *gacc, TileGroup *sgroups,
                                    SGate<Real> *sgates) {
     const int begin = adjoint ? pg.adj_begin : pg.fwd_begin;
     const int count = adjoint ? pg.adj_count : pg.fwd_count;
@@ -112,8 +113,8 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
     T2 *tl = tp + T;
     Real *cs = reinterpret_cast<Real *>(tl + T);                                   // [2 * max_params]
-    double *gacc = reinterpret_cast<double *>(cs + 2 * ((a.max_params + 1) & ~1));  // [max_params * nwarps]
-    double *red = gacc + (size_t)a.max_params * (kBatchThreads / 32);              // [nwarps]
+    Acc<Real> *gacc = reinterpret_cast<Acc<Real> *>(cs + 2 * ((a.max_params + 1) & ~1));  // [max_params * nwarps]
+    double *red = reinterpret_cast<double *>(gacc + (size_t)a.max_params * (kBatchThreads / 32));  // [nwarps]
     TileGroup *sgroups = reinterpret_cast<TileGroup *>(red + kBatchThreads / 32);
     SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
     int *next = reinterpret_cast<int *>(sgates + kTileMaxGates);
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
             cs[2 * p] = (Real)c;
             cs[2 * p + 1] = (Real)s;
         }
-        for (int i = tid; i < st.nparam * nwarps; i += kBatchThreads) gacc[i] = 0.0;
+        for (int i = tid; i < st.nparam * nwarps; i += kBatchThreads) gacc[i] = Acc<Real>{};
         double energy;
         if (pg.small) {
             const uint32_t N = 1u << n;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
         if (tid == 0) a.energy[a.order[qi]] = energy;
         for (int p = tid; p < st.nparam; p += kBatchThreads) {
             double s = 0.0;
-            for (int w = 0; w < nwarps; ++w) s += gacc[p * nwarps + w];
+            for (int w = 0; w < nwarps; ++w) s += gacc[p * nwarps + w].value();
             a.grad[st.param_off + p] = 2.0 * s;
         }
         __syncthreads();

@@ -119,6 +119,26 @@ __device__ __forceinline__ void pair_update(T2 &x, T2 &y, const Real *m) {
     }
 }
 
+// Running sum in the state's precision, 8 bytes either way: float64 for complex128; for
+// complex64 a float sum with its compensation term (Kahan), because float64 arithmetic runs
+// at a small fraction of the float32 rate on this GPU. All-zero bits = 0.
+template <typename Real> struct Acc;
+template <> struct Acc<double> {
+    double s;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s, c;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 constexpr int kGateThreads = 256;
 
 template <int R> struct Log2;

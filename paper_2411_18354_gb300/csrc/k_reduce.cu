@@ -10,14 +10,15 @@
 //  - warp shuffles reduce the per-thread sums and form the lane-bit sums;
 //  - warp totals give the warp-bit sums; bits at or above TB are constant per tile and
 //    take the tile total when set;
-//  - thread b of the block owns output b and accumulates it in float64 over the block's
-//    tiles; a final one-block pass adds the per-block results in a fixed order.
-// Complex64: per-thread and per-warp sums are float32 (at most 32 and 1024 terms),
-// everything above is float64. Complex128: float64 everywhere. The result does not depend
-// on scheduling (fixed tile-to-block assignment and fixed summation order).
+//  - thread b of the block owns output b and accumulates it over the block's tiles; a final
+//    one-block pass adds the per-block results in float64 in a fixed order.
+// Complex64: per-thread, per-warp and per-tile sums are float32 (at most 32, 1024 and 8192
+// terms), the running sum over a block's tiles is a compensated (Kahan) float32 sum, and the
+// sum over blocks is float64. Complex128: float64 everywhere. The result does not depend on
+// scheduling (fixed tile-to-block assignment and fixed summation order).
 #include <algorithm>
 
-#include "qs_internal.cuh"
+#include "k_gate.cuh"
 
 namespace qs {
 namespace {
@@ -55,7 +56,7 @@ k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t nt
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    double acc = 0.0;
+    Acc<Real> acc{};  // output `tid` of this block, over its tiles
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         A tot = 0, sv = 0, sj[4] = {0, 0, 0, 0};
         if (VB == 1) {
@@ -115,27 +116,27 @@ k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t nt
         __syncthreads();
         if (tid <= n) {
             // output tid: tid == n -> total; else S_tid (sum over amplitudes with bit tid set)
-            double v = 0.0;
+            A v = 0;
             const int b = tid;
             if (b == n) {
-                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][0];
+                for (int w = 0; w < kRedThreads / 32; ++w) v += wpart[w][0];
             } else if (b < VB) {
-                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][1];
+                for (int w = 0; w < kRedThreads / 32; ++w) v += wpart[w][1];
             } else if (b < VB + 5) {
-                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][5 + VB + (b - VB)];
+                for (int w = 0; w < kRedThreads / 32; ++w) v += wpart[w][5 + VB + (b - VB)];
             } else if (b < VB + 8) {
                 for (int w = 0; w < kRedThreads / 32; ++w)
-                    if ((w >> (b - VB - 5)) & 1) v += (double)wpart[w][0];
+                    if ((w >> (b - VB - 5)) & 1) v += wpart[w][0];
             } else if (b < TB) {
-                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][1 + VB + (b - VB - 8)];
+                for (int w = 0; w < kRedThreads / 32; ++w) v += wpart[w][1 + VB + (b - VB - 8)];
             } else if ((tile >> (b - TB)) & 1ull) {
-                for (int w = 0; w < kRedThreads / 32; ++w) v += (double)wpart[w][0];
+                for (int w = 0; w < kRedThreads / 32; ++w) v += wpart[w][0];
             }
-            acc += v;
+            acc.add(v);
         }
         __syncthreads();
     }
-    if (tid <= n) partials[(size_t)blockIdx.x * (n + 1) + tid] = acc;
+    if (tid <= n) partials[(size_t)blockIdx.x * (n + 1) + tid] = acc.value();
 }
 
 // Fixed-order sum of the per-block partials; one block.

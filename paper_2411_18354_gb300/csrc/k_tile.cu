@@ -18,12 +18,12 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
     const uint32_t T = 1u << P.k;
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
     T2 *tl = tp + T;  // adjoint: lambda tile
-    double *acc = reinterpret_cast<double *>(smem_raw + (ADJ ? 2 : 1) * (size_t)T * sizeof(T2));  // [kTileMaxParam][8]
+    Acc<Real> *acc = reinterpret_cast<Acc<Real> *>(smem_raw + (ADJ ? 2 : 1) * (size_t)T * sizeof(T2));  // [kTileMaxParam][8]
     TileGroup *sgroups = reinterpret_cast<TileGroup *>(acc + (ADJ ? kTileMaxParam * (kTileThreads / 32) : 0));
     SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
     const int tid = threadIdx.x;
     if (ADJ)
-        for (int i = tid; i < kTileMaxParam * (kTileThreads / 32); i += kTileThreads) acc[i] = 0.0;
+        for (int i = tid; i < kTileMaxParam * (kTileThreads / 32); i += kTileThreads) acc[i] = Acc<Real>{};
     stage_pass<Real>(P, groups, gates, sgroups, sgates);
     const SGate<Real> *G0 = sgates;
     for (uint64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
@@ -45,7 +45,7 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
         __syncthreads();
         for (int p = tid; p < P.nparam; p += kTileThreads) {
             double s = 0.0;
-            for (int w = 0; w < kTileThreads / 32; ++w) s += acc[p * (kTileThreads / 32) + w];
+            for (int w = 0; w < kTileThreads / 32; ++w) s += acc[p * (kTileThreads / 32) + w].value();
             part[(size_t)P.param_gslot[p] * part_stride + blockIdx.x] = s;
         }
     }

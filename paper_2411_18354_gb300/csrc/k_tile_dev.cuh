@@ -219,12 +219,12 @@ template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
 
 // Apply the pass's register groups to the tile tp (and lambda tile tl if ADJ) whose global
 // base index is `base`. Adjoint: for a gate with slot >= 0 the warp partial of
-// Re <lambda| dU psi> is added to acc[slot * nwarps + warp] (float64). Every executed group
-// ends with a block barrier.
+// Re <lambda| dU psi> (summed over the warp in the state's precision) is added to
+// acc[slot * nwarps + warp]. Every executed group ends with a block barrier.
 template <typename Real, bool ADJ>
 __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
                                              int k, const TileGroup *groups, int group_count, const SGate<Real> *gates,
-                                             const Real *cs, double *acc) {
+                                             const Real *cs, Acc<Real> *acc) {
     using T2 = typename TileT<Real>::T2;
     constexpr int SW = TileT<Real>::SW;
     constexpr int GB = GroupBits<ADJ>::v;
@@ -274,10 +274,10 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                 Real dot = 0;
                 row_gate<ADJ, GB, T2, Real>(v, w, R, row_ok, dot);
                 if (ADJ && R.slot >= 0) {
-                    double d = (double)dot;
+                    Real d = dot;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                    if (lane == 0) acc[R.slot * nwarps + warp] += d;
+                    if (lane == 0) acc[R.slot * nwarps + warp].add(d);
                 }
             }
 #pragma unroll
