@@ -76,12 +76,17 @@ template <typename Real>
 __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool adjoint, typename TileT<Real>::T2 *psi,
                                    typename TileT<Real>::T2 *lam, typename TileT<Real>::T2 *tp,
                                    typename TileT<Real>::T2 *tl, const Real *cs, Acc<Real> *gacc, TileGroup *sgroups,
-                                   SGate<Real> *sgates) {
+                                   SGate<Real> *sgates, TilePass *spass, uint64_t *g_j, uint32_t *s_j) {
     const int begin = adjoint ? pg.adj_begin : pg.fwd_begin;
     const int count = adjoint ? pg.adj_count : pg.fwd_count;
     for (int pi = begin; pi < begin + count; ++pi) {
-        const TilePass &P = a.passes[pi];
+        // the pass descriptor, its gates and the tile address tables go to shared memory
+        for (int i = threadIdx.x; i < (int)(sizeof(TilePass) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t *>(spass)[i] = reinterpret_cast<const uint32_t *>(a.passes + pi)[i];
+        __syncthreads();
+        const TilePass &P = *spass;
         stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+        const TileAddr ta = tile_addr<Real>(P, g_j, s_j);
         const SGate<Real> *G0 = sgates;
         for (uint64_t tau = 0; tau < P.ntiles; ++tau) {
             const uint64_t base = tile_base(P, tau);
@@ -90,15 +95,15 @@ __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool
                 for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
                 if (!any) continue;
             }
-            load_tile<Real>(P, base, psi, tp);
-            if (adjoint) load_tile<Real>(P, base, lam, tl);
+            load_tile<Real>(ta, g_j, s_j, base, psi, tp);
+            if (adjoint) load_tile<Real>(ta, g_j, s_j, base, lam, tl);
             __syncthreads();
             if (adjoint)
-                apply_groups<Real, true>(tp, tl, base, P.k, sgroups, P.group_count, sgates, cs, gacc);
+                apply_groups<Real, true, kGroupBitsAdjoint>(tp, tl, base, P.k, sgroups, P.group_count, sgates, cs, gacc);
             else
-                apply_groups<Real, false>(tp, nullptr, base, P.k, sgroups, P.group_count, sgates, cs, nullptr);
-            store_tile<Real>(P, base, tp, psi);
-            if (adjoint) store_tile<Real>(P, base, tl, lam);
+                apply_groups<Real, false, kGroupBitsAdjoint>(tp, nullptr, base, P.k, sgroups, P.group_count, sgates, cs, nullptr);
+            store_tile<Real>(ta, g_j, s_j, base, tp, psi);
+            if (adjoint) store_tile<Real>(ta, g_j, s_j, base, tl, lam);
             __syncthreads();
         }
         __syncthreads();  // the next pass restages the gate table
@@ -117,7 +122,10 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
     double *red = reinterpret_cast<double *>(gacc + (size_t)a.max_params * (kBatchThreads / 32));  // [nwarps]
     TileGroup *sgroups = reinterpret_cast<TileGroup *>(red + kBatchThreads / 32);
     SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
-    int *next = reinterpret_cast<int *>(sgates + kTileMaxGates);
+    TilePass *spass = reinterpret_cast<TilePass *>(sgates + kTileMaxGates);
+    uint64_t *g_j = reinterpret_cast<uint64_t *>(spass + 1);
+    uint32_t *s_j = reinterpret_cast<uint32_t *>(g_j + kTileMaxSteps);
+    int *next = reinterpret_cast<int *>(s_j + kTileMaxSteps);
     const int tid = threadIdx.x;
     const int nwarps = kBatchThreads / 32;
     T2 *ws_psi = reinterpret_cast<T2 *>(a.workspace) + (size_t)blockIdx.x * 2 * a.ws_stride;
@@ -147,23 +155,23 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
             for (int pi = pg.fwd_begin; pi < pg.fwd_begin + pg.fwd_count; ++pi) {
                 const TilePass &P = a.passes[pi];
                 stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
-                apply_groups<Real, false>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
+                apply_groups<Real, false, kGroupBitsAdjoint>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
                 __syncthreads();
             }
             energy = obs_pass<Real>(tp, tl, n, red, TileT<Real>::SW);
             for (int pi = pg.adj_begin; pi < pg.adj_begin + pg.adj_count; ++pi) {
                 const TilePass &P = a.passes[pi];
                 stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
-                apply_groups<Real, true>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
+                apply_groups<Real, true, kGroupBitsAdjoint>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
                 __syncthreads();
             }
         } else {
             const uint64_t N = 1ull << n;
             for (uint64_t k = tid; k < N; k += kBatchThreads) ws_psi[k] = T2{(Real)(k == 0), (Real)0};
             __syncthreads();
-            run_program_global<Real>(a, pg, false, ws_psi, ws_lam, tp, tl, cs, nullptr, sgroups, sgates);
+            run_program_global<Real>(a, pg, false, ws_psi, ws_lam, tp, tl, cs, nullptr, sgroups, sgates, spass, g_j, s_j);
             energy = obs_pass<Real>(ws_psi, ws_lam, n, red, 0);
-            run_program_global<Real>(a, pg, true, ws_psi, ws_lam, tp, tl, cs, gacc, sgroups, sgates);
+            run_program_global<Real>(a, pg, true, ws_psi, ws_lam, tp, tl, cs, gacc, sgroups, sgates, spass, g_j, s_j);
         }
         __syncthreads();
         if (tid == 0) a.energy[a.order[qi]] = energy;
@@ -184,7 +192,7 @@ size_t batch_smem_bytes(int dtype, int smem_bits, int max_params) {
     const size_t sg = dtype == QS_C64 ? sizeof(SGate<float>) : sizeof(SGate<double>);
     return 2 * (size_t(1) << smem_bits) * es + 2 * (size_t)((max_params + 1) & ~1) * rs +
            (size_t)max_params * (kBatchThreads / 32) * sizeof(double) + (kBatchThreads / 32) * sizeof(double) +
-           kTileMaxGates * (sizeof(TileGroup) + sg) + 16;
+           kTileMaxGates * (sizeof(TileGroup) + sg) + sizeof(TilePass) + kTileMaxSteps * (sizeof(uint64_t) + 4) + 16;
 }
 
 int batch_grid(int dtype, size_t smem) {

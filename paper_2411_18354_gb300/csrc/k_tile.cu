@@ -21,10 +21,13 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
     Acc<Real> *acc = reinterpret_cast<Acc<Real> *>(smem_raw + (ADJ ? 2 : 1) * (size_t)T * sizeof(T2));  // [kTileMaxParam][8]
     TileGroup *sgroups = reinterpret_cast<TileGroup *>(acc + (ADJ ? kTileMaxParam * (kTileThreads / 32) : 0));
     SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
+    uint64_t *g_j = reinterpret_cast<uint64_t *>(sgates + kTileMaxGates);
+    uint32_t *s_j = reinterpret_cast<uint32_t *>(g_j + kTileMaxSteps);
     const int tid = threadIdx.x;
     if (ADJ)
         for (int i = tid; i < kTileMaxParam * (kTileThreads / 32); i += kTileThreads) acc[i] = Acc<Real>{};
     stage_pass<Real>(P, groups, gates, sgroups, sgates);
+    const TileAddr ta = tile_addr<Real>(P, g_j, s_j);
     const SGate<Real> *G0 = sgates;
     for (uint64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
         const uint64_t base = tile_base(P, tau);
@@ -33,12 +36,12 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
             for (int g = 0; g < P.gate_count; ++g) any |= ((base & G0[g].hmask) == G0[g].hvals);
             if (!any) continue;  // no gate of the pass selects this tile
         }
-        load_tile<Real>(P, base, psi, tp);
-        if (ADJ) load_tile<Real>(P, base, lam, tl);
+        load_tile<Real>(ta, g_j, s_j, base, psi, tp);
+        if (ADJ) load_tile<Real>(ta, g_j, s_j, base, lam, tl);
         __syncthreads();
         apply_groups<Real, ADJ>(tp, tl, base, P.k, sgroups, P.group_count, sgates, nullptr, acc);
-        store_tile<Real>(P, base, tp, psi);
-        if (ADJ) store_tile<Real>(P, base, tl, lam);
+        store_tile<Real>(ta, g_j, s_j, base, tp, psi);
+        if (ADJ) store_tile<Real>(ta, g_j, s_j, base, tl, lam);
         __syncthreads();
     }
     if (ADJ) {
@@ -79,7 +82,7 @@ size_t tile_smem_bytes(int dtype, int k, bool adjoint) {
     const size_t es = dtype == QS_C64 ? 8 : 16;
     const size_t sg = dtype == QS_C64 ? sizeof(SGate<float>) : sizeof(SGate<double>);
     return (adjoint ? 2 : 1) * (size_t(1) << k) * es + (adjoint ? kTileMaxParam * (kTileThreads / 32) * sizeof(double) : 0) +
-           kTileMaxGates * (sizeof(TileGroup) + sg);
+           kTileMaxGates * (sizeof(TileGroup) + sg) + kTileMaxSteps * (sizeof(uint64_t) + sizeof(uint32_t));
 }
 
 cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,

@@ -221,13 +221,12 @@ template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
 // base index is `base`. Adjoint: for a gate with slot >= 0 the warp partial of
 // Re <lambda| dU psi> (summed over the warp in the state's precision) is added to
 // acc[slot * nwarps + warp]. Every executed group ends with a block barrier.
-template <typename Real, bool ADJ>
+template <typename Real, bool ADJ, int GB = GroupBits<ADJ>::v>
 __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
                                              int k, const TileGroup *groups, int group_count, const SGate<Real> *gates,
                                              const Real *cs, Acc<Real> *acc) {
     using T2 = typename TileT<Real>::T2;
     constexpr int SW = TileT<Real>::SW;
-    constexpr int GB = GroupBits<ADJ>::v;
     constexpr int E = 1 << GB;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int gi = 0; gi < group_count; ++gi) {
@@ -310,50 +309,72 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Element o = VEC * (tid + j * blockDim) + i of a tile: both its global offset (a bit deposit)
-// and its shared-memory position (the swizzle) are XOR-linear over disjoint bit fields, so
-// they split into a per-thread part, a per-step part and a per-element part.
+// Address tables of a pass's tile copies. Element o = VEC * (tid + j * blockDim) + i of a tile:
+// both its global offset (a bit deposit) and its shared-memory position (the swizzle) are
+// XOR-linear over disjoint bit fields, so they split into a per-thread part (registers), a
+// per-step part (a small shared table, the same for all threads) and the element bit i.
+constexpr int kTileMaxSteps = (1 << kTileMaxBits) / kTileThreads;  // 64
+
+struct TileAddr {
+    uint64_t g_t;   // this thread's part of the global offset
+    uint32_t s_t;   // this thread's part of the shared-memory position
+    uint32_t s_1;   // position offset of element bit i = 1 (complex64 pairs)
+    uint32_t steps; // blockDim-strided steps that cover the tile (0 for threads past a small tile)
+};
+
+// Fills the per-step tables g_j / s_j (shared, kTileMaxSteps entries) and returns the thread's
+// part. Ends with a block barrier.
 template <typename Real>
-__device__ __forceinline__ void load_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
-                                          typename TileT<Real>::T2 *dst) {
+__device__ __forceinline__ TileAddr tile_addr(const TilePass &P, uint64_t *g_j, uint32_t *s_j) {
     constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
     const uint32_t nvec = (1u << P.k) / VEC;
+    TileAddr a;
     const uint32_t o_t = threadIdx.x * VEC;
-    const uint64_t g_t = base | scatter_local(P, o_t);
-    const uint32_t s_t = tile_swizzle(o_t, SW);
-    const uint32_t s_1 = tile_swizzle(1u, SW);
-    for (uint32_t v0 = 0; v0 + threadIdx.x < nvec; v0 += blockDim.x) {
-        const uint32_t o_j = v0 * VEC;  // disjoint from o_t: blockDim * VEC is a power of two
-        const typename TileT<Real>::T2 *g = src + (g_t | scatter_local(P, o_j));
-        const uint32_t s = s_t ^ tile_swizzle(o_j, SW);
-#pragma unroll
-        for (int i = 0; i < VEC; ++i) {
-            if (sizeof(Real) == 4) cp_async_8(dst + (i ? (s ^ s_1) : s), g + i);
-            else cp_async_16(dst + s, g);
+    a.g_t = scatter_local(P, o_t);
+    a.s_t = tile_swizzle(o_t, SW);
+    a.s_1 = tile_swizzle(1u, SW);
+    a.steps = threadIdx.x < nvec ? (nvec + blockDim.x - 1) / blockDim.x : 0u;
+    const uint32_t nsteps = (nvec + blockDim.x - 1) / blockDim.x;
+    for (uint32_t j = threadIdx.x; j < nsteps; j += blockDim.x) {
+        const uint32_t o_j = j * blockDim.x * VEC;  // disjoint from o_t: blockDim * VEC is a power of two
+        g_j[j] = scatter_local(P, o_j);
+        s_j[j] = tile_swizzle(o_j, SW);
+    }
+    __syncthreads();
+    return a;
+}
+
+template <typename Real>
+__device__ __forceinline__ void load_tile(const TileAddr &ta, const uint64_t *g_j, const uint32_t *s_j, uint64_t base,
+                                          const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst) {
+    const uint64_t g0 = base | ta.g_t;
+    for (uint32_t j = 0; j < ta.steps; ++j) {
+        const typename TileT<Real>::T2 *g = src + (g0 | g_j[j]);
+        const uint32_t s = ta.s_t ^ s_j[j];
+        if (sizeof(Real) == 4) {
+            cp_async_8(dst + s, g);
+            cp_async_8(dst + (s ^ ta.s_1), g + 1);
+        } else {
+            cp_async_16(dst + s, g);
         }
     }
     cp_async_wait_all();
 }
 
 template <typename Real>
-__device__ __forceinline__ void store_tile(const TilePass &P, uint64_t base, const typename TileT<Real>::T2 *src,
-                                           typename TileT<Real>::T2 *dst) {
+__device__ __forceinline__ void store_tile(const TileAddr &ta, const uint64_t *g_j, const uint32_t *s_j, uint64_t base,
+                                           const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst) {
     using V = typename TileT<Real>::V;
     using T2 = typename TileT<Real>::T2;
-    constexpr int VEC = TileT<Real>::VEC, SW = TileT<Real>::SW;
-    const uint32_t nvec = (1u << P.k) / VEC;
-    const uint32_t o_t = threadIdx.x * VEC;
-    const uint64_t g_t = base | scatter_local(P, o_t);
-    const uint32_t s_t = tile_swizzle(o_t, SW);
-    const uint32_t s_1 = tile_swizzle(1u, SW);
-    for (uint32_t v0 = 0; v0 + threadIdx.x < nvec; v0 += blockDim.x) {
-        const uint32_t o_j = v0 * VEC;
-        const uint32_t s = s_t ^ tile_swizzle(o_j, SW);
+    constexpr int VEC = TileT<Real>::VEC;
+    const uint64_t g0 = base | ta.g_t;
+    for (uint32_t j = 0; j < ta.steps; ++j) {
+        const uint32_t s = ta.s_t ^ s_j[j];
         V x;
         T2 *xs = reinterpret_cast<T2 *>(&x);
-#pragma unroll
-        for (int i = 0; i < VEC; ++i) xs[i] = src[i ? (s ^ s_1) : s];
-        *reinterpret_cast<V *>(dst + (g_t | scatter_local(P, o_j))) = x;
+        xs[0] = src[s];
+        if (VEC == 2) xs[VEC - 1] = src[s ^ ta.s_1];
+        *reinterpret_cast<V *>(dst + (g0 | g_j[j])) = x;
     }
 }
 

@@ -196,9 +196,10 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
             std::vector<int> seq(gc);
             std::iota(seq.begin(), seq.end(), 0);
             FusedProgram pf, pa;
-            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false);
+            // the batch kernel runs both directions with kGroupBitsAdjoint-qubit register groups
+            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false, kGroupBitsAdjoint);
             std::reverse(seq.begin(), seq.end());
-            plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa, max_pass_gates, false);
+            plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa, max_pass_gates, false, kGroupBitsAdjoint);
             BatchProg bp{};
             bp.small = small;
             bp.n = n;

@@ -222,7 +222,7 @@ static double pass_gate_cost(int dtype) { return dtype == QS_C64 ? 0.15 : 0.6; }
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates, bool allow_single) {
+                int max_gates, bool allow_single, int group_bits) {
     prog->ops.clear();
     prog->passes.clear();
     prog->gates.clear();
@@ -304,7 +304,8 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             ds.push_back(d);
             src.push_back(mbr);
         }
-        add_groups(lg, slots, ds, src, P.k, dtype, adjoint ? kGroupBitsAdjoint : kGroupBits, prog, &P);
+        add_groups(lg, slots, ds, src, P.k, dtype, group_bits > 0 ? group_bits : (adjoint ? kGroupBitsAdjoint : kGroupBits),
+                   prog, &P);
         prog->ops.push_back({(int)prog->passes.size(), -1});
         prog->passes.push_back(P);
         i = j;

@@ -34,7 +34,8 @@ const RegGate *table_gates(const FusedProgram &p, const void *dev_base);
 // goes into a pass, also when the pass holds only that gate.
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates = kTileMaxGates, bool allow_single = true);
-// (the group size is kGroupBits for forward programs, kGroupBitsAdjoint when dus != nullptr)
+                int max_gates = kTileMaxGates, bool allow_single = true, int group_bits = 0);
+// group_bits: register qubits per group; 0 = kGroupBits for forward programs and
+// kGroupBitsAdjoint when dus != nullptr. The kernel that runs the program must use the same.
 
 }  // namespace qs
