@@ -85,7 +85,7 @@ __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool
             reinterpret_cast<uint32_t *>(spass)[i] = reinterpret_cast<const uint32_t *>(a.passes + pi)[i];
         __syncthreads();
         const TilePass &P = *spass;
-        stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+        stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates, cs, adjoint);
         const TileAddr ta = tile_addr<Real>(P, g_j, s_j);
         const SGate<Real> *G0 = sgates;
         for (uint64_t tau = 0; tau < P.ntiles; ++tau) {
@@ -154,14 +154,14 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
             __syncthreads();
             for (int pi = pg.fwd_begin; pi < pg.fwd_begin + pg.fwd_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates, cs, false);
                 apply_groups<Real, false, kGroupBitsAdjoint>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
                 __syncthreads();
             }
             energy = obs_pass<Real>(tp, tl, n, red, TileT<Real>::SW);
             for (int pi = pg.adj_begin; pi < pg.adj_begin + pg.adj_count; ++pi) {
                 const TilePass &P = a.passes[pi];
-                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates);
+                stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates, cs, true);
                 apply_groups<Real, true, kGroupBitsAdjoint>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
                 __syncthreads();
             }

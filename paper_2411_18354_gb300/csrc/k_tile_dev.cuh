@@ -35,11 +35,16 @@ template <typename Real> struct SGate {
     int8_t p, cqm, cqv, op, side, pkind;
     int16_t slot;
     int32_t pidx;
+    int32_t code;  // dispatch code: (op * 4 + p) * 2 + (cqm != 0)
+    int32_t pad;
     Real u[8], d[8];
 };
 
 template <typename Real>
-__device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S) {
+__device__ __forceinline__ void param_matrices(int kind, Real c, Real s, bool adjoint, Real *u, Real *d);
+
+template <typename Real>
+__device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S, const Real *cs, bool adjoint) {
     S.hmask = G.hmask;
     S.hvals = G.hvals;
     S.crm = G.crm;
@@ -52,12 +57,19 @@ __device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S) {
     S.pkind = (int8_t)G.pkind;
     S.slot = (int16_t)G.slot;
     S.pidx = G.pidx;
-    const Real *u = TileT<Real>::U(G);
-    const Real *d = TileT<Real>::D(G);
+    S.code = (G.op * 4 + G.p) * 2 + (G.cqm != 0);
+    S.pad = 0;
+    if (G.pkind != 0 && cs) {  // the state's parameter: matrices built once per pass
+        param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, S.u, S.d);
+        S.pkind = 0;
+    } else {
+        const Real *u = TileT<Real>::U(G);
+        const Real *d = TileT<Real>::D(G);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        S.u[i] = u[i];
-        S.d[i] = d[i];
+        for (int i = 0; i < 8; ++i) {
+            S.u[i] = u[i];
+            S.d[i] = d[i];
+        }
     }
 }
 
@@ -65,20 +77,22 @@ __device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S) {
 // Ends with a block barrier.
 template <typename Real>
 __device__ __forceinline__ void stage_pass(const TilePass &P, const TileGroup *groups, const RegGate *gates,
-                                           TileGroup *sgroups, SGate<Real> *sgates) {
+                                           TileGroup *sgroups, SGate<Real> *sgates, const Real *cs = nullptr,
+                                           bool adjoint = false) {
     for (int i = threadIdx.x; i < P.group_count; i += blockDim.x) {
         TileGroup g = groups[P.group_begin + i];
         g.gate_begin -= P.gate_begin;
         sgroups[i] = g;
     }
-    for (int i = threadIdx.x; i < P.gate_count; i += blockDim.x) stage_gate<Real>(gates[P.gate_begin + i], sgates[i]);
+    for (int i = threadIdx.x; i < P.gate_count; i += blockDim.x)
+        stage_gate<Real>(gates[P.gate_begin + i], sgates[i], cs, adjoint);
     __syncthreads();
 }
 
 // Gate fields kept in registers while a row is processed.
 template <typename Real> struct GateRegs {
     uint32_t crm, crv;
-    int p, cqm, cqv, op, side, slot;
+    int p, cqm, cqv, op, side, slot, code;
     Real u[8], d[8];
 };
 
@@ -125,6 +139,7 @@ __device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &
     r.op = G.op;
     r.side = G.side;
     r.slot = G.slot;
+    r.code = G.code;
     if (G.pkind != 0 && cs) {
         param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, r.u, r.d);
     } else {
@@ -186,31 +201,27 @@ __device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R,
     }
 }
 
-template <int OP, bool ADJ, int GB, bool CQ, typename T2, typename Real>
-__device__ __forceinline__ void row_gate_p(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
-    switch (R.p) {
-        case 0: row_pairs<0, OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
-        case 1: if (GB > 1) row_pairs<(GB > 1 ? 1 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
-        case 2: if (GB > 2) row_pairs<(GB > 2 ? 2 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
-        default: if (GB > 3) row_pairs<(GB > 3 ? 3 : 0), OP, ADJ, GB, CQ, T2, Real>(v, w, R, row_ok, dot); break;
-    }
-}
-
-template <int OP, bool ADJ, int GB, typename T2, typename Real>
-__device__ __forceinline__ void row_gate_op(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
-    if (R.cqm) row_gate_p<OP, ADJ, GB, true, T2, Real>(v, w, R, row_ok, dot);
-    else row_gate_p<OP, ADJ, GB, false, T2, Real>(v, w, R, row_ok, dot);
-}
-
+// One switch on the staged dispatch code selects (operation, target place, in-row controls).
 template <bool ADJ, int GB, typename T2, typename Real>
 __device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
-    switch (R.op) {
-        case OP_GEN: row_gate_op<OP_GEN, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
-        case OP_REAL: row_gate_op<OP_REAL, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
-        case OP_DIAG: row_gate_op<OP_DIAG, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
-        case OP_SWAP: row_gate_op<OP_SWAP, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
-        default: row_gate_op<OP_SIDE, ADJ, GB, T2, Real>(v, w, R, row_ok, dot); break;
+#define QS_ROW(OP, P)                                                                                    \
+    case ((OP)*4 + (P)) * 2 + 0:                                                                         \
+        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, false, T2, Real>(v, w, R, row_ok, dot); \
+        break;                                                                                           \
+    case ((OP)*4 + (P)) * 2 + 1:                                                                         \
+        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, true, T2, Real>(v, w, R, row_ok, dot);  \
+        break;
+#define QS_ROW_OP(OP) QS_ROW(OP, 0) QS_ROW(OP, 1) QS_ROW(OP, 2) QS_ROW(OP, 3)
+    switch (R.code) {
+        QS_ROW_OP(OP_GEN)
+        QS_ROW_OP(OP_SWAP)
+        QS_ROW_OP(OP_DIAG)
+        QS_ROW_OP(OP_SIDE)
+        QS_ROW_OP(OP_REAL)
+        default: break;
     }
+#undef QS_ROW_OP
+#undef QS_ROW
 }
 
 // Register qubits per group: 4 for forward passes, 3 for the adjoint sweep (psi and lambda
