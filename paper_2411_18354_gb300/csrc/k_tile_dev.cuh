@@ -29,14 +29,11 @@ template <> struct TileT<double> {
 
 // Compact copy of a RegGate in shared memory (matrices in the state's precision), staged once
 // per pass so that every row reads its gates with broadcast shared-memory loads.
-template <typename Real> struct SGate {
+template <typename Real> struct alignas(16) SGate {
     uint64_t hmask, hvals;
-    uint32_t crm, crv;
-    int8_t p, cqm, cqv, op, side, pkind;
-    int16_t slot;
-    int32_t pidx;
-    int32_t code;  // dispatch code: (op * 4 + p) * 2 + (cqm != 0)
-    int32_t pad;
+    // crm, crv, meta, pidx -- one 16-byte load; meta = code | cqm << 8 | cqv << 12 | side << 16 |
+    // pkind << 17 | (slot + 1) << 20, code = (op * 4 + p) * 2 + (cqm != 0)
+    uint32_t crm, crv, meta, pidx;
     Real u[8], d[8];
 };
 
@@ -49,19 +46,12 @@ __device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S, con
     S.hvals = G.hvals;
     S.crm = G.crm;
     S.crv = G.crv;
-    S.p = (int8_t)G.p;
-    S.cqm = (int8_t)G.cqm;
-    S.cqv = (int8_t)G.cqv;
-    S.op = (int8_t)G.op;
-    S.side = (int8_t)G.side;
-    S.pkind = (int8_t)G.pkind;
-    S.slot = (int16_t)G.slot;
-    S.pidx = G.pidx;
-    S.code = (G.op * 4 + G.p) * 2 + (G.cqm != 0);
-    S.pad = 0;
+    const uint32_t code = (uint32_t)((G.op * 4 + G.p) * 2 + (G.cqm != 0));
+    int pkind = G.pkind;
+    S.pidx = (uint32_t)G.pidx;
     if (G.pkind != 0 && cs) {  // the state's parameter: matrices built once per pass
         param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, S.u, S.d);
-        S.pkind = 0;
+        pkind = 0;
     } else {
         const Real *u = TileT<Real>::U(G);
         const Real *d = TileT<Real>::D(G);
@@ -71,6 +61,8 @@ __device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S, con
             S.d[i] = d[i];
         }
     }
+    S.meta = code | ((uint32_t)G.cqm << 8) | ((uint32_t)G.cqv << 12) | ((uint32_t)(G.side & 1) << 16) |
+             ((uint32_t)(pkind & 7) << 17) | ((uint32_t)(G.slot + 1) << 20);
 }
 
 // Copy a pass's groups and gates to shared memory (group gate indices become pass-relative).
@@ -92,7 +84,7 @@ __device__ __forceinline__ void stage_pass(const TilePass &P, const TileGroup *g
 // Gate fields kept in registers while a row is processed.
 template <typename Real> struct GateRegs {
     uint32_t crm, crv;
-    int p, cqm, cqv, op, side, slot, code;
+    int cqm, cqv, side, slot, code;
     Real u[8], d[8];
 };
 
@@ -131,17 +123,18 @@ __device__ __forceinline__ void param_matrices(int kind, Real c, Real s, bool ad
 
 template <typename Real>
 __device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
-    r.crm = G.crm;
-    r.crv = G.crv;
-    r.p = G.p;
-    r.cqm = G.cqm;
-    r.cqv = G.cqv;
-    r.op = G.op;
-    r.side = G.side;
-    r.slot = G.slot;
-    r.code = G.code;
-    if (G.pkind != 0 && cs) {
-        param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, r.u, r.d);
+    const uint4 w = *reinterpret_cast<const uint4 *>(&G.crm);
+    r.crm = w.x;
+    r.crv = w.y;
+    const uint32_t meta = w.z;
+    r.code = (int)(meta & 0xffu);
+    r.cqm = (int)((meta >> 8) & 0xfu);
+    r.cqv = (int)((meta >> 12) & 0xfu);
+    r.side = (int)((meta >> 16) & 1u);
+    const int pkind = (int)((meta >> 17) & 7u);
+    r.slot = (int)(meta >> 20) - 1;
+    if (pkind != 0 && cs) {
+        param_matrices<Real>(pkind, cs[2 * w.w], cs[2 * w.w + 1], adjoint, r.u, r.d);
     } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) r.u[i] = G.u[i];

@@ -196,8 +196,8 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
             std::vector<int> seq(gc);
             std::iota(seq.begin(), seq.end(), 0);
             FusedProgram pf, pa;
-            // the batch kernel runs both directions with kGroupBitsAdjoint-qubit register groups
-            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false, kGroupBitsAdjoint);
+            // the batch kernel runs kGroupBits-qubit groups forward, kGroupBitsAdjoint in the sweep
+            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false, kGroupBits);
             std::reverse(seq.begin(), seq.end());
             plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa, max_pass_gates, false, kGroupBitsAdjoint);
             BatchProg bp{};
