@@ -216,12 +216,68 @@ def test_negative_control_identity_fig1():
         assert np.max(np.abs(a - b)) < 1e-15
 
 
+def _bit_reverse(x, n):
+    x = np.asarray(x, dtype=np.int64)
+    r = np.zeros_like(x)
+    for i in range(n):
+        r |= ((x >> i) & 1) << (n - 1 - i)
+    return r
+
+
+def test_qft_generator_matches_figure():
+    """The QFT generator at n = 5 reproduces Fig. qft_circuit gate for gate; R_m is
+    diag(1, exp(2 pi i / 2^m)) and H is the Section II-A Hadamard."""
+    fig = _load("qft_circuit_5q.json")
+    gates = W.qft_circuit(fig["n"])
+    assert len(gates) == len(fig["gates"]) == 15
+    for g, f in zip(gates, fig["gates"]):
+        assert int(g["target"]) == f["target"]
+        m = sum(1 << c for c in f["controls"])
+        assert int(g["ctrl_mask"]) == m and int(g["ctrl_vals"]) == m
+        want = W.H_MATRIX if f["gate"] == "H" else np.diag([1.0, np.exp(2j * np.pi / 2 ** f["m"])])
+        assert np.array_equal(W.unpack_u(g["U"]), want)
+    assert len(W.qft_circuit(29)) == 29 + 29 * 28 // 2
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 10])
+def test_qft_circuit_is_bit_reversed_dft(n):
+    """The drawn QFT circuit (q0 processed first, no swaps, q0 the least significant bit)
+    maps psi to out[y] = 2^(-n/2) sum_x psi[x] exp(2 pi i rev(x) y / 2^n), rev the n-bit
+    reversal: the textbook QFT with the input read in reversed bit order. Checked against
+    numpy's inverse FFT."""
+    N = 1 << n
+    psi = W.random_state(n, 100 + n)
+    out = psi.copy()
+    for g in W.qft_circuit(n):
+        oracle.apply_gate(out, n, int(g["target"]), int(g["ctrl_mask"]), int(g["ctrl_vals"]),
+                          W.unpack_u(g["U"]))
+    a = np.empty(N, dtype=np.complex128)
+    a[_bit_reverse(np.arange(N), n)] = psi
+    want = np.sqrt(N) * np.fft.ifft(a)
+    assert np.max(np.abs(out - want)) < 1e-13
+    # basis input |x>: every amplitude has modulus 2^(-n/2) and phase 2 pi rev(x) y / 2^n
+    x = (0x2D5 * n + 3) % N
+    out = W.basis_state(n, x)
+    for g in W.qft_circuit(n):
+        oracle.apply_gate(out, n, int(g["target"]), int(g["ctrl_mask"]), int(g["ctrl_vals"]),
+                          W.unpack_u(g["U"]))
+    y = np.arange(N)
+    ph = 2.0 * np.pi * ((int(_bit_reverse(x, n)) * y) % N) / N
+    assert np.max(np.abs(out - np.exp(1j * ph) / np.sqrt(N))) < 1e-13
+
+
 @pytest.mark.parametrize("n", [2, 3, 4, 7, 10])
 def test_streaming_circuit_closed_form(n):
     """Fig. streaming_circ, read with x0 as the least significant bit, maps |k> to
     |k - 1 mod 2^n>; in reverse gate order it maps |k> to |k + 1 mod 2^n>."""
     fig = _load("streaming_circuit_4q.json")
     assert [g["target"] for g in fig["gates"]] == [0, 1, 2, 3]
+    gen = W.streaming_circuit(fig["n"])
+    for g, f in zip(gen, fig["gates"]):
+        m = sum(1 << c for c in f["controls"])
+        assert int(g["target"]) == f["target"] and int(g["kind"]) == W.KIND_X
+        assert int(g["ctrl_mask"]) == m and int(g["ctrl_vals"]) == m
+    assert [int(g["target"]) for g in W.streaming_circuit(n, reverse=True)] == list(range(n - 1, -1, -1))
     gates = [(q, list(range(q))) for q in range(n)]
     for order, step in ((gates, -1), (list(reversed(gates)), +1)):
         for k in range(1 << n):

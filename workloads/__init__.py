@@ -24,6 +24,7 @@ open):
   probability 0.25, uniform over {X, CNOT, Toffoli} on distinct random qubits.
 - Hardware-efficient ansatz: per layer RY(theta) then RZ(theta) on every qubit (separate
   parameters), then CNOT(i -> i+1) for i = 0..n-2 (an open ladder), from |0...0>.
+- R_m (QFT, Section IV-A) is not defined in the text: R_m = diag(1, exp(2 pi i / 2^m)).
 - Seeds: numpy ``default_rng(seed)``; seed = workload index 0..4; state s of the batch
   uses seed 4_000_000 + s.
 """
@@ -206,6 +207,32 @@ def batch_workload(num_states: int = 4096, nmin: int = 10, nmax: int = 20, layer
     ns = rng.integers(nmin, nmax + 1, size=num_states).astype(np.int32)
     thetas = [hea_params(int(n), layers, seed=4_000_000 + s) for s, n in enumerate(ns)]
     return ns, thetas
+
+
+def phase_rm(m: int) -> np.ndarray:
+    """R_m = diag(1, exp(2 pi i / 2^m)). The text uses R_m in its QFT circuit without
+    defining it; this is the usual QFT phase gate."""
+    return np.diag([1.0 + 0.0j, np.exp(2j * np.pi / float(1 << m))])
+
+
+def qft_circuit(n: int) -> np.ndarray:
+    """The QFT staircase of Section IV-A (Fig. qft_circuit) for n qubits, as drawn: for
+    j = 0..n-1, H on q_j, then R_m on q_j controlled by q_(j+m-1) for m = 2..n-j. No final
+    swaps. n + n(n-1)/2 gates (435 at n = 29)."""
+    gates = []
+    for j in range(n):
+        gates.append(make_gate(j, H_MATRIX))
+        for m in range(2, n - j + 1):
+            gates.append(make_gate(j, phase_rm(m), (j + m - 1,)))
+    return gate_list(gates)
+
+
+def streaming_circuit(n: int, reverse: bool = False) -> np.ndarray:
+    """The streaming circuit of Section IV-C (Fig. streaming_circ): X on x_q controlled by
+    x_0..x_(q-1) on |1>, for q = 0..n-1 in drawn order (``reverse`` runs q = n-1..0). Gate q
+    has q controls, so the last one has n-1."""
+    order = range(n - 1, -1, -1) if reverse else range(n)
+    return gate_list([make_gate(q, None, tuple(range(q)), kind=KIND_X) for q in order])
 
 
 def random_state(n: int, seed: int, dtype=np.complex128) -> np.ndarray:
