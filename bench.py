@@ -339,6 +339,45 @@ def measure_masked(qs, n, sched):
     return {c: round(sum(v) / len(v), 2) for c, v in out.items()}
 
 
+# Section IV, Tables 2 and 4: whole-circuit times of the 29-qubit QFT and streaming circuits
+# (fp32 complex, one OpenCL compute unit) on the paper's GTX Titan Black (GK110B) and Stratix V
+# FPGA, baseline (masked) and optimised (reduced iteration set) kernels. Context only.
+PAPER_TIMES_S = {
+    "qft29": {"gk110b_masked": 9.58, "gk110b_reduced": 9.22, "fpga_masked": 413.83, "fpga_reduced": 251.00},
+    "stream29": {"gk110b_masked": 1.73, "gk110b_reduced": 0.95, "fpga_masked": 26.07, "fpga_reduced": 3.78},
+}
+
+
+def measure_paper_circuits(qs, W, reps=3):
+    """The paper's 29-qubit QFT (435 gates) and streaming circuit (29 X gates with 0..28
+    controls) in complex64, each as one graph launch of the whole circuit through
+    qs_apply_circuit: baseline schedule (QS_FLAG_MASKED), reduced iteration set, and fused
+    tile passes. Device time per circuit (CUDA events, state 4.3 GB > L2)."""
+    import torch
+
+    n = 29
+    out = {}
+    st = qs.State(n, "c64")
+    try:
+        for name, gates in (("qft29", W.qft_circuit(n)), ("stream29", W.streaming_circuit(n))):
+            r = {"gates": int(len(gates)),
+                 "algorithmic_GB": round(sum(2.0 * (1 << (n - bin(int(g["ctrl_mask"])).count("1"))) * 8
+                                             for g in gates) / 1e9, 3)}
+            for label, flags in (("masked", qs.QS_FLAG_MASKED), ("reduced", 0), ("fused", qs.QS_FLAG_FUSE)):
+                st.set_basis(0)
+                ms = _events_ms(lambda: st.apply_circuit(gates, flags=flags | qs.QS_FLAG_GRAPH), reps)
+                r[f"{label}_ms"] = round(ms, 3)
+            r["masked_over_reduced"] = round(r["masked_ms"] / r["reduced_ms"], 2)
+            r["paper_s"] = PAPER_TIMES_S[name]
+            out[name] = r
+    finally:
+        st.close()
+        torch.cuda.empty_cache()
+    out["note"] = ("paper_s: Tables 2 and 4 (GTX Titan Black / Stratix V, one OpenCL compute unit), context only; "
+                   "algorithmic_GB counts 2*2^(n-c)*8 bytes per gate")
+    return out
+
+
 def measure_batch(qs, W):
     """Batching workload: 4096 states, n uniform in 10..20, 8 ansatz layers, complex64: one
     graph-launched persistent kernel for energies and gradients; settings from the autotuner."""
@@ -553,6 +592,7 @@ def run_ours(args, rank, world, local_rank):
         result["reduce_expect_z_n30"] = measure_reduce(qs, W, peak)
         result["masked_over_reduced_time_by_c"] = measure_masked(qs, n, sched)
         result["batch"] = measure_batch(qs, W)
+        result["paper_circuits"] = measure_paper_circuits(qs, W)
         result["cpu_baseline"] = cpu_oracle_sample(n, sched)
 
     if rank == 0:

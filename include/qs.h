@@ -62,7 +62,8 @@ enum {
 enum {
     QS_FLAG_FUSE = 1,        /* group runs of low-target gates into one tile pass      */
     QS_FLAG_GRAPH = 2,       /* launch the whole sequence as one CUDA graph            */
-    QS_FLAG_OUT_DEVICE = 4   /* energy / grad / expectation outputs are device pointers */
+    QS_FLAG_OUT_DEVICE = 4,  /* energy / grad / expectation outputs are device pointers */
+    QS_FLAG_MASKED = 8       /* qs_apply_circuit: baseline schedule (comparator only)   */
 };
 
 /* One gate (96 bytes, naturally aligned). Section III-A: target t, controls, matrix. */
@@ -144,7 +145,10 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
  * theta[param] (theta may be NULL when no gate is parameterised; n_theta is its length).
  * All gates are validated before anything is launched. flags: QS_FLAG_FUSE runs maximal
  * runs of consecutive gates whose target and controls are below the tile size in one
- * HBM round trip; QS_FLAG_GRAPH records the launches into a CUDA graph and launches it. */
+ * HBM round trip; QS_FLAG_GRAPH records the launches into a CUDA graph and launches it.
+ * QS_FLAG_MASKED runs every gate with the baseline schedule of Section III-A instead (all
+ * 2^(n-1) pair iterations, controls tested per pair, the general 2x2 update), the
+ * comparator of qs_apply_gate_masked for whole circuits; QS_EINVAL with QS_FLAG_FUSE. */
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
                            const double *theta, size_t n_theta, int flags);
 

@@ -17,7 +17,7 @@ from .build import LIB_PATH
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
 QS_GATE_U, QS_GATE_X, QS_GATE_RY, QS_GATE_RZ = 0, 1, 2, 3
-QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE = 1, 2, 4
+QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED = 1, 2, 4, 8
 
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EUNSUPPORTED"}
 

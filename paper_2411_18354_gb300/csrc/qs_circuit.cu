@@ -121,9 +121,12 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
     return h;
 }
 
-static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, cudaStream_t st) {
+static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, cudaStream_t st,
+                              bool masked = false) {
     for (size_t i = 0; i < plans.size(); ++i) {
-        cudaError_t e = launch_gate(s->dtype, s->psi, plans[i], st);
+        cudaError_t e = masked ? launch_gate_masked(s->dtype, s->psi, plans[i], plans[i].ctrl_mask,
+                                                    plans[i].ctrl_vals, st)
+                               : launch_gate(s->dtype, s->psi, plans[i], st);
         if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit launch");
     }
     return QS_OK;
@@ -208,12 +211,26 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
                            int flags) {
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_apply_circuit: gates is NULL");
-    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH)) return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED))
+        return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
+    if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
+        return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
     std::vector<GatePlan> plans(count);
     char err[256];
     for (size_t i = 0; i < count; ++i)
         if (!plan_record(s, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
+    const bool masked = (flags & QS_FLAG_MASKED) != 0;
+    if (masked) {
+        // baseline schedule: every pair iteration launched, the controls tested per unit,
+        // the general update with the full matrix (as the Section III-A kernel does)
+        for (GatePlan &p : plans) {
+            GatePlan pm;
+            plan_masked(p, &pm);
+            std::memcpy(pm.U, p.Ufull, sizeof(pm.U));
+            p = pm;
+        }
+    }
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     FusedProgram prog;
     if (fuse) {
@@ -226,7 +243,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     if (table_bytes) pack_program_table(prog, table_host.data());
 
     if (!(flags & QS_FLAG_GRAPH)) {
-        if (!fuse) return launch_plans(s, plans, s->stream);
+        if (!fuse) return launch_plans(s, plans, s->stream, masked);
         qs_status st = ensure_device(&s->tile_table, &s->tile_table_bytes, table_bytes, s->stream,
                                      "qs_apply_circuit: cannot allocate the fused gate table");
         if (st != QS_OK) return st;
@@ -279,7 +296,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         }
         qs_status st = fuse ? launch_program(s, prog, plans, table, nullptr, nullptr, nullptr, nullptr, 0,
                                              s->capture_stream)
-                            : launch_plans(s, plans, s->capture_stream);
+                            : launch_plans(s, plans, s->capture_stream, masked);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(s->capture_stream, &graph);
         if (st != QS_OK || e != cudaSuccess) {

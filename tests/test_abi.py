@@ -130,6 +130,9 @@ def test_wrapped_state_validates_gates_on_host():
             qs.qs_adjoint_grad(h, gates, np.zeros(0))
         with pytest.raises(qs.QsError):
             qs.qs_apply_circuit(h, gates, np.zeros(1), flags=1 << 10)
+        with pytest.raises(qs.QsError) as e:  # baseline schedule has no fused form
+            qs.qs_apply_circuit(h, gates, np.zeros(1), flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_MASKED)
+        assert e.value.status == _lib.QS_EINVAL
     finally:
         qs.qs_state_free(h)  # wrapped memory is not freed by the library
 

@@ -1,0 +1,260 @@
+"""GPU parity on the paper's circuit families (Section IV: QFT, streaming), the precision
+circuit (n = 32, complex64 against complex128) and the 32/64-bit index boundary."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import ATOL_CIRCUIT, NP, RTOL_GATE, c128_of, oracle_outputs, prepare_product, random_state, \
+    rotations, sample_indices
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["c64", "c128"]
+MODES = ["gate", "circuit", "fuse", "masked", "masked_circuit"]
+# QFT output on a basis input: every amplitude has modulus 2^(-n/2). Relative error bound of
+# the whole 435-gate circuit: each gate adds at most ~3u (u = 2^-24 / 2^-53) to the error
+# norm and unitary gates do not grow it, so 435 * 3u = 8e-5 (c64) / 1.5e-13 (c128); the
+# assertions allow a factor of ~4 over that.
+QFT_RTOL = {"c64": 3e-4, "c128": 1e-12}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2411_18354_gb300 as q
+
+    q.build()
+    return q
+
+
+def _apply(qs, st, gates, mode):
+    if mode == "circuit":
+        st.apply_circuit(gates)
+    elif mode == "fuse":
+        st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE)
+    elif mode == "masked_circuit":
+        st.apply_circuit(gates, flags=qs.QS_FLAG_MASKED | qs.QS_FLAG_GRAPH)
+    else:
+        for g in gates:
+            t, m, v = int(g["target"]), int(g["ctrl_mask"]), int(g["ctrl_vals"])
+            if mode == "masked":
+                st.apply_gate_masked(t, W.unpack_u(g["U"]), m, v)
+            elif int(g["kind"]) == W.KIND_X:
+                st.apply_x(t, m, v)
+            else:
+                st.apply_gate(t, W.unpack_u(g["U"]), m, v)
+
+
+def _bit_reverse(x: int, n: int) -> int:
+    return int(format(x, f"0{n}b")[::-1], 2)
+
+
+def _qft_basis_amplitudes(x: int, n: int, ys: np.ndarray) -> np.ndarray:
+    """QFT circuit as drawn applied to |x>: amplitude y is exp(2 pi i rev(x) y / 2^n) 2^(-n/2)
+    (pinned against the oracle and numpy's FFT on the CPU)."""
+    N = 1 << n
+    r = _bit_reverse(x, n)
+    ph = np.array([(r * int(y)) % N for y in ys], dtype=np.float64) * (2.0 * np.pi / N)
+    return np.exp(1j * ph) / np.sqrt(N)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+def test_qft_matches_oracle(qs, dtype, mode):
+    """QFT (Fig. qft_circuit pattern) at n = 14 from a random state, every schedule."""
+    n = 14
+    gates = W.qft_circuit(n)
+    psi0 = random_state(n, dtype, 140)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates)
+    with qs.State(n, dtype) as st:
+        st.from_numpy(psi0)
+        _apply(qs, st, gates, mode)
+        got = c128_of(st.to_numpy())
+    assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("reverse", [False, True])
+def test_streaming_matches_oracle_bit_exact(qs, dtype, mode, reverse):
+    """Streaming circuit (Fig. streaming_circ) at n = 15: gates with 0..14 controls; the result
+    equals the oracle's bit for bit and is the closed-form shift by -1 (drawn order) / +1."""
+    n = 15
+    gates = W.streaming_circuit(n, reverse)
+    psi0 = random_state(n, dtype, 150)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates)
+    with qs.State(n, dtype) as st:
+        st.from_numpy(psi0)
+        _apply(qs, st, gates, mode)
+        got = st.to_numpy()
+    assert np.array_equal(got, ref.astype(NP[dtype]))
+    assert np.array_equal(got, np.roll(psi0, 1 if reverse else -1))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", ["circuit", "fuse"])
+def test_qft29_basis_closed_form(qs, dtype, mode):
+    """QFT29 (the paper's 29-qubit QFT, 435 gates) on a basis state: 2^14 sampled amplitudes
+    against the closed form, and the modulus of every amplitude (whole vector, on the
+    device) equal to 2^(-n/2)."""
+    import torch
+
+    n = 29
+    x = 0x0A5C3E71 & ((1 << n) - 1)
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    buf = torch.empty(1 << n, dtype=tdt, device="cuda")
+    st = qs.State.wrap(buf, n)
+    try:
+        st.set_basis(x)
+        _apply(qs, st, W.qft_circuit(n), mode)
+        torch.cuda.synchronize()
+        ys = sample_indices(n, 1 << 14, 29)
+        got = buf[torch.from_numpy(ys.astype(np.int64)).cuda()].cpu().numpy().astype(np.complex128)
+        want = _qft_basis_amplitudes(x, n, ys)
+        scale = 2.0 ** (-n / 2.0)
+        assert np.max(np.abs(got - want)) <= QFT_RTOL[dtype] * scale
+        mod_err = 0.0
+        for i in range(0, 1 << n, 1 << 26):
+            blk = buf[i:i + (1 << 26)].abs().double() * (2.0 ** (n / 2.0))
+            mod_err = max(mod_err, float((blk - 1.0).abs().max()))
+        assert mod_err <= 2 * QFT_RTOL[dtype]
+    finally:
+        st.close()
+        del buf
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", ["circuit", "fuse", "masked_circuit"])
+def test_stream29_whole_vector_shift(qs, dtype, mode):
+    """Streaming circuit at n = 29 (the paper's Stream29, gates with up to 28 controls) on a
+    product state with distinct amplitudes: the whole output vector is the input shifted by
+    one index, bit for bit (compared on the device)."""
+    import torch
+
+    n = 29
+    al, be = rotations(n, 290)
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    buf = torch.empty(1 << n, dtype=tdt, device="cuda")
+    st = qs.State.wrap(buf, n)
+    try:
+        prepare_product(st, al, be)
+        torch.cuda.synchronize()
+        inp = buf.clone()
+        _apply(qs, st, W.streaming_circuit(n), mode)
+        torch.cuda.synchronize()
+        assert torch.equal(buf[:-1], inp[1:])
+        assert torch.equal(buf[-1:], inp[:1])
+        del inp
+    finally:
+        st.close()
+        del buf
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [32, 33])
+def test_index_width_boundary_sampled(qs, n):
+    """n = 32 (the last size with 32-bit device indices) and n = 33 (64-bit indices,
+    68.7 GB complex64): single gates with targets and controls on the lowest and highest
+    qubits, sampled outputs against the oracle's one-amplitude update; then the streaming
+    circuit fused and unfused, sampled outputs against the inputs one index up."""
+    import torch
+
+    al, be = rotations(n, n)
+    buf = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    st = qs.State.wrap(buf, n)
+    inp = None
+    try:
+        prepare_product(st, al, be)
+        torch.cuda.synchronize()
+        inp = buf.clone()
+        ks = sample_indices(n, 1 << 13, n)
+        kt = torch.from_numpy(ks.astype(np.int64)).cuda()
+        xin = inp[kt].cpu().numpy().astype(np.complex128)
+        rng = np.random.default_rng(n)
+        cases = [(0, 0, ()), (n - 1, 0, ()), (n - 1, 1, (0,)), (0, 1, (n - 1,)), (n // 2, 3, (1, n - 2, n - 1)),
+                 (n - 1, 8, (0, 2, 5, 9, 14, 20, 27, n - 2)), (3, 5, (0, 1, 2, n - 2, n - 1))]
+        for t, c, ctrls in cases:
+            vals = [int(b) for b in rng.integers(0, 2, size=c)]
+            g = W.make_gate(t, W.haar_2x2(rng), ctrls, vals)
+            m, v, U = int(g["ctrl_mask"]), int(g["ctrl_vals"]), W.unpack_u(g["U"])
+            buf.copy_(inp)
+            st.apply_gate(t, U, m, v)
+            kp = torch.from_numpy((ks ^ np.uint64(1 << t)).astype(np.int64)).cuda()
+            pin = inp[kp].cpu().numpy().astype(np.complex128)
+            out = buf[kt].cpu().numpy().astype(np.complex128)
+            want = oracle_outputs(ks, t, m, v, U, xin, pin)
+            assert np.all(np.abs(out - want) <= 4 * RTOL_GATE["c64"] * (np.abs(xin) + np.abs(pin)) + 1e-300), (t, c)
+        N = np.uint64(1 << n)
+        kup = torch.from_numpy(((ks + np.uint64(1)) % N).astype(np.int64)).cuda()
+        want = inp[kup].cpu().numpy()
+        for flags in (0, qs.QS_FLAG_FUSE):
+            buf.copy_(inp)
+            st.apply_circuit(W.streaming_circuit(n), flags=flags)
+            assert np.array_equal(buf[kt].cpu().numpy(), want), flags
+    finally:
+        st.close()
+        del buf, inp
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_precision_recipe_against_oracle(qs, dtype):
+    """The precision circuit's recipe (2000 gates, 0-6 controls, 25 % X / CNOT / Toffoli) at
+    n = 20: whole vector against the oracle, plain and fused."""
+    n = 20
+    gates = W.precision_circuit(n, 2000, seed=2)
+    psi0 = random_state(n, dtype, 220)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates)
+    for mode in ("circuit", "fuse"):
+        with qs.State(n, dtype) as st:
+            st.from_numpy(psi0)
+            _apply(qs, st, gates, mode)
+            got = c128_of(st.to_numpy())
+        assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype], mode
+
+
+def test_precision_circuit_n32(qs):
+    """The precision circuit at full size: n = 32 from H on every qubit, 2000 gates, run in
+    complex128 (68.7 GB) and complex64 (34.4 GB, plain and fused) on the device. complex64
+    against complex128: max-abs amplitude error <= 3e-5, norm drift <= 1e-5, and every
+    <Z_i> within 2 ||psi64 - psi128|| (+ the float64 sums' rounding) of the complex128 one;
+    complex128 keeps its norm to 1e-11."""
+    import torch
+
+    n = 32
+    gates = W.precision_circuit(n, 2000, seed=2)
+    prefix = W.gate_list([W.make_gate(q, W.H_MATRIX) for q in range(n)])
+    b128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    b64 = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    s128 = qs.State.wrap(b128, n)
+    s64 = qs.State.wrap(b64, n)
+    try:
+        s128.set_basis(0)
+        s128.apply_circuit(prefix)
+        s128.apply_circuit(gates)
+        z128, nrm128 = s128.expect_z()
+        assert abs(nrm128 - 1.0) <= 1e-11
+        for flags in (0, qs.QS_FLAG_FUSE):
+            s64.set_basis(0)
+            s64.apply_circuit(prefix, flags=flags)
+            s64.apply_circuit(gates, flags=flags)
+            z64, nrm64 = s64.expect_z()
+            torch.cuda.synchronize()
+            err = 0.0
+            d2 = 0.0
+            for i in range(0, 1 << n, 1 << 26):
+                d = b64[i:i + (1 << 26)].to(torch.complex128) - b128[i:i + (1 << 26)]
+                err = max(err, float(d.abs().max()))
+                d2 += float((d.abs() ** 2).sum())
+            assert err <= 3e-5, (flags, err)
+            assert abs(nrm64 - 1.0) <= 1e-5, (flags, nrm64)
+            assert np.max(np.abs(np.asarray(z64) - np.asarray(z128))) <= 2.0 * np.sqrt(d2) + 1e-9, flags
+    finally:
+        s128.close()
+        s64.close()
+        del b128, b64
+        torch.cuda.empty_cache()
