@@ -160,6 +160,17 @@ qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits);
 /* The tile size the next fused call will use. */
 int qs_get_tile_bits(qs_dtype dtype, int adjoint);
 
+/* DRAM fetch size of the L2 (the context limit cudaLimitMaxL2FetchGranularity of this
+ * process) that qs_state_alloc / qs_state_wrap set on their device: 32 (default), 64 or 128
+ * bytes, or 0 to leave the context's limit alone. A gate whose controls sit on low qubits
+ * selects runs of 8-64 bytes (every other run of 2^p amplitudes, p the lowest inserted
+ * bit); with a 128-byte fetch each run costs a whole 128-byte DRAM block. The limit
+ * belongs to the process's context and ends with it; it applies to every kernel of the
+ * process on that device. The QS_L2_FETCH_BYTES environment variable sets the initial
+ * value. EINVAL for any other value; takes effect at the next state on a device. */
+qs_status qs_set_l2_fetch_bytes(int bytes);
+int qs_get_l2_fetch_bytes(void);
+
 /* ------------------------------------------------------------------------------------ */
 /* Reductions (double-precision accumulation on the device)                             */
 /* ------------------------------------------------------------------------------------ */

@@ -62,6 +62,8 @@ _SIGNATURES = [
     ("qs_batch_free", ctypes.c_int, [_vp]),
     ("qs_set_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("qs_get_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    ("qs_set_l2_fetch_bytes", ctypes.c_int, [ctypes.c_int]),
+    ("qs_get_l2_fetch_bytes", ctypes.c_int, []),
 ]
 
 _lib = None
@@ -271,3 +273,11 @@ def qs_set_tile_bits(dtype: int, adjoint: int, bits: int) -> None:
 
 def qs_get_tile_bits(dtype: int, adjoint: int) -> int:
     return int(lib().qs_get_tile_bits(dtype, adjoint))
+
+
+def qs_set_l2_fetch_bytes(nbytes: int) -> None:
+    _check(lib().qs_set_l2_fetch_bytes(nbytes))
+
+
+def qs_get_l2_fetch_bytes() -> int:
+    return int(lib().qs_get_l2_fetch_bytes())

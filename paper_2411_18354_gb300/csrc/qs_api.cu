@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -37,6 +38,37 @@ qs_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 size_t elem_bytes(int dtype) { return dtype == QS_C64 ? 8 : 16; }
+
+// L2 fetch size for DRAM misses (cudaLimitMaxL2FetchGranularity of this process's context).
+// A gate with controls on low qubits selects runs of 8-64 bytes; with the device's default
+// fetch size each such run pulls a 128-byte block from DRAM, so the limit is set to one
+// 32-byte sector per device the library works on (QS_L2_FETCH_BYTES or qs_set_l2_fetch_bytes
+// choose another value; 0 leaves the context's limit alone).
+static std::mutex g_l2_mutex;
+static int g_l2_bytes = -1;           // configured value, -1 = not read from the environment yet
+static int g_l2_applied[64];          // per device: value applied (0 = none yet)
+
+static bool valid_l2_bytes(int b) { return b == 0 || b == 32 || b == 64 || b == 128; }
+
+static int l2_configured_locked() {
+    if (g_l2_bytes < 0) {
+        g_l2_bytes = 32;
+        if (const char *env = std::getenv("QS_L2_FETCH_BYTES")) {
+            const int v = std::atoi(env);
+            if (valid_l2_bytes(v)) g_l2_bytes = v;
+        }
+    }
+    return g_l2_bytes;
+}
+
+void apply_l2_fetch(int device) {
+    std::lock_guard<std::mutex> lock(g_l2_mutex);
+    const int want = l2_configured_locked();
+    if (want == 0 || device < 0 || device >= 64 || g_l2_applied[device] == want) return;
+    if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)want) == cudaSuccess)
+        g_l2_applied[device] = want;
+    cudaGetLastError();  // a hint: a context that refuses it keeps its default
+}
 
 qs_status ensure_reduce_scratch(qs_state *s) {
     const size_t need = reduce_scratch_doubles(s->n) + 64;
@@ -80,6 +112,18 @@ extern "C" {
 
 const char *qs_last_error(void) { return g_err; }
 
+qs_status qs_set_l2_fetch_bytes(int bytes) {
+    if (!valid_l2_bytes(bytes)) return fail(QS_EINVAL, "qs_set_l2_fetch_bytes: %d is not 0, 32, 64 or 128", bytes);
+    std::lock_guard<std::mutex> lock(g_l2_mutex);
+    g_l2_bytes = bytes;
+    return QS_OK;
+}
+
+int qs_get_l2_fetch_bytes(void) {
+    std::lock_guard<std::mutex> lock(g_l2_mutex);
+    return l2_configured_locked();
+}
+
 const char *qs_build_info(void) {
     return "libqs: sm_103a state-vector kernels (reduced iteration scheduling, Section III-B of arXiv 2411.18354)";
 }
@@ -108,6 +152,7 @@ qs_status qs_state_alloc(int n, qs_dtype dtype, void *stream, qs_state **out) {
     s->owned = true;
     s->stream = reinterpret_cast<cudaStream_t>(stream);
     cudaGetDevice(&s->device);
+    apply_l2_fetch(s->device);
     qs_status st = qs_state_set_basis(s, 0);
     if (st != QS_OK) {
         qs_state_free(s);
@@ -134,7 +179,8 @@ qs_status qs_state_wrap(void *dev_ptr, size_t bytes, int n, qs_dtype dtype, void
     s->bytes = need;
     s->owned = false;
     s->stream = reinterpret_cast<cudaStream_t>(stream);
-    cudaGetDevice(&s->device);
+    if (cudaGetDevice(&s->device) == cudaSuccess) apply_l2_fetch(s->device);
+    cudaGetLastError();
     *out = s;
     return QS_OK;
 }

@@ -47,6 +47,8 @@ namespace qs {
 qs_status set_error(qs_status st, const char *msg);
 qs_status cuda_fail(cudaError_t e, const char *what);
 size_t elem_bytes(int dtype);
+// Sets the L2 fetch size limit once per device (see qs_set_l2_fetch_bytes).
+void apply_l2_fetch(int device);
 qs_status ensure_reduce_scratch(qs_state *s);
 void release_state_buffers(qs_state *s);  // scratch, lambda, graphs, capture stream
 

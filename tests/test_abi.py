@@ -137,6 +137,21 @@ def test_wrapped_state_validates_gates_on_host():
         qs.qs_state_free(h)  # wrapped memory is not freed by the library
 
 
+def test_l2_fetch_setting_is_validated_on_host():
+    before = qs.qs_get_l2_fetch_bytes()
+    assert before in (0, 32, 64, 128)
+    for bad in (1, 16, 48, 256, -32):
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_set_l2_fetch_bytes(bad)
+        assert e.value.status == _lib.QS_EINVAL
+    try:
+        for ok in (0, 64, 128, 32):
+            qs.qs_set_l2_fetch_bytes(ok)
+            assert qs.qs_get_l2_fetch_bytes() == ok
+    finally:
+        qs.qs_set_l2_fetch_bytes(before)
+
+
 def test_tile_bits_setting_is_validated_on_host():
     for bad in (1, 4, 15, -2):
         with pytest.raises(qs.QsError):
