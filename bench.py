@@ -553,7 +553,7 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = sum(ms for _, _, ms, _ in per)
     achieved = launch_bytes / (launch_ms * 1e-3) / 1e9
     sect_bytes = sum(sector_bytes(n, m, esize) for _, _, _, m in per)
-    per_c = measure_per_c(qs, st, n, esize, sched, peak)
+    per_c = None if args.quick else measure_per_c(qs, st, n, esize, sched, peak)
     traffic = profiled_traffic(n, "c64")
 
     result = {
