@@ -99,9 +99,9 @@ __device__ void run_program_global(const BatchArgs &a, const BatchProg &pg, bool
             if (adjoint) load_tile<Real>(ta, g_j, s_j, base, lam, tl);
             __syncthreads();
             if (adjoint)
-                apply_groups<Real, true, kGroupBitsAdjoint>(tp, tl, base, P.k, sgroups, P.group_count, sgates, cs, gacc);
+                apply_groups<Real, true, kGroupBitsAdjoint, 1, true>(tp, tl, base, P.k, sgroups, P.group_count, sgates, cs, gacc);
             else
-                apply_groups<Real, false, kGroupBits>(tp, nullptr, base, P.k, sgroups, P.group_count, sgates, cs, nullptr);
+                apply_groups<Real, false, kGroupBits, 1, true>(tp, nullptr, base, P.k, sgroups, P.group_count, sgates, cs, nullptr);
             store_tile<Real>(ta, g_j, s_j, base, tp, psi);
             if (adjoint) store_tile<Real>(ta, g_j, s_j, base, tl, lam);
             __syncthreads();
@@ -155,14 +155,14 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(Real) == 4 ? 2 : 1) k_ba
             for (int pi = pg.fwd_begin; pi < pg.fwd_begin + pg.fwd_count; ++pi) {
                 const TilePass &P = a.passes[pi];
                 stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates, cs, false);
-                apply_groups<Real, false, kGroupBits>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
+                apply_groups<Real, false, kGroupBits, 1, true>(tp, nullptr, 0, n, sgroups, P.group_count, sgates, cs, nullptr);
                 __syncthreads();
             }
             energy = obs_pass<Real>(tp, tl, n, red, TileT<Real>::SW);
             for (int pi = pg.adj_begin; pi < pg.adj_begin + pg.adj_count; ++pi) {
                 const TilePass &P = a.passes[pi];
                 stage_pass<Real>(P, a.groups, a.gates, sgroups, sgates, cs, true);
-                apply_groups<Real, true, kGroupBitsAdjoint>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
+                apply_groups<Real, true, kGroupBitsAdjoint, 1, true>(tp, tl, 0, n, sgroups, P.group_count, sgates, cs, gacc);
                 __syncthreads();
             }
         } else {

@@ -121,12 +121,30 @@ __device__ __forceinline__ void param_matrices(int kind, Real c, Real s, bool ad
     }
 }
 
+// Raw copy of a staged gate (one 16-byte control word and the matrices).
+template <typename Real> struct GateRaw {
+    uint4 w;  // crm, crv, meta, pidx
+    Real u[8], d[8];
+};
+
+template <typename Real, bool ADJ>
+__device__ __forceinline__ void fetch_gate(const SGate<Real> &G, GateRaw<Real> &r) {
+    using V = typename TileT<Real>::V;  // 16 bytes
+    constexpr int PER = 16 / sizeof(Real);
+    r.w = *reinterpret_cast<const uint4 *>(&G.crm);
+#pragma unroll
+    for (int i = 0; i < 8; i += PER) *reinterpret_cast<V *>(&r.u[i]) = *reinterpret_cast<const V *>(&G.u[i]);
+    if (ADJ) {
+#pragma unroll
+        for (int i = 0; i < 8; i += PER) *reinterpret_cast<V *>(&r.d[i]) = *reinterpret_cast<const V *>(&G.d[i]);
+    }
+}
+
 template <typename Real>
-__device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &r, const Real *cs, bool adjoint) {
-    const uint4 w = *reinterpret_cast<const uint4 *>(&G.crm);
-    r.crm = w.x;
-    r.crv = w.y;
-    const uint32_t meta = w.z;
+__device__ __forceinline__ void decode_gate(const GateRaw<Real> &g, GateRegs<Real> &r, const Real *cs, bool adjoint) {
+    r.crm = g.w.x;
+    r.crv = g.w.y;
+    const uint32_t meta = g.w.z;
     r.code = (int)(meta & 0xffu);
     r.cqm = (int)((meta >> 8) & 0xfu);
     r.cqv = (int)((meta >> 12) & 0xfu);
@@ -134,13 +152,13 @@ __device__ __forceinline__ void load_gate(const SGate<Real> &G, GateRegs<Real> &
     const int pkind = (int)((meta >> 17) & 7u);
     r.slot = (int)(meta >> 20) - 1;
     if (pkind != 0 && cs) {
-        param_matrices<Real>(pkind, cs[2 * w.w], cs[2 * w.w + 1], adjoint, r.u, r.d);
+        param_matrices<Real>(pkind, cs[2 * g.w.w], cs[2 * g.w.w + 1], adjoint, r.u, r.d);
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) r.u[i] = G.u[i];
-        if (adjoint && r.slot >= 0) {
+        for (int i = 0; i < 8; ++i) r.u[i] = g.u[i];
+        if (adjoint) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) r.d[i] = G.d[i];
+            for (int i = 0; i < 8; ++i) r.d[i] = g.d[i];
         }
     }
 }
@@ -168,42 +186,50 @@ __device__ __forceinline__ void op_pair(T2 &x, T2 &y, const Real *u, int side) {
     }
 }
 
-// All pairs (e, e | 2^P) of one row for one gate with operation OP; CQ: the gate has
-// controls on group qubits (else every pair of a selected row is updated). Rows of tiles with
-// fewer than GB qubits are padded with zero elements that pair only with each other, so they
-// stay zero and add nothing to the inner products.
-template <int P, int OP, bool ADJ, int GB, bool CQ, typename T2, typename Real>
-__device__ __forceinline__ void row_pairs(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
+// All pairs (e, e | 2^P) of the thread's RPT rows for one gate with operation OP; CQ: the
+// gate has controls on group qubits (else every pair of a selected row is updated); UNI: every
+// row is selected (no per-row predicate). The RPT rows are independent, which gives each
+// thread RPT times the arithmetic per decoded gate. Rows of tiles with fewer than GB qubits
+// are padded with zero elements that pair only with each other, so they stay zero and add
+// nothing to the inner products.
+template <int P, int OP, bool ADJ, int GB, bool CQ, int RPT, bool UNI, typename T2, typename Real>
+__device__ __forceinline__ void row_pairs(T2 (&v)[RPT][1 << GB], T2 (&w)[RPT][ADJ ? (1 << GB) : 1],
+                                          const GateRegs<Real> &R, const bool (&ok)[RPT], Real &dot) {
     constexpr int DOP = OP == OP_DIAG ? OP_DIAG : (OP == OP_REAL ? OP_REAL : OP_GEN);
-    if (!row_ok) return;
 #pragma unroll
     for (int e = 0; e < (1 << GB); ++e) {
         if ((e >> P) & 1) continue;
         const int e2 = e | (1 << P);
         if (!CQ || ((e & R.cqm) == R.cqv)) {
-            op_pair<OP, T2, Real>(v[e], v[e2], R.u, R.side);
-            if (ADJ) {
-                if (R.slot >= 0) {
-                    T2 mx = v[e], my = v[e2];
-                    pair_update<DOP, T2, Real>(mx, my, R.d);
-                    dot += w[e].x * mx.x + w[e].y * mx.y + w[e2].x * my.x + w[e2].y * my.y;
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                if (!UNI && !ok[j]) continue;
+                op_pair<OP, T2, Real>(v[j][e], v[j][e2], R.u, R.side);
+                if (ADJ) {
+                    if (R.slot >= 0) {
+                        T2 mx = v[j][e], my = v[j][e2];
+                        pair_update<DOP, T2, Real>(mx, my, R.d);
+                        dot += w[j][e].x * mx.x + w[j][e].y * mx.y + w[j][e2].x * my.x + w[j][e2].y * my.y;
+                    }
+                    op_pair<OP, T2, Real>(w[j][e], w[j][e2], R.u, R.side);
                 }
-                op_pair<OP, T2, Real>(w[e], w[e2], R.u, R.side);
             }
         }
     }
 }
 
-// One switch on the staged dispatch code selects (operation, target place, in-row controls).
-template <bool ADJ, int GB, typename T2, typename Real>
-__device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, bool row_ok, Real &dot) {
-#define QS_ROW(OP, P)                                                                                    \
-    case ((OP)*4 + (P)) * 2 + 0:                                                                         \
-        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, false, T2, Real>(v, w, R, row_ok, dot); \
-        break;                                                                                           \
-    case ((OP)*4 + (P)) * 2 + 1:                                                                         \
-        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, true, T2, Real>(v, w, R, row_ok, dot);  \
+// Gate dispatch. FOLD: one switch on (staged code << 1 | pred) selects operation, target
+// place, in-row controls and whether rows need a per-thread predicate (fewer live registers:
+// the batched kernel, which holds both sweep directions). Otherwise a uniform branch on pred
+// picks one of two switches on the staged code (faster in the tile pass).
+template <bool ADJ, int GB, int RPT, bool UNI, typename T2, typename Real>
+__device__ __forceinline__ void row_switch(T2 (&v)[RPT][1 << GB], T2 (&w)[RPT][ADJ ? (1 << GB) : 1],
+                                          const GateRegs<Real> &R, const bool (&ok)[RPT], Real &dot) {
+#define QS_ROW1(OP, P, CQ)                                                                                   \
+    case (((OP)*4 + (P)) * 2 + (CQ)):                                                                        \
+        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, CQ, RPT, UNI, T2, Real>(v, w, R, ok, dot); \
         break;
+#define QS_ROW(OP, P) QS_ROW1(OP, P, 0) QS_ROW1(OP, P, 1)
 #define QS_ROW_OP(OP) QS_ROW(OP, 0) QS_ROW(OP, 1) QS_ROW(OP, 2) QS_ROW(OP, 3)
     switch (R.code) {
         QS_ROW_OP(OP_GEN)
@@ -215,6 +241,38 @@ __device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, 
     }
 #undef QS_ROW_OP
 #undef QS_ROW
+#undef QS_ROW1
+}
+
+template <bool ADJ, int GB, int RPT, typename T2, typename Real>
+__device__ __forceinline__ void row_switch_folded(T2 (&v)[RPT][1 << GB], T2 (&w)[RPT][ADJ ? (1 << GB) : 1],
+                                                 const GateRegs<Real> &R, const bool (&ok)[RPT], bool pred,
+                                                 Real &dot) {
+#define QS_ROW1(OP, P, CQ, PR)                                                                                  \
+    case ((((OP)*4 + (P)) * 2 + (CQ)) << 1) | (PR):                                                             \
+        if ((P) < GB) row_pairs<((P) < GB ? (P) : 0), OP, ADJ, GB, CQ, RPT, !(PR), T2, Real>(v, w, R, ok, dot); \
+        break;
+#define QS_ROW(OP, P) QS_ROW1(OP, P, 0, 0) QS_ROW1(OP, P, 0, 1) QS_ROW1(OP, P, 1, 0) QS_ROW1(OP, P, 1, 1)
+#define QS_ROW_OP(OP) QS_ROW(OP, 0) QS_ROW(OP, 1) QS_ROW(OP, 2) QS_ROW(OP, 3)
+    switch ((R.code << 1) | (pred ? 1 : 0)) {
+        QS_ROW_OP(OP_GEN)
+        QS_ROW_OP(OP_SWAP)
+        QS_ROW_OP(OP_DIAG)
+        QS_ROW_OP(OP_SIDE)
+        QS_ROW_OP(OP_REAL)
+        default: break;
+    }
+#undef QS_ROW_OP
+#undef QS_ROW
+#undef QS_ROW1
+}
+
+template <bool ADJ, int GB, int RPT, bool FOLD, typename T2, typename Real>
+__device__ __forceinline__ void row_gate(T2 (&v)[RPT][1 << GB], T2 (&w)[RPT][ADJ ? (1 << GB) : 1],
+                                         const GateRegs<Real> &R, const bool (&ok)[RPT], bool pred, Real &dot) {
+    if (FOLD) row_switch_folded<ADJ, GB, RPT, T2, Real>(v, w, R, ok, pred, dot);
+    else if (!pred) row_switch<ADJ, GB, RPT, true, T2, Real>(v, w, R, ok, dot);
+    else row_switch<ADJ, GB, RPT, false, T2, Real>(v, w, R, ok, dot);
 }
 
 // Register qubits per group: 4 for forward passes, 3 for the adjoint sweep (psi and lambda
@@ -222,10 +280,11 @@ __device__ __forceinline__ void row_gate(T2 *v, T2 *w, const GateRegs<Real> &R, 
 template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
 
 // Apply the pass's register groups to the tile tp (and lambda tile tl if ADJ) whose global
-// base index is `base`. Adjoint: for a gate with slot >= 0 the warp partial of
-// Re <lambda| dU psi> (summed over the warp in the state's precision) is added to
-// acc[slot * nwarps + warp]. Every executed group ends with a block barrier.
-template <typename Real, bool ADJ, int GB = GroupBits<ADJ>::v>
+// base index is `base`. Each thread holds RPT rows of 2^GB elements at a time. Adjoint: for a
+// gate with slot >= 0 the warp partial of Re <lambda| dU psi> (summed over the warp in the
+// state's precision) is added to acc[slot * nwarps + warp]. Every executed group ends with a
+// block barrier.
+template <typename Real, bool ADJ, int GB = GroupBits<ADJ>::v, int RPT = 1, bool FOLD = false>
 __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typename TileT<Real>::T2 *tl, uint64_t base,
                                              int k, const TileGroup *groups, int group_count, const SGate<Real> *gates,
                                              const Real *cs, Acc<Real> *acc) {
@@ -249,33 +308,45 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
 #pragma unroll
         for (int i = 0; i < 4; ++i) qs_[i] = Gr.qsw[i];
         const uint32_t rows = 1u << (k - r);
-        for (uint32_t rb = 0; rb < rows; rb += blockDim.x) {
-            const uint32_t rho = rb + tid;
-            const bool active = rho < rows;
-            uint32_t ra = 0;
-            for (int s = 0; s < Gr.nrseg; ++s) ra |= (rho << Gr.rshift[s]) & Gr.rmask[s];
-            const uint32_t rs = tile_swizzle(ra, SW);
-            T2 v[E], w[ADJ ? E : 1];
+        const uint32_t step = blockDim.x * RPT;
+        const bool all_rows = (rows % step) == 0;  // uniform: no thread idles in any row block
+        for (uint32_t rb = 0; rb < rows; rb += step) {
+            uint32_t ra[RPT], rs[RPT];
+            bool active[RPT];
+            T2 v[RPT][E], w[RPT][ADJ ? E : 1];
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const uint32_t ps = rs ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^ ((e & 4) ? qs_[2] : 0u) ^
-                                    ((e & 8) ? qs_[3] : 0u);
-                if (active && e < (1 << r)) {
-                    v[e] = tp[ps];
-                    if (ADJ) w[e] = tl[ps];
-                } else {
-                    v[e] = T2{0, 0};
-                    if (ADJ) w[e] = T2{0, 0};
+            for (int j = 0; j < RPT; ++j) {
+                const uint32_t rho = rb + j * blockDim.x + tid;
+                active[j] = rho < rows;
+                ra[j] = 0;
+                for (int s = 0; s < Gr.nrseg; ++s) ra[j] |= (rho << Gr.rshift[s]) & Gr.rmask[s];
+                rs[j] = tile_swizzle(ra[j], SW);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t ps = rs[j] ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
+                                        ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u);
+                    if (active[j] && e < (1 << r)) {
+                        v[j][e] = tp[ps];
+                        if (ADJ) w[j][e] = tl[ps];
+                    } else {
+                        v[j][e] = T2{0, 0};
+                        if (ADJ) w[j][e] = T2{0, 0};
+                    }
                 }
             }
-            for (int g = 0; g < Gr.gate_count; ++g) {
-                const SGate<Real> &G = gates[Gr.gate_begin + g];
-                if (Gr.hctrl && (base & G.hmask) != G.hvals) continue;  // uniform
+            const int gb = Gr.gate_begin, gc = Gr.gate_count;
+            for (int g = 0; g < gc; ++g) {
+                if (Gr.hctrl && (base & gates[gb + g].hmask) != gates[gb + g].hvals) continue;  // uniform
+                GateRaw<Real> cr;
+                fetch_gate<Real, ADJ>(gates[gb + g], cr);
                 GateRegs<Real> R;
-                load_gate<Real>(G, R, cs, ADJ);
-                const bool row_ok = active && ((ra & R.crm) == R.crv);
+                decode_gate<Real>(cr, R, cs, ADJ);
                 Real dot = 0;
-                row_gate<ADJ, GB, T2, Real>(v, w, R, row_ok, dot);
+                bool ok[RPT];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) ok[j] = active[j] && ((ra[j] & R.crm) == R.crv);
+                // uniform: without row controls and with every thread on a row, no predicate
+                row_gate<ADJ, GB, RPT, FOLD, T2, Real>(v, w, R, ok, !(all_rows && R.crm == 0), dot);
                 if (ADJ && R.slot >= 0) {
                     Real d = dot;
 #pragma unroll
@@ -284,12 +355,15 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                 }
             }
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const uint32_t ps = rs ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^ ((e & 4) ? qs_[2] : 0u) ^
-                                    ((e & 8) ? qs_[3] : 0u);
-                if (active && e < (1 << r)) {
-                    tp[ps] = v[e];
-                    if (ADJ) tl[ps] = w[e];
+            for (int j = 0; j < RPT; ++j) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t ps = rs[j] ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
+                                        ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u);
+                    if (active[j] && e < (1 << r)) {
+                        tp[ps] = v[j][e];
+                        if (ADJ) tl[ps] = w[j][e];
+                    }
                 }
             }
         }

@@ -121,13 +121,71 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
     return h;
 }
 
+// Forward application only: runs of consecutive gates with the same target and the same
+// controls act on the same pairs, so their product (U_last ... U_first, formed in double
+// precision) replaces them; e.g. RY then RZ on one qubit become one launch or one tile-pass
+// gate. Exchange products that are the identity drop out. The baseline comparator
+// (QS_FLAG_MASKED) and the adjoint sweep keep every gate.
+static void cmatmul2(const double *A, const double *B, double *C) {  // C = A B, row-major 2x2
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < 2; ++k) {
+                const double ar = A[2 * (2 * i + k)], ai = A[2 * (2 * i + k) + 1];
+                const double br = B[2 * (2 * k + j)], bi = B[2 * (2 * k + j) + 1];
+                re += ar * br - ai * bi;
+                im += ar * bi + ai * br;
+            }
+            C[2 * (2 * i + j)] = re;
+            C[2 * (2 * i + j) + 1] = im;
+        }
+}
+
+static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans) {
+    std::vector<GatePlan> out;
+    out.reserve(plans.size());
+    size_t i = 0;
+    while (i < plans.size()) {
+        size_t j = i + 1;
+        while (j < plans.size() && plans[j].t == plans[i].t && plans[j].ctrl_mask == plans[i].ctrl_mask &&
+               plans[j].ctrl_vals == plans[i].ctrl_vals)
+            ++j;
+        if (j == i + 1) {
+            out.push_back(plans[i]);
+        } else {
+            double U[8], T[8];
+            std::memcpy(U, plans[i].Ufull, sizeof(U));
+            for (size_t q = i + 1; q < j; ++q) {
+                cmatmul2(plans[q].Ufull, U, T);
+                std::memcpy(U, T, sizeof(U));
+            }
+            GatePlan m;
+            char e2[200];
+            // an exact exchange product stays an exchange (bit-exact), else the planner
+            // classifies the product's structure
+            if (plan_gate(s->n, s->dtype, plans[i].t, plans[i].ctrl_mask, plans[i].ctrl_vals, U, QS_GATE_U, -1, &m, e2,
+                          sizeof(e2)))
+                out.push_back(m);
+            else
+                out.insert(out.end(), plans.begin() + i, plans.begin() + j);  // not finite: keep the run
+        }
+        i = j;
+    }
+    plans.swap(out);
+}
+
 static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, cudaStream_t st,
                               bool masked = false) {
     for (size_t i = 0; i < plans.size(); ++i) {
         cudaError_t e = masked ? launch_gate_masked(s->dtype, s->psi, plans[i], plans[i].ctrl_mask,
                                                     plans[i].ctrl_vals, st)
                                : launch_gate(s->dtype, s->psi, plans[i], st);
-        if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit launch");
+        if (e != cudaSuccess) {
+            char what[128];
+            std::snprintf(what, sizeof(what), "qs_apply_circuit launch (gate %zu: t=%d op=%d layout=%d r=%d)", i,
+                          plans[i].t, plans[i].op, plans[i].layout, plans[i].r);
+            return cuda_fail(e, what);
+        }
     }
     return QS_OK;
 }
@@ -177,6 +235,8 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
     const TileGroup *groups = dev_table ? table_groups(prog, dev_table) : nullptr;
     const RegGate *gates = dev_table ? table_gates(prog, dev_table) : nullptr;
     for (const FusedOp &op : prog.ops) {
+        if (op.pass >= (int)prog.passes.size() || (op.pass < 0 && (op.gate < 0 || (size_t)op.gate >= plans.size())))
+            return set_error(QS_EINVAL, "fused program refers to a gate or pass it does not hold");
         cudaError_t e;
         if (op.pass >= 0) {
             e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], groups, gates, part, P, st);
@@ -187,7 +247,16 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
             e = launch_adj_step(s->dtype, s->psi, lam, plans[op.gate], (*dus)[op.gate],
                                 slot >= 0 ? part + (size_t)slot * P : nullptr, st);
         }
-        if (e != cudaSuccess) return cuda_fail(e, "fused program launch");
+        if (e != cudaSuccess) {
+            char what[160];
+            if (op.pass >= 0)
+                std::snprintf(what, sizeof(what), "fused program launch (tile pass %d, k=%d, %d gates)", op.pass,
+                              prog.passes[op.pass].k, prog.passes[op.pass].gate_count);
+            else
+                std::snprintf(what, sizeof(what), "fused program launch (gate %d: t=%d op=%d layout=%d r=%d)", op.gate,
+                              plans[op.gate].t, plans[op.gate].op, plans[op.gate].layout, plans[op.gate].r);
+            return cuda_fail(e, what);
+        }
     }
     return QS_OK;
 }
@@ -221,6 +290,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         if (!plan_record(s, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     const bool masked = (flags & QS_FLAG_MASKED) != 0;
+    if (!masked) merge_runs(s, plans);
     if (masked) {
         // baseline schedule: every pair iteration launched, the controls tested per unit,
         // the general update with the full matrix (as the Section III-A kernel does)
@@ -234,8 +304,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     FusedProgram prog;
     if (fuse) {
-        std::vector<int> seq(count);
-        for (size_t i = 0; i < count; ++i) seq[i] = (int)i;
+        std::vector<int> seq(plans.size());  // after merging: fewer plans than records
+        for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
         plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog);
     }
     const size_t table_bytes = fuse ? program_table_bytes(prog) : 0;
@@ -376,10 +446,12 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     FusedProgram pf, pa;
     std::vector<const double *> dusp(count, nullptr);
+    merge_runs(s, fwd);  // the forward pass needs no per-gate state
     if (fuse) {
-        std::vector<int> seq(count);
-        for (size_t i = 0; i < count; ++i) seq[i] = (int)i;
+        std::vector<int> seq(fwd.size());
+        for (size_t i = 0; i < fwd.size(); ++i) seq[i] = (int)i;
         plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &pf);
+        seq.resize(count);
         for (size_t i = 0; i < count; ++i) {
             seq[i] = (int)(count - 1 - i);
             if (slot_of[i] >= 0) dusp[i] = &dus[8 * slot_of[i]];

@@ -258,3 +258,55 @@ def test_precision_circuit_n32(qs):
         s64.close()
         del b128, b64
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mode", ["circuit", "fuse"])
+def test_runs_on_one_target_match_oracle(qs, dtype, mode):
+    """Forward application multiplies runs of consecutive gates with the same target and
+    controls into one matrix: runs of 2-5 gates (Haar, parameterised RY / RZ, exchanges, with
+    and without controls) against the oracle applying every gate; runs of exchanges alone stay
+    bit-exact (X X X = X, X X = identity)."""
+    n = 13
+    rng = np.random.default_rng(77)
+    gl = []
+    theta = rng.uniform(0, 6.3, size=64)
+    p = 0
+    for r in range(40):
+        t = int(rng.integers(0, n))
+        others = [q for q in range(n) if q != t]
+        c = int(rng.integers(0, 3))
+        ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+        vals = [int(b) for b in rng.integers(0, 2, size=c)]
+        for _ in range(int(rng.integers(2, 6))):
+            u = rng.random()
+            if u < 0.3:
+                gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_X))
+            elif u < 0.5 and p < 64:
+                gl.append(W.make_gate(t, None, ctrls, vals, kind=W.KIND_RY if u < 0.4 else W.KIND_RZ, param=p))
+                p += 1
+            else:
+                gl.append(W.make_gate(t, W.haar_2x2(rng), ctrls, vals))
+    gates = W.gate_list(gl)
+    psi0 = random_state(n, dtype, 78)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates, theta)
+    with qs.State(n, dtype) as st:
+        st.from_numpy(psi0)
+        st.apply_circuit(gates, theta, flags=qs.QS_FLAG_FUSE if mode == "fuse" else 0)
+        got = c128_of(st.to_numpy())
+    assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype]
+    # exchanges only: runs of 1-4 X gates on one target, bit-exact
+    xs = []
+    for r in range(30):
+        t = int(rng.integers(0, n))
+        m = [q for q in range(n) if q != t][: int(rng.integers(0, 3))]
+        xs += [W.make_gate(t, None, m, kind=W.KIND_X)] * int(rng.integers(1, 5))
+    xs = W.gate_list(xs)
+    ref = psi0.copy().astype(np.complex128)
+    oracle.run_circuit(ref, n, xs)
+    with qs.State(n, dtype) as st:
+        st.from_numpy(psi0)
+        st.apply_circuit(xs, flags=qs.QS_FLAG_FUSE if mode == "fuse" else 0)
+        got = st.to_numpy()
+    assert np.array_equal(got, ref.astype(NP[dtype]))
