@@ -1,0 +1,229 @@
+// k_diag.cu -- one pass over the state for a run of diagonal gates (see k_diag.cuh).
+#include <algorithm>
+#include <cstring>
+
+#include "k_diag.cuh"
+#include "k_gate.cuh"
+
+namespace qs {
+
+bool make_diag_gate(const GatePlan &p, DiagGate *g) {
+    if (p.op != OP_DIAG && p.op != OP_SIDE) return false;
+    std::memset(g, 0, sizeof(*g));
+    const double *U = p.Ufull;  // diag(a, d): a = U[0..1], d = U[6..7]
+    g->a[0] = U[0];
+    g->a[1] = U[1];
+    g->d[0] = U[6];
+    g->d[1] = U[7];
+    g->aone = U[0] == 1.0 && U[1] == 0.0;
+    g->done = U[6] == 1.0 && U[7] == 0.0;
+    const uint64_t lo = (1ull << kDiagChunkBits) - 1ull;
+    g->hm = p.ctrl_mask & ~lo;
+    g->hv = p.ctrl_vals & ~lo;
+    const uint64_t clo = p.ctrl_mask & lo;
+    const bool tlo = p.t < kDiagChunkBits;
+    g->thi = tlo ? 0ull : (1ull << p.t);
+    g->tlo = tlo ? (1 << p.t) : 0;
+    const int nlo = __builtin_popcountll(clo) + (tlo ? 1 : 0);
+    const uint64_t warp_lo = (1ull << kDiagWarpBits) - 1ull;
+    if (nlo == 0 && ((p.ctrl_mask | (1ull << p.t)) & warp_lo) == 0 && p.n >= kDiagWarpBits) {
+        g->cls = DIAG_WARP;
+    } else if (nlo == 0) {
+        g->cls = DIAG_HI;
+    } else if (nlo == 1) {
+        g->cls = DIAG_LO1;
+        if (tlo) {
+            g->u = p.t;
+            g->ut = 1;
+        } else {
+            g->u = __builtin_ctzll(clo);
+            g->ut = 0;
+            g->cv = (int32_t)((p.ctrl_vals >> g->u) & 1ull);
+        }
+    } else {
+        g->cls = DIAG_LOM;
+        g->lm = (int32_t)clo;
+        g->lv = (int32_t)(p.ctrl_vals & lo);
+    }
+    return true;
+}
+
+namespace {
+
+template <typename Real> struct SDiag {
+    uint64_t hm, hv, thi;
+    int32_t cls, u, ut, cv, lm, lv, tlo, aone, done, pad;
+    Real a[2], d[2];
+};
+
+// A chunk of 8 amplitudes: four 16-byte vectors (complex64) or eight (complex128).
+__device__ __forceinline__ void ld8(const float2 *p, float2 *v) {
+    Vec<float, 4>::ld(p, v);
+    Vec<float, 4>::ld(p + 4, v + 4);
+}
+__device__ __forceinline__ void st8(float2 *p, const float2 *v) {
+    Vec<float, 4>::st(p, v);
+    Vec<float, 4>::st(p + 4, v + 4);
+}
+__device__ __forceinline__ void ld8(const double2 *p, double2 *v) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = p[i];
+}
+__device__ __forceinline__ void st8(double2 *p, const double2 *v) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = v[i];
+}
+
+template <typename T2, typename Real>
+__device__ __forceinline__ T2 cm(const Real *f, T2 x) {
+    return cmul<T2, Real>(f[0], f[1], x);
+}
+
+// s0[u], s1[u]: chunk scalars for elements whose bit u is 0 / 1 (u = 0, 1, 2), unrolled so
+// they stay in registers.
+template <typename T2, typename Real>
+__device__ __forceinline__ void mul_bit(T2 (&s0)[3], T2 (&s1)[3], int u, int val, const Real *f) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if (b == u) {
+            if (val) s1[b] = cm<T2, Real>(f, s1[b]);
+            else s0[b] = cm<T2, Real>(f, s0[b]);
+        }
+    }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restrict__ psi, const DiagGate *__restrict__ gates,
+                                                  int count, DiagCounts nc, uint64_t nchunks) {
+    using T2 = typename CxT<Real>::T;
+    constexpr int E = 1 << kDiagChunkBits;
+    __shared__ SDiag<Real> sg[kDiagMaxGates];
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const DiagGate &G = gates[i];
+        SDiag<Real> &S = sg[i];
+        S.hm = G.hm;
+        S.hv = G.hv;
+        S.thi = G.thi;
+        S.cls = G.cls;
+        S.u = G.u;
+        S.ut = G.ut;
+        S.cv = G.cv;
+        S.lm = G.lm;
+        S.lv = G.lv;
+        S.tlo = G.tlo;
+        S.aone = G.aone;
+        S.done = G.done;
+        S.a[0] = (Real)G.a[0];
+        S.a[1] = (Real)G.a[1];
+        S.d[0] = (Real)G.d[0];
+        S.d[1] = (Real)G.d[1];
+    }
+    __syncthreads();
+    const int w_end = nc.ncls[DIAG_WARP], h_end = w_end + nc.ncls[DIAG_HI], l1_end = h_end + nc.ncls[DIAG_LO1];
+    const bool any_lo1 = nc.ncls[DIAG_LO1] > 0, any_lom = nc.ncls[DIAG_LOM] > 0;  // uniform
+    const int lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay aligned
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += stride) {
+        const uint64_t base = c << kDiagChunkBits;
+        T2 s = T2{1, 0};
+        bool touched = false;
+        if (w_end > 0) {
+            // gates on bits >= 8: each lane takes every 32nd, then the warp multiplies the partial
+            // products (all 32 chunks of the warp are in range: nchunks is a multiple of 32 here)
+            for (int g = lane; g < w_end; g += 32) {
+                const SDiag<Real> &G = sg[g];
+                if ((base & G.hm) != G.hv) continue;
+                const bool tb = (base & G.thi) != 0;
+                if (tb ? !G.done : !G.aone) {
+                    s = cm<T2, Real>(tb ? G.d : G.a, s);
+                    touched = true;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                T2 q;
+                q.x = __shfl_xor_sync(0xffffffffu, s.x, o);
+                q.y = __shfl_xor_sync(0xffffffffu, s.y, o);
+                s = cmul<T2, Real>(q.x, q.y, s);
+            }
+            touched = __any_sync(0xffffffffu, touched);
+        }
+        for (int g = w_end; g < h_end; ++g) {
+            const SDiag<Real> &G = sg[g];
+            if ((base & G.hm) != G.hv) continue;
+            const bool tb = (base & G.thi) != 0;
+            if (tb ? !G.done : !G.aone) {
+                s = cm<T2, Real>(tb ? G.d : G.a, s);
+                touched = true;
+            }
+        }
+        T2 s0[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}}, s1[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}};
+        for (int g = h_end; g < l1_end; ++g) {
+            const SDiag<Real> &G = sg[g];
+            if ((base & G.hm) != G.hv) continue;
+            const bool tb = (base & G.thi) != 0;
+            if (G.ut) {  // bit u is the target: a where it is 0, d where it is 1
+                if (!G.aone) mul_bit<T2, Real>(s0, s1, G.u, 0, G.a);
+                if (!G.done) mul_bit<T2, Real>(s0, s1, G.u, 1, G.d);
+                touched |= !(G.aone && G.done);
+            } else if (tb ? !G.done : !G.aone) {  // bit u is a control with value cv
+                mul_bit<T2, Real>(s0, s1, G.u, G.cv, tb ? G.d : G.a);
+                touched = true;
+            }
+        }
+        T2 acc[E];
+        if (any_lom) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] = T2{1, 0};
+            for (int g = l1_end; g < count; ++g) {
+                const SDiag<Real> &G = sg[g];
+                if ((base & G.hm) != G.hv) continue;
+                const bool tb = (base & G.thi) != 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & G.lm) != G.lv) continue;
+                    const bool bt = G.tlo ? (e & G.tlo) != 0 : tb;
+                    if (bt ? !G.done : !G.aone) {
+                        acc[e] = cm<T2, Real>(bt ? G.d : G.a, acc[e]);
+                        touched = true;
+                    }
+                }
+            }
+        }
+        if (!touched) continue;  // every factor of this chunk is 1
+        T2 x[E];
+        ld8(psi + base, x);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            T2 f = s;
+            if (any_lo1) {
+                f = cmul<T2, Real>((e & 1) ? s1[0].x : s0[0].x, (e & 1) ? s1[0].y : s0[0].y, f);
+                f = cmul<T2, Real>((e & 2) ? s1[1].x : s0[1].x, (e & 2) ? s1[1].y : s0[1].y, f);
+                f = cmul<T2, Real>((e & 4) ? s1[2].x : s0[2].x, (e & 4) ? s1[2].y : s0[2].y, f);
+            }
+            if (any_lom) f = cmul<T2, Real>(acc[e].x, acc[e].y, f);
+            x[e] = cmul<T2, Real>(f.x, f.y, x[e]);
+        }
+        st8(psi + base, x);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_diag_run(int dtype, void *psi, int n, const DiagGate *gates, int count, DiagCounts nc,
+                            cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    if (count > kDiagMaxGates || n < kDiagChunkBits ||
+        nc.ncls[0] + nc.ncls[1] + nc.ncls[2] + nc.ncls[3] != count || (nc.ncls[DIAG_WARP] > 0 && n < kDiagWarpBits))
+        return cudaErrorInvalidValue;
+    const uint64_t nchunks = 1ull << (n - kDiagChunkBits);
+    const uint64_t cap = (uint64_t)device_sm_count() * 8;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((nchunks + 255) / 256, cap));
+    if (dtype == QS_C64)
+        k_diag_run<float><<<grid, 256, 0, st>>>(reinterpret_cast<float2 *>(psi), gates, count, nc, nchunks);
+    else
+        k_diag_run<double><<<grid, 256, 0, st>>>(reinterpret_cast<double2 *>(psi), gates, count, nc, nchunks);
+    return cudaGetLastError();
+}
+
+}  // namespace qs

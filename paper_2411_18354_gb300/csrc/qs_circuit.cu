@@ -234,11 +234,17 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
                                 const std::vector<int> *slots, double *part, size_t P, cudaStream_t st) {
     const TileGroup *groups = dev_table ? table_groups(prog, dev_table) : nullptr;
     const RegGate *gates = dev_table ? table_gates(prog, dev_table) : nullptr;
+    const DiagGate *dgates = dev_table ? table_dgates(prog, dev_table) : nullptr;
     for (const FusedOp &op : prog.ops) {
-        if (op.pass >= (int)prog.passes.size() || (op.pass < 0 && (op.gate < 0 || (size_t)op.gate >= plans.size())))
-            return set_error(QS_EINVAL, "fused program refers to a gate or pass it does not hold");
+        const bool bad = op.drun >= 0 ? (op.drun >= (int)prog.druns.size() || !dgates)
+                                      : (op.pass >= (int)prog.passes.size() ||
+                                         (op.pass < 0 && (op.gate < 0 || (size_t)op.gate >= plans.size())));
+        if (bad) return set_error(QS_EINVAL, "fused program refers to a gate or pass it does not hold");
         cudaError_t e;
-        if (op.pass >= 0) {
+        if (op.drun >= 0) {
+            const DiagRun &r = prog.druns[op.drun];
+            e = launch_diag_run(s->dtype, s->psi, s->n, dgates + r.begin, r.count, r.nc, st);
+        } else if (op.pass >= 0) {
             e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], groups, gates, part, P, st);
         } else if (!lam) {
             e = launch_gate(s->dtype, s->psi, plans[op.gate], st);
@@ -249,7 +255,10 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
         }
         if (e != cudaSuccess) {
             char what[160];
-            if (op.pass >= 0)
+            if (op.drun >= 0)
+                std::snprintf(what, sizeof(what), "fused program launch (diagonal run %d, %d gates)", op.drun,
+                              prog.druns[op.drun].count);
+            else if (op.pass >= 0)
                 std::snprintf(what, sizeof(what), "fused program launch (tile pass %d, k=%d, %d gates)", op.pass,
                               prog.passes[op.pass].k, prog.passes[op.pass].gate_count);
             else

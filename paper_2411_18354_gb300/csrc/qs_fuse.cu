@@ -228,6 +228,8 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     prog->gates.clear();
     prog->groups.clear();
     prog->gate_src.clear();
+    prog->druns.clear();
+    prog->dgates.clear();
     max_gates = std::max(1, std::min(max_gates, kTileMaxGates));
     // k >= b0 + 1 so that any single target fits next to the b0 low qubits (n permitting)
     const int b0 = dtype == QS_C64 ? 4 : 3;
@@ -235,8 +237,60 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     const int b = std::min(k, b0);
     const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
     const bool adjoint = dus != nullptr;
+    const bool diag_runs = !adjoint && allow_single && n >= kDiagChunkBits;
+    // drun[j]: diagonal gates in the run of diagonal gates (identities included) starting at j
+    std::vector<int> drun(seq.size() + 1, 0);
+    if (diag_runs)
+        for (size_t j = seq.size(); j-- > 0;) {
+            const GatePlan &p = plans[seq[j]];
+            drun[j] = p.units == 0 ? drun[j + 1] : ((p.op == OP_DIAG || p.op == OP_SIDE) ? drun[j + 1] + 1 : 0);
+        }
     size_t i = 0;
     while (i < seq.size()) {
+        if (diag_runs) {
+            // a run of diagonal gates (identities included) goes to one k_diag pass per
+            // kDiagMaxGates gates: it commutes, and a chunk's factor costs a few operations
+            size_t j = i;
+            int real = 0;
+            while (j < seq.size()) {
+                const GatePlan &p = plans[seq[j]];
+                if (p.units == 0) {
+                    ++j;
+                    continue;
+                }
+                if (p.op != OP_DIAG && p.op != OP_SIDE) break;
+                ++real;
+                ++j;
+            }
+            if (real >= kDiagMinRun) {
+                std::vector<DiagGate> run;
+                for (size_t q = i; q < j; ++q) {
+                    const GatePlan &p = plans[seq[q]];
+                    if (p.units == 0) continue;
+                    DiagGate dg;
+                    make_diag_gate(p, &dg);
+                    run.push_back(dg);
+                }
+                // the gates commute: order them by class for the kernel's loops
+                std::stable_sort(run.begin(), run.end(),
+                                 [](const DiagGate &a, const DiagGate &b) { return a.cls < b.cls; });
+                for (size_t q0 = 0; q0 < run.size(); q0 += kDiagMaxGates) {
+                    const size_t q1 = std::min(run.size(), q0 + kDiagMaxGates);
+                    DiagRun r;
+                    r.begin = (int)prog->dgates.size();
+                    r.count = (int)(q1 - q0);
+                    r.nc = DiagCounts{{0, 0, 0, 0}};
+                    for (size_t q = q0; q < q1; ++q) {
+                        ++r.nc.ncls[run[q].cls];
+                        prog->dgates.push_back(run[q]);
+                    }
+                    prog->ops.push_back({-1, -1, (int)prog->druns.size()});
+                    prog->druns.push_back(r);
+                }
+                i = j;
+                continue;
+            }
+        }
         uint64_t L = low;
         double frac = 0.0, singles = 0.0;
         const double cc = pass_gate_cost(dtype);
@@ -245,6 +299,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         size_t j = i;
         while (j < seq.size() && (int)members.size() < max_gates) {
             const GatePlan &p = plans[seq[j]];
+            if (diag_runs && j > i && drun[j] >= kDiagMinRun) break;  // a diagonal pass follows
             const bool param = adjoint && (*dus)[seq[j]] != nullptr;
             if (p.units == 0 && !param) {  // identity: nothing to apply
                 members.push_back(-1 - seq[j]);
@@ -315,15 +370,22 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
 
 static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-size_t program_table_bytes(const FusedProgram &p) {
-    return align16(p.groups.size() * sizeof(TileGroup)) + p.gates.size() * sizeof(RegGate);
+static size_t dgate_offset(const FusedProgram &p) {
+    return align16(p.groups.size() * sizeof(TileGroup)) + align16(p.gates.size() * sizeof(RegGate));
 }
+
+size_t program_table_bytes(const FusedProgram &p) { return dgate_offset(p) + p.dgates.size() * sizeof(DiagGate); }
 
 void pack_program_table(const FusedProgram &p, void *host_dst) {
     char *d = static_cast<char *>(host_dst);
     if (!p.groups.empty()) std::memcpy(d, p.groups.data(), p.groups.size() * sizeof(TileGroup));
     if (!p.gates.empty())
         std::memcpy(d + align16(p.groups.size() * sizeof(TileGroup)), p.gates.data(), p.gates.size() * sizeof(RegGate));
+    if (!p.dgates.empty()) std::memcpy(d + dgate_offset(p), p.dgates.data(), p.dgates.size() * sizeof(DiagGate));
+}
+
+const DiagGate *table_dgates(const FusedProgram &p, const void *dev_base) {
+    return reinterpret_cast<const DiagGate *>(static_cast<const char *>(dev_base) + dgate_offset(p));
 }
 
 const TileGroup *table_groups(const FusedProgram &, const void *dev_base) {

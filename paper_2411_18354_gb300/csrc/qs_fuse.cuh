@@ -3,13 +3,20 @@
 
 #include <vector>
 
+#include "k_diag.cuh"
 #include "k_tile.cuh"
 
 namespace qs {
 
 struct FusedOp {
-    int pass;  // >= 0: index into passes; -1: single gate
-    int gate;  // single gate: index into the plan list
+    int pass;       // >= 0: index into passes; -1: single gate or diagonal run
+    int gate;       // single gate: index into the plan list
+    int drun = -1;  // >= 0: index into druns (a run of diagonal gates in one pass, k_diag)
+};
+
+struct DiagRun {
+    int begin, count;  // into FusedProgram::dgates (sorted by class)
+    DiagCounts nc;
 };
 
 struct FusedProgram {
@@ -18,14 +25,18 @@ struct FusedProgram {
     std::vector<TileGroup> groups;  // all passes' register groups
     std::vector<RegGate> gates;     // all groups' gates
     std::vector<int> gate_src;      // plan index each RegGate came from
+    std::vector<DiagRun> druns;
+    std::vector<DiagGate> dgates;   // all diagonal runs' gates
 };
 
-// Byte size and packing of a program's device table: groups first, then gates (16-byte aligned).
+// Byte size and packing of a program's device table: groups, then gates, then the diagonal
+// runs' gates (each part 16-byte aligned).
 size_t program_table_bytes(const FusedProgram &p);
 void pack_program_table(const FusedProgram &p, void *host_dst);
 // Device pointers of the two parts, given the table's device base address.
 const TileGroup *table_groups(const FusedProgram &p, const void *dev_base);
 const RegGate *table_gates(const FusedProgram &p, const void *dev_base);
+const DiagGate *table_dgates(const FusedProgram &p, const void *dev_base);
 
 // Plan the gates plans[seq[0]], plans[seq[1]], ... (execution order). For the adjoint
 // sweep, `dus[g]` is dU/dtheta of gate g (nullptr when g has no parameter) and `gslots[g]` its
@@ -37,5 +48,8 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
                 int max_gates = kTileMaxGates, bool allow_single = true, int group_bits = 0);
 // group_bits: register qubits per group; 0 = kGroupBits for forward programs and
 // kGroupBitsAdjoint when dus != nullptr. The kernel that runs the program must use the same.
+// Forward programs with allow_single (not the batched kernel) also turn runs of at least
+// kDiagMinRun consecutive diagonal gates into diagonal-run ops.
+constexpr int kDiagMinRun = 4;
 
 }  // namespace qs

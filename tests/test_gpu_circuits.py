@@ -310,3 +310,49 @@ def test_runs_on_one_target_match_oracle(qs, dtype, mode):
         st.apply_circuit(xs, flags=qs.QS_FLAG_FUSE if mode == "fuse" else 0)
         got = st.to_numpy()
     assert np.array_equal(got, ref.astype(NP[dtype]))
+
+
+def _diag_gate(rng, n, t, ctrls, vals):
+    u = rng.random()
+    if u < 0.35:   # one-sided: phase on the |1> side (R_m, S, T, CZ-like)
+        D = np.diag([1.0, np.exp(1j * rng.uniform(0, 6.3))])
+    elif u < 0.5:  # one-sided on the |0> side
+        D = np.diag([np.exp(1j * rng.uniform(0, 6.3)), 1.0])
+    elif u < 0.6:  # identity (drops out)
+        D = np.eye(2)
+    elif u < 0.9:  # general diagonal phase
+        D = np.diag(np.exp(1j * rng.uniform(0, 6.3, 2)))
+    else:          # non-unit modulus (the library does not require unitarity)
+        D = np.diag(rng.uniform(0.97, 1.03, 2) * np.exp(1j * rng.uniform(0, 6.3, 2)))
+    return W.make_gate(t, D, ctrls, vals)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_diagonal_runs_match_oracle(qs, dtype):
+    """Fused programs turn runs of >= 4 diagonal gates into one pass (k_diag): targets and
+    controls on the lowest three qubits (inside a chunk) and above, control values 0 and 1,
+    one-sided / general / identity diagonals, runs longer than one launch (64 gates), mixed
+    with non-diagonal gates; n = 3..16 against the oracle."""
+    rng = np.random.default_rng(314)
+    for n in (3, 4, 5, 9, 16):
+        gl = []
+        for blk in range(6):
+            for _ in range(int(rng.integers(1, 4))):
+                gl.append(W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng)))
+            for _ in range(int(rng.choice([3, 4, 9, 70]))):
+                t = int(rng.integers(0, n))
+                others = [q for q in range(n) if q != t]
+                c = int(rng.integers(0, min(3, n - 1) + 1))
+                ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+                vals = [int(b) for b in rng.integers(0, 2, size=c)]
+                gl.append(_diag_gate(rng, n, t, ctrls, vals))
+        gates = W.gate_list(gl)
+        psi0 = random_state(n, dtype, 300 + n)
+        ref = c128_of(psi0).copy()
+        oracle.run_circuit(ref, n, gates)
+        for flags in (qs.QS_FLAG_FUSE, qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH):
+            with qs.State(n, dtype) as st:
+                st.from_numpy(psi0)
+                st.apply_circuit(gates, flags=flags)
+                got = c128_of(st.to_numpy())
+            assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), (n, flags)
