@@ -53,6 +53,10 @@ def parse_args():
                     help="small profiling case: 2 layers of the ansatz at n=24, fused forward then fused gradient")
     ap.add_argument("--ncu-reduce", action="store_true",
                     help="small profiling case: <Z_i> + norm of an n=27 state, twice")
+    ap.add_argument("--tile-costs", action="store_true",
+                    help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
+    ap.add_argument("--ncu-qft", action="store_true",
+                    help="profiling case: the fused 29-qubit QFT, twice (diagonal-run passes)")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="small profiling case: one batch launch of 304 states (n=16, 2 layers of the ansatz)")
     return ap.parse_args()
@@ -694,6 +698,70 @@ def run_ncu_batch(args):
     print("ncu batch case done")
 
 
+def run_tile_costs(args):
+    """Device time of a fused pass of 1, 16 and 64 gates of one kind on local qubits 0..11
+    (n = 24, complex64, tiles of 2^12 amplitudes); the slope is the per-gate cost inside a pass."""
+    import numpy as np
+
+    os.environ["QS_TILE_BITS"] = "12"
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    n = 24
+    rng = np.random.default_rng(0)
+
+    def circ(kind, count):
+        gl = []
+        for i in range(count):
+            t = i % 12
+            q = (t // 4) * 4 + ((t % 4) + 1) % 4  # a control in the same 4-qubit group
+            if kind == "real":
+                th = rng.uniform(0, 6)
+                c, s_ = np.cos(th / 2), np.sin(th / 2)
+                gl.append(W.make_gate(t, np.array([[c, -s_], [s_, c]])))
+            elif kind == "diagonal":
+                th = rng.uniform(0, 6)
+                gl.append(W.make_gate(t, np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)])))
+            elif kind == "general":
+                gl.append(W.make_gate(t, W.haar_2x2(rng)))
+            elif kind == "exchange":
+                gl.append(W.make_gate(t, None, (), kind=W.KIND_X))
+            elif kind == "cnot_in_row":
+                gl.append(W.make_gate(t, None, (q,), kind=W.KIND_X))
+            else:
+                gl.append(W.make_gate(t, W.haar_2x2(rng), (q,)))
+        return W.gate_list(gl)  # targets cycle over 0..11: neighbours never share one (no merging)
+
+    out = {}
+    with qs.State(n, "c64") as st:
+        st.apply_gate(0, W.H_MATRIX)
+        for kind in ("real", "diagonal", "general", "exchange", "cnot_in_row", "controlled_general_in_row"):
+            t = {}
+            for cnt in (1, 16, 64):
+                g = circ(kind, cnt)
+                t[cnt] = _events_ms(lambda: st.apply_circuit(g, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH), 10)
+            out[kind] = {"pass_us": {str(k): round(v * 1e3, 1) for k, v in t.items()},
+                         "us_per_gate": round((t[64] - t[16]) / 48 * 1e3, 2)}
+    print(json.dumps({"tile_costs_n24_c64": out}), flush=True)
+
+
+def run_ncu_qft(args):
+    """Profiling case: the 29-qubit QFT with QS_FLAG_FUSE, twice; no timing."""
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    g = W.qft_circuit(29)
+    with qs.State(29, "c64") as st:
+        for _ in range(2):
+            st.apply_circuit(g, flags=qs.QS_FLAG_FUSE)
+        torch.cuda.synchronize()
+    print("ncu qft case done")
+
+
 def main():
     args = parse_args()
     if args.ncu_case is not None:
@@ -701,6 +769,12 @@ def main():
         return
     if args.ncu_fused:
         run_ncu_fused(args)
+        return
+    if args.tile_costs:
+        run_tile_costs(args)
+        return
+    if args.ncu_qft:
+        run_ncu_qft(args)
         return
     if args.ncu_batch:
         run_ncu_batch(args)

@@ -17,6 +17,7 @@ bool make_diag_gate(const GatePlan &p, DiagGate *g) {
     g->d[1] = U[7];
     g->aone = U[0] == 1.0 && U[1] == 0.0;
     g->done = U[6] == 1.0 && U[7] == 0.0;
+    g->t = p.t;
     const uint64_t lo = (1ull << kDiagChunkBits) - 1ull;
     g->hm = p.ctrl_mask & ~lo;
     g->hv = p.ctrl_vals & ~lo;
@@ -25,10 +26,7 @@ bool make_diag_gate(const GatePlan &p, DiagGate *g) {
     g->thi = tlo ? 0ull : (1ull << p.t);
     g->tlo = tlo ? (1 << p.t) : 0;
     const int nlo = __builtin_popcountll(clo) + (tlo ? 1 : 0);
-    const uint64_t warp_lo = (1ull << kDiagWarpBits) - 1ull;
-    if (nlo == 0 && ((p.ctrl_mask | (1ull << p.t)) & warp_lo) == 0 && p.n >= kDiagWarpBits) {
-        g->cls = DIAG_WARP;
-    } else if (nlo == 0) {
+    if (nlo == 0) {
         g->cls = DIAG_HI;
     } else if (nlo == 1) {
         g->cls = DIAG_LO1;
@@ -48,11 +46,89 @@ bool make_diag_gate(const GatePlan &p, DiagGate *g) {
     return true;
 }
 
+// Index bits >= 3 a gate needs for its factor to differ from 1: its controls, and its target
+// when one side of the matrix is exactly 1.
+static void necessary_bits(const DiagGate &g, uint64_t *mask, uint64_t *vals) {
+    *mask = g.hm;
+    *vals = g.hv;
+    if (g.thi && g.aone != g.done) {
+        *mask |= g.thi;
+        if (g.aone) *vals |= g.thi;  // only the bit-1 side changes
+    }
+}
+
+DiagCounts assign_diag_classes(DiagGate *g, int count, int n) {
+    DiagCounts nc;
+    std::memset(&nc, 0, sizeof(nc));
+    nc.wt = -1;
+    // fixed bits: necessary for every gate, with the same value
+    uint64_t fm = ~0ull, fv = 0;
+    for (int i = 0; i < count; ++i) {
+        uint64_t m, v;
+        necessary_bits(g[i], &m, &v);
+        if (i == 0) {
+            fm = m;
+            fv = v;
+        } else {
+            fm &= m & ~(fv ^ v);
+            fv &= fm;
+        }
+    }
+    if (count == 0) fm = 0;
+    int nfix = 0;
+    for (int b = kDiagChunkBits; b < n && nfix < kDiagMaxFixed; ++b)
+        if ((fm >> b) & 1ull) {
+            nc.fix_pos[nfix] = b - kDiagChunkBits;
+            nc.fix_val |= (uint32_t)((fv >> b) & 1ull) << nfix;
+            ++nfix;
+        }
+    nc.nfix = nfix;
+    uint64_t fixed = 0;
+    for (int i = 0; i < nfix; ++i) fixed |= 1ull << (nc.fix_pos[i] + kDiagChunkBits);
+    // lane bits: the five lowest free chunk-level bits
+    uint64_t lanes = 0;
+    int nl = 0;
+    for (int b = kDiagChunkBits; b < n && nl < 5; ++b)
+        if (!((fixed >> b) & 1ull)) {
+            lanes |= 1ull << b;
+            ++nl;
+        }
+    const bool warp_ok = nl == 5;  // the compact counter has >= 32 values
+    const uint64_t varying = lanes | ((1ull << kDiagChunkBits) - 1ull);
+    int wt = -1;
+    bool one_target = true;
+    for (int i = 0; i < count; ++i) {
+        DiagGate &G = g[i];
+        if (!warp_ok || G.cls == DIAG_LOM) continue;
+        const uint64_t ctrl = (G.hm | (G.cls == DIAG_LO1 && !G.ut ? (1ull << G.u) : 0ull)) & ~fixed;
+        const uint64_t tb = (1ull << G.t) & ~fixed;
+        if ((ctrl & varying) != 0) continue;
+        if ((tb & varying) == 0) {
+            G.cls = DIAG_WARP;  // controls and target constant over the warp (fixed or above the lanes)
+        } else if (G.cls == DIAG_HI || (G.cls == DIAG_LO1 && G.ut)) {
+            if (wt < 0) wt = G.t;
+            else if (wt != G.t) one_target = false;
+        }
+    }
+    if (wt >= 0 && one_target) {
+        for (int i = 0; i < count; ++i) {
+            DiagGate &G = g[i];
+            if (G.cls == DIAG_WARP || G.cls == DIAG_LOM || G.t != wt) continue;
+            const uint64_t ctrl = (G.hm | (G.cls == DIAG_LO1 && !G.ut ? (1ull << G.u) : 0ull)) & ~fixed;
+            if ((ctrl & varying) == 0 && (G.cls == DIAG_HI || (G.cls == DIAG_LO1 && G.ut))) G.cls = DIAG_WT;
+        }
+        nc.wt = wt;
+    }
+    std::stable_sort(g, g + count, [](const DiagGate &a, const DiagGate &b) { return a.cls < b.cls; });
+    for (int i = 0; i < count; ++i) ++nc.ncls[g[i].cls];
+    return nc;
+}
+
 namespace {
 
 template <typename Real> struct SDiag {
     uint64_t hm, hv, thi;
-    int32_t cls, u, ut, cv, lm, lv, tlo, aone, done, pad;
+    int32_t cls, u, ut, cv, lm, lv, tlo, aone, done, t;
     Real a[2], d[2];
 };
 
@@ -113,23 +189,33 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
         S.tlo = G.tlo;
         S.aone = G.aone;
         S.done = G.done;
+        S.t = G.t;
         S.a[0] = (Real)G.a[0];
         S.a[1] = (Real)G.a[1];
         S.d[0] = (Real)G.d[0];
         S.d[1] = (Real)G.d[1];
     }
     __syncthreads();
-    const int w_end = nc.ncls[DIAG_WARP], h_end = w_end + nc.ncls[DIAG_HI], l1_end = h_end + nc.ncls[DIAG_LO1];
-    const bool any_lo1 = nc.ncls[DIAG_LO1] > 0, any_lom = nc.ncls[DIAG_LOM] > 0;  // uniform
+    const int w_end = nc.ncls[DIAG_WARP], wt_end = w_end + nc.ncls[DIAG_WT], h_end = wt_end + nc.ncls[DIAG_HI],
+              l1_end = h_end + nc.ncls[DIAG_LO1];
+    const int wt = nc.wt;
+    // uniform
+    const bool any_lo1 = nc.ncls[DIAG_LO1] > 0 || (nc.ncls[DIAG_WT] > 0 && wt < kDiagChunkBits),
+               any_lom = nc.ncls[DIAG_LOM] > 0;
     const int lane = threadIdx.x & 31;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay aligned
-    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += stride) {
+    for (uint64_t cc = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; cc < nchunks; cc += stride) {
+        uint64_t c = cc;  // insert the fixed bits, lowest position first
+        for (int i = 0; i < nc.nfix; ++i) {
+            const int p = nc.fix_pos[i];
+            c = ((c >> p) << (p + 1)) | (c & ((1ull << p) - 1ull)) | ((uint64_t)((nc.fix_val >> i) & 1u) << p);
+        }
         const uint64_t base = c << kDiagChunkBits;
         T2 s = T2{1, 0};
         bool touched = false;
         if (w_end > 0) {
-            // gates on bits >= 8: each lane takes every 32nd, then the warp multiplies the partial
-            // products (all 32 chunks of the warp are in range: nchunks is a multiple of 32 here)
+            // factors constant over the warp: each lane takes every 32nd gate, then the warp
+            // multiplies the partial products (the compact counter has >= 32 values here)
             for (int g = lane; g < w_end; g += 32) {
                 const SDiag<Real> &G = sg[g];
                 if ((base & G.hm) != G.hv) continue;
@@ -148,7 +234,52 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
             }
             touched = __any_sync(0xffffffffu, touched);
         }
-        for (int g = w_end; g < h_end; ++g) {
+        T2 s0[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}}, s1[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}};
+        if (wt_end > w_end) {
+            // controls constant over the warp, one target in the lane or element bits: the
+            // warp forms the products for target bit 0 (p0) and 1 (p1) the same way
+            T2 p0 = T2{1, 0}, p1 = T2{1, 0};
+            bool n0 = false, n1 = false;
+            for (int g = w_end + lane; g < wt_end; g += 32) {
+                const SDiag<Real> &G = sg[g];
+                if ((base & G.hm) != G.hv) continue;
+                if (!G.aone) {
+                    p0 = cm<T2, Real>(G.a, p0);
+                    n0 = true;
+                }
+                if (!G.done) {
+                    p1 = cm<T2, Real>(G.d, p1);
+                    n1 = true;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                T2 q0, q1;
+                q0.x = __shfl_xor_sync(0xffffffffu, p0.x, o);
+                q0.y = __shfl_xor_sync(0xffffffffu, p0.y, o);
+                q1.x = __shfl_xor_sync(0xffffffffu, p1.x, o);
+                q1.y = __shfl_xor_sync(0xffffffffu, p1.y, o);
+                p0 = cmul<T2, Real>(q0.x, q0.y, p0);
+                p1 = cmul<T2, Real>(q1.x, q1.y, p1);
+            }
+            n0 = __any_sync(0xffffffffu, n0);
+            n1 = __any_sync(0xffffffffu, n1);
+            if (wt >= kDiagChunkBits) {  // the target bit is constant in this chunk
+                const bool tb = (base >> wt) & 1ull;
+                s = cmul<T2, Real>(tb ? p1.x : p0.x, tb ? p1.y : p0.y, s);
+                touched |= tb ? n1 : n0;
+            } else {                     // the target bit varies inside the chunk
+#pragma unroll
+                for (int b = 0; b < kDiagChunkBits; ++b) {
+                    if (b == wt) {
+                        s0[b] = p0;
+                        s1[b] = p1;
+                    }
+                }
+                touched |= n0 || n1;
+            }
+        }
+        for (int g = wt_end; g < h_end; ++g) {
             const SDiag<Real> &G = sg[g];
             if ((base & G.hm) != G.hv) continue;
             const bool tb = (base & G.thi) != 0;
@@ -157,7 +288,6 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
                 touched = true;
             }
         }
-        T2 s0[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}}, s1[3] = {T2{1, 0}, T2{1, 0}, T2{1, 0}};
         for (int g = h_end; g < l1_end; ++g) {
             const SDiag<Real> &G = sg[g];
             if ((base & G.hm) != G.hv) continue;
@@ -213,10 +343,14 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
 cudaError_t launch_diag_run(int dtype, void *psi, int n, const DiagGate *gates, int count, DiagCounts nc,
                             cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    if (count > kDiagMaxGates || n < kDiagChunkBits ||
-        nc.ncls[0] + nc.ncls[1] + nc.ncls[2] + nc.ncls[3] != count || (nc.ncls[DIAG_WARP] > 0 && n < kDiagWarpBits))
+    int total = 0;
+    for (int c = 0; c < kDiagClasses; ++c) total += nc.ncls[c];
+    if (count > kDiagMaxGates || n < kDiagChunkBits || total != count || nc.nfix < 0 || nc.nfix > kDiagMaxFixed ||
+        n - kDiagChunkBits - nc.nfix < 0 ||
+        ((nc.ncls[DIAG_WARP] > 0 || nc.ncls[DIAG_WT] > 0) && n - kDiagChunkBits - nc.nfix < 5) ||
+        (nc.ncls[DIAG_WT] > 0 && (nc.wt < 0 || nc.wt >= n)))
         return cudaErrorInvalidValue;
-    const uint64_t nchunks = 1ull << (n - kDiagChunkBits);
+    const uint64_t nchunks = 1ull << (n - kDiagChunkBits - nc.nfix);  // compact counter range
     const uint64_t cap = (uint64_t)device_sm_count() * 8;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((nchunks + 255) / 256, cap));
     if (dtype == QS_C64)

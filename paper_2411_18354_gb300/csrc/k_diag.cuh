@@ -20,14 +20,20 @@ namespace qs {
 constexpr int kDiagChunkBits = 3;   // amplitudes per chunk: 8
 constexpr int kDiagMaxGates = 64;   // gates per launch (staged in shared memory)
 
+// The chunks of a launch are visited through a compact counter with the launch's fixed bits
+// inserted (index bits >= 3 on which every gate needs the same value for its factor to differ
+// from 1, as the controls of a single gate are inserted into its pair counter): the 32 chunks of
+// a warp then differ only in the five lowest free chunk bits, the warp's "lane bits".
 enum DiagClass : int32_t {
-    DIAG_WARP = 0, // factor depends on bits >= 8 only: the same for the 32 chunks of a warp
-    DIAG_HI = 1,   // on bits >= 3 only: one scalar per chunk
-    DIAG_LO1 = 2,  // on bits >= 3 and one bit u < 3: a scalar per value of bit u
-    DIAG_LOM = 3,  // on two or more bits < 3: per element
+    DIAG_WARP = 0, // factor independent of bits 0-2 and the lane bits: the same for a whole warp
+    DIAG_WT = 1,   // controls off bits 0-2 and the lane bits, target t in them, t shared by all
+                   // DIAG_WT gates of a launch: the warp forms the products for bit t = 0 and 1
+    DIAG_HI = 2,   // independent of bits 0-2: one scalar per chunk
+    DIAG_LO1 = 3,  // on one bit u < 3 (and bits >= 3): a scalar per value of bit u
+    DIAG_LOM = 4,  // on two or more bits < 3: per element
 };
-// A warp's 32 consecutive chunks differ only in index bits 3-7.
-constexpr int kDiagWarpBits = kDiagChunkBits + 5;
+constexpr int kDiagClasses = 5;
+constexpr int kDiagMaxFixed = 8;
 
 // Host-built description of one diagonal gate (device table entry).
 struct DiagGate {
@@ -40,18 +46,27 @@ struct DiagGate {
     int32_t lm, lv;       // DIAG_LOM: controls on bits < 3
     int32_t tlo;          // 1 << t when t < 3, else 0
     int32_t aone, done;   // a == 1, d == 1 exactly
-    int32_t pad;
+    int32_t t;
     double a[2], d[2];
 };
 
-// Classify gate plan p (op DIAG or SIDE) into a DiagGate. Returns false for other ops.
+// Classify gate plan p (op DIAG or SIDE) into a DiagGate (never DIAG_WT: that needs the whole
+// launch, see assign_diag_classes). Returns false for other ops.
 bool make_diag_gate(const GatePlan &p, DiagGate *out);
 
-// Gates of one launch, sorted by class (DIAG_WARP first, then HI, LO1, LOM); ncls[c] = gates of
-// class c. count <= kDiagMaxGates; DIAG_WARP gates need n >= kDiagWarpBits.
+// One launch: gates sorted by class, ncls[c] = gates of class c, wt = the DIAG_WT target;
+// nfix fixed bits at chunk-level positions fix_pos (ascending) with values fix_val (bit i for
+// fix_pos[i]); warp classes only when the compact counter has >= 32 values.
 struct DiagCounts {
-    int32_t ncls[4];
+    int32_t ncls[kDiagClasses];
+    int32_t wt;
+    int32_t nfix;
+    int32_t fix_pos[kDiagMaxFixed];
+    uint32_t fix_val;
 };
+
+// Find the launch's fixed bits, classify its gates (sorted by class in place) and count them.
+DiagCounts assign_diag_classes(DiagGate *gates, int count, int n);
 
 // Apply gates[0..count) (device table) to the 2^n amplitudes at psi.
 cudaError_t launch_diag_run(int dtype, void *psi, int n, const DiagGate *gates, int count, DiagCounts counts,

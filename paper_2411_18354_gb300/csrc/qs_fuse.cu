@@ -271,19 +271,14 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
                     make_diag_gate(p, &dg);
                     run.push_back(dg);
                 }
-                // the gates commute: order them by class for the kernel's loops
-                std::stable_sort(run.begin(), run.end(),
-                                 [](const DiagGate &a, const DiagGate &b) { return a.cls < b.cls; });
+                // the gates commute: each launch's gates are ordered by class for the kernel
                 for (size_t q0 = 0; q0 < run.size(); q0 += kDiagMaxGates) {
                     const size_t q1 = std::min(run.size(), q0 + kDiagMaxGates);
                     DiagRun r;
                     r.begin = (int)prog->dgates.size();
                     r.count = (int)(q1 - q0);
-                    r.nc = DiagCounts{{0, 0, 0, 0}};
-                    for (size_t q = q0; q < q1; ++q) {
-                        ++r.nc.ncls[run[q].cls];
-                        prog->dgates.push_back(run[q]);
-                    }
+                    r.nc = assign_diag_classes(run.data() + q0, r.count, n);
+                    prog->dgates.insert(prog->dgates.end(), run.begin() + q0, run.begin() + q1);
                     prog->ops.push_back({-1, -1, (int)prog->druns.size()});
                     prog->druns.push_back(r);
                 }

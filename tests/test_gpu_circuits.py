@@ -346,6 +346,31 @@ def test_diagonal_runs_match_oracle(qs, dtype):
                 ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
                 vals = [int(b) for b in rng.integers(0, 2, size=c)]
                 gl.append(_diag_gate(rng, n, t, ctrls, vals))
+        if n >= 8:  # runs whose gates all need one bit value: skipped by the compact counter
+            for _ in range(2):
+                common = int(rng.integers(3, n))
+                cv = int(rng.integers(0, 2))
+                for _ in range(10):
+                    t = int(rng.choice([q for q in range(n) if q != common]))
+                    others = [q for q in range(n) if q not in (t, common)]
+                    extra = sorted(int(q) for q in rng.choice(others, size=int(rng.integers(0, 3)), replace=False))
+                    ctrls = sorted(extra + [common])
+                    vals = [cv if q == common else int(rng.integers(0, 2)) for q in ctrls]
+                    gl.append(_diag_gate(rng, n, t, ctrls, vals))
+                t = int(rng.integers(3, n))  # one-sided gates sharing a target: bit t = 1 needed
+                for _ in range(10):
+                    others = [q for q in range(n) if q != t]
+                    ctrls = sorted(int(q) for q in rng.choice(others, size=int(rng.integers(0, 3)), replace=False))
+                    gl.append(W.make_gate(t, np.diag([1.0, np.exp(1j * rng.uniform(0, 6.3))]), ctrls))
+                gl.append(W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng)))
+        if n >= 9:  # runs sharing one low target, controls on qubits >= 8 (warp-level classes)
+            for t in (0, 2, 5):
+                for _ in range(12):
+                    c = int(rng.integers(0, min(3, n - 8) + 1))
+                    ctrls = sorted(int(q) for q in rng.choice(range(8, n), size=c, replace=False)) if c else []
+                    vals = [int(b) for b in rng.integers(0, 2, size=c)]
+                    gl.append(_diag_gate(rng, n, t, ctrls, vals))
+                gl.append(W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng)))
         gates = W.gate_list(gl)
         psi0 = random_state(n, dtype, 300 + n)
         ref = c128_of(psi0).copy()
