@@ -57,18 +57,24 @@ bool make_diag_gate(const GatePlan &p, DiagGate *out);
 // One launch: gates sorted by class, ncls[c] = gates of class c, wt = the DIAG_WT target;
 // nfix fixed bits at chunk-level positions fix_pos (ascending) with values fix_val (bit i for
 // fix_pos[i]); warp classes only when the compact counter has >= 32 values.
+// lead_t >= 0: the pass first applies the uncontrolled 2x2 gate lu (row-major, interleaved
+// re / im) on target lead_t to every amplitude (then no bits are fixed: every chunk changes).
 struct DiagCounts {
     int32_t ncls[kDiagClasses];
     int32_t wt;
     int32_t nfix;
     int32_t fix_pos[kDiagMaxFixed];
     uint32_t fix_val;
+    int32_t lead_t;
+    double lu[8];
 };
 
-// Find the launch's fixed bits, classify its gates (sorted by class in place) and count them.
-DiagCounts assign_diag_classes(DiagGate *gates, int count, int n);
+// Find the launch's fixed bits (none with a leading gate on lead_t >= 0), classify its gates
+// (sorted by class in place) and count them.
+DiagCounts assign_diag_classes(DiagGate *gates, int count, int n, int lead_t = -1);
 
-// Apply gates[0..count) (device table) to the 2^n amplitudes at psi.
+// Apply gates[0..count) (device table), after the leading gate if counts.lead_t >= 0, to the
+// 2^n amplitudes at psi.
 cudaError_t launch_diag_run(int dtype, void *psi, int n, const DiagGate *gates, int count, DiagCounts counts,
                             cudaStream_t st);
 

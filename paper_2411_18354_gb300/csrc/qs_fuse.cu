@@ -271,13 +271,26 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
                     make_diag_gate(p, &dg);
                     run.push_back(dg);
                 }
+                // an uncontrolled arithmetic gate launched alone just before the run goes into the
+                // run's first pass (applied first): one read + write instead of two
+                int lead = -1;
+                if (!prog->ops.empty() && prog->ops.back().pass < 0 && prog->ops.back().drun < 0 &&
+                    n >= kDiagChunkBits + 1) {
+                    const GatePlan &lp = plans[prog->ops.back().gate];
+                    if (lp.ctrl_mask == 0 && lp.op != OP_SWAP && lp.op != OP_DIAG && lp.op != OP_SIDE) {
+                        lead = prog->ops.back().gate;
+                        prog->ops.pop_back();
+                    }
+                }
                 // the gates commute: each launch's gates are ordered by class for the kernel
                 for (size_t q0 = 0; q0 < run.size(); q0 += kDiagMaxGates) {
                     const size_t q1 = std::min(run.size(), q0 + kDiagMaxGates);
                     DiagRun r;
                     r.begin = (int)prog->dgates.size();
                     r.count = (int)(q1 - q0);
-                    r.nc = assign_diag_classes(run.data() + q0, r.count, n);
+                    const int lt = (q0 == 0 && lead >= 0) ? plans[lead].t : -1;
+                    r.nc = assign_diag_classes(run.data() + q0, r.count, n, lt);
+                    if (lt >= 0) std::memcpy(r.nc.lu, plans[lead].Ufull, sizeof(r.nc.lu));
                     prog->dgates.insert(prog->dgates.end(), run.begin() + q0, run.begin() + q1);
                     prog->ops.push_back({-1, -1, (int)prog->druns.size()});
                     prog->druns.push_back(r);
