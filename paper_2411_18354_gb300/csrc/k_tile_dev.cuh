@@ -188,8 +188,9 @@ __device__ __forceinline__ void op_pair(T2 &x, T2 &y, const Real *u, int side) {
 
 // All pairs (e, e | 2^P) of the thread's RPT rows for one gate with operation OP; CQ: the
 // gate has controls on group qubits (else every pair of a selected row is updated); UNI: every
-// row is selected (no per-row predicate). The RPT rows are independent, which gives each
-// thread RPT times the arithmetic per decoded gate. Rows of tiles with fewer than GB qubits
+// row is selected (no per-row predicate). RPT independent rows per thread share one decoded
+// gate (the kernels use RPT = 1: with 2 rows the register budget of 2 CTAs per SM spills).
+// Rows of tiles with fewer than GB qubits
 // are padded with zero elements that pair only with each other, so they stay zero and add
 // nothing to the inner products.
 template <int P, int OP, bool ADJ, int GB, bool CQ, int RPT, bool UNI, typename T2, typename Real>

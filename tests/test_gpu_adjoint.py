@@ -47,6 +47,34 @@ def test_hea_n10_against_parameter_shift(qs, dtype, tol, fuse):
     assert abs(back[0] - 1.0) <= (1e-10 if dtype == "c128" else 1e-4)
 
 
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 1e-4)])
+def test_diagonal_layers_against_parameter_shift(qs, dtype, tol):
+    """Layers of RY on every qubit, then RZ on every qubit and a CZ ladder (runs of diagonal
+    gates, which the fused forward pass applies as diagonal-run passes, the Hadamard-free RY
+    before them as a leading gate), n = 9, 6 layers, against parameter shift."""
+    n, layers = 9, 6
+    gl = []
+    p = 0
+    cz = np.diag([1.0, -1.0])
+    for _ in range(layers):
+        for q in range(n):
+            gl.append(W.make_gate(q, None, (), kind=W.KIND_RY, param=p))
+            p += 1
+        for q in range(n):
+            gl.append(W.make_gate(q, None, (), kind=W.KIND_RZ, param=p))
+            p += 1
+        for q in range(n - 1):
+            gl.append(W.make_gate(q + 1, cz, (q,)))
+    gates = W.gate_list(gl)
+    th = np.random.default_rng(91).uniform(0, 2 * np.pi, size=p)
+    ps = oracle.param_shift_grad(n, gates, th)
+    e_ref = oracle.energy(n, gates, th)
+    for flags in (qs.QS_FLAG_FUSE, 0):
+        e, g, _ = _adjoint(qs, n, dtype, gates, th, flags=flags)
+        assert abs(e - e_ref) <= tol, flags
+        assert np.max(np.abs(g - ps)) <= tol, flags
+
+
 @pytest.mark.parametrize("tile_bits", [None, 3, 6])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-6), ("c64", 1e-4)])
 def test_controlled_rotations_against_finite_differences(qs, dtype, tol, tile_bits, monkeypatch):
