@@ -381,3 +381,35 @@ def test_diagonal_runs_match_oracle(qs, dtype):
                 st.apply_circuit(gates, flags=flags)
                 got = c128_of(st.to_numpy())
             assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), (n, flags)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_fused_programs_at_the_smallest_sizes(qs, dtype):
+    """n = 1..5 with QS_FLAG_FUSE: diagonal runs (only from n = 3: one 8-amplitude chunk),
+    leading gates on every target (chunk pairs from n = 4), exchanges and general gates,
+    against the oracle; an empty circuit changes nothing."""
+    rng = np.random.default_rng(5)
+    for n in range(1, 6):
+        gl = []
+        for blk in range(5):
+            gl.append(W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng)))
+            for _ in range(int(rng.integers(3, 8))):
+                t = int(rng.integers(0, n))
+                others = [q for q in range(n) if q != t]
+                c = int(rng.integers(0, len(others) + 1)) if others else 0
+                ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+                vals = [int(b) for b in rng.integers(0, 2, size=c)]
+                gl.append(_diag_gate(rng, n, t, ctrls, vals))
+            gl.append(W.make_gate(int(rng.integers(0, n)), None, (), kind=W.KIND_X))
+        gates = W.gate_list(gl)
+        psi0 = random_state(n, dtype, 500 + n)
+        ref = c128_of(psi0).copy()
+        oracle.run_circuit(ref, n, gates)
+        with qs.State(n, dtype) as st:
+            st.from_numpy(psi0)
+            st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE)
+            got = c128_of(st.to_numpy())
+            st.from_numpy(psi0)
+            st.apply_circuit(W.gate_list([]), flags=qs.QS_FLAG_FUSE)
+            assert np.array_equal(st.to_numpy(), psi0.astype(NP[dtype]))
+        assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), n
