@@ -38,6 +38,7 @@ struct RegGate {
     int32_t slot;             // adjoint: accumulator index, -1 if no parameter
     int32_t pkind;            // batch: QS_GATE_RY / QS_GATE_RZ -> matrices from theta[pidx]; 0 = fixed
     int32_t pidx;             // batch: parameter index inside the state
+    int32_t pkind2, pidx2;    // batch forward: a second rotation applied after the first (0 = none)
     int32_t pad1;
     uint64_t hmask, hvals;    // non-local controls: the tile predicate (global bits)
     double U[8];              // forward: U; adjoint: U^dagger

@@ -51,6 +51,20 @@ __device__ __forceinline__ void stage_gate(const RegGate &G, SGate<Real> &S, con
     S.pidx = (uint32_t)G.pidx;
     if (G.pkind != 0 && cs) {  // the state's parameter: matrices built once per pass
         param_matrices<Real>(G.pkind, cs[2 * G.pidx], cs[2 * G.pidx + 1], adjoint, S.u, S.d);
+        if (G.pkind2 != 0) {  // forward only: a second rotation on the same qubit, u <- u2 u
+            Real u2[8], d2[8], w[8];
+            param_matrices<Real>(G.pkind2, cs[2 * G.pidx2], cs[2 * G.pidx2 + 1], false, u2, d2);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const Real *a0 = u2 + 4 * i, *b0 = S.u + 2 * j, *b1 = S.u + 4 + 2 * j;
+                    w[4 * i + 2 * j] = a0[0] * b0[0] - a0[1] * b0[1] + a0[2] * b1[0] - a0[3] * b1[1];
+                    w[4 * i + 2 * j + 1] = a0[0] * b0[1] + a0[1] * b0[0] + a0[2] * b1[1] + a0[3] * b1[0];
+                }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S.u[i] = w[i];
+        }
         pkind = 0;
     } else {
         const Real *u = TileT<Real>::U(G);

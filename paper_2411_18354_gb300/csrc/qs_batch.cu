@@ -14,6 +14,7 @@
 #include <map>
 #include <numeric>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "k_batch.cuh"
@@ -191,13 +192,37 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
                     slots[i] = gs[i].param;
                 }
             }
+            // forward program: two consecutive rotations on the same qubit with the same controls
+            // (RY then RZ in the ansatz) become one general gate whose matrix the kernel forms
+            // per state at staging (u = R2 R1); the sweep keeps every gate for its gradients
+            std::vector<GatePlan> fwdm;
+            std::vector<std::pair<int, int>> srcm;  // merged plan -> (first gate, second gate or -1)
+            for (size_t i = 0; i < gc; ++i) {
+                const bool rot = gs[i].kind == QS_GATE_RY || gs[i].kind == QS_GATE_RZ;
+                if (rot && i + 1 < gc && (gs[i + 1].kind == QS_GATE_RY || gs[i + 1].kind == QS_GATE_RZ) &&
+                    gs[i + 1].target == gs[i].target && gs[i + 1].ctrl_mask == gs[i].ctrl_mask &&
+                    gs[i + 1].ctrl_vals == gs[i].ctrl_vals) {
+                    static const double kGeneral[8] = {0.5, 0.1, 0.3, 0.0, 0.2, 0.0, 0.4, -0.2};  // structure only
+                    GatePlan m;
+                    if (!plan_gate(n, dtype, gs[i].target, gs[i].ctrl_mask, gs[i].ctrl_vals, kGeneral, QS_GATE_U, OP_GEN,
+                                   &m, err, sizeof(err)))
+                        return set_error(QS_EINVAL, err);
+                    fwdm.push_back(m);
+                    srcm.push_back({(int)i, (int)i + 1});
+                    ++i;
+                } else {
+                    fwdm.push_back(fwd[i]);
+                    srcm.push_back({(int)i, -1});
+                }
+            }
             const bool small = n <= small_bits;
             const int k = small ? n : tile_bits;
-            std::vector<int> seq(gc);
+            std::vector<int> seqf(fwdm.size()), seq(gc);
+            std::iota(seqf.begin(), seqf.end(), 0);
             std::iota(seq.begin(), seq.end(), 0);
             FusedProgram pf, pa;
             // the batch kernel runs kGroupBits-qubit groups forward, kGroupBitsAdjoint in the sweep
-            plan_fused(n, dtype, k, seq, fwd, nullptr, nullptr, &pf, max_pass_gates, false, kGroupBits);
+            plan_fused(n, dtype, k, seqf, fwdm, nullptr, nullptr, &pf, max_pass_gates, false, kGroupBits);
             std::reverse(seq.begin(), seq.end());
             plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa, max_pass_gates, false, kGroupBitsAdjoint);
             BatchProg bp{};
@@ -213,11 +238,19 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
                 }
                 for (size_t gi = 0; gi < fp.gates.size(); ++gi) {
                     RegGate G = fp.gates[gi];
-                    const qs_gate &src = gs[fp.gate_src[gi]];
+                    const int first = dir ? fp.gate_src[gi] : srcm[fp.gate_src[gi]].first;
+                    const int second = dir ? -1 : srcm[fp.gate_src[gi]].second;
+                    const qs_gate &src = gs[first];
+                    G.pkind2 = 0;
+                    G.pidx2 = 0;
                     if (src.kind == QS_GATE_RY || src.kind == QS_GATE_RZ) {
                         G.pkind = src.kind;
                         G.pidx = src.param;
                         G.slot = dir ? src.param : -1;
+                        if (second >= 0) {
+                            G.pkind2 = gs[second].kind;
+                            G.pidx2 = gs[second].param;
+                        }
                     } else {
                         G.slot = -1;
                     }
