@@ -476,6 +476,23 @@ def cpu_oracle_sample(n_target: int, sched, max_gates=None):
             "seconds": dt}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The maximum of x over all ranks (the timed region of the slowest replica)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, step_bytes: float, total_ms: float) -> float:
+    """Whole-job algorithmic GB/s: every replica moves step_bytes per step; the job takes the
+    slowest replica's time."""
+    return world * steps * step_bytes / (total_ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, same metric/unit/config."""
     if rank != 0:
@@ -544,13 +561,9 @@ def run_ours(args, rank, world, local_rank):
     step_ms, per = run_sweep(qs, st, n, esize, sched, args.steps, args.warmup)
     t_wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), world)
     step_bytes = sum(alg_bytes(n, c, esize) for (c, _, _, _, _) in sched[0])
-    value = world * args.steps * step_bytes / (total_ms * 1e-3) / 1e9
+    value = job_value(world, args.steps, step_bytes, total_ms)
 
     # per-launch roofline of the gate kernel (algorithmic bytes / CUDA-event launch time)
     launch_bytes = sum(alg_bytes(n, c, esize) for c, _, _, _ in per)
