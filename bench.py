@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--tile-costs", action="store_true",
                     help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
     ap.add_argument("--ncu-qft", action="store_true",
-                    help="profiling case: the fused 29-qubit QFT, twice (diagonal-run passes)")
+                    help="profiling case: the fused QFT (29 qubits, or --n), twice (diagonal-run passes)")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="small profiling case: one batch launch of 304 states (n=16, 2 layers of the ansatz)")
     return ap.parse_args()
@@ -760,15 +760,16 @@ def run_tile_costs(args):
 
 
 def run_ncu_qft(args):
-    """Profiling case: the 29-qubit QFT with QS_FLAG_FUSE, twice; no timing."""
+    """Profiling case: the QFT (29 qubits unless --n is given) with QS_FLAG_FUSE, twice; no timing."""
     import torch
 
     import paper_2411_18354_gb300 as qs
     import workloads as W
 
     qs.build()
-    g = W.qft_circuit(29)
-    with qs.State(29, "c64") as st:
+    n = args.n if args.n != 30 else 29
+    g = W.qft_circuit(n)
+    with qs.State(n, "c64") as st:
         for _ in range(2):
             st.apply_circuit(g, flags=qs.QS_FLAG_FUSE)
         torch.cuda.synchronize()

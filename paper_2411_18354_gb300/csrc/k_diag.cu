@@ -374,11 +374,12 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
                 c = ((c >> p) << (p + 1)) | (c & ((1ull << p) - 1ull)) | ((uint64_t)((nc.fix_val >> i) & 1u) << p);
             }
             const uint64_t base = c << kDiagChunkBits;
-            T2 f[E];
-            const bool touched = chunk_factors<Real>(base, sg, count, nc, lane, f);
-            if (LEAD == 0 && !touched) continue;  // every factor of this chunk is 1
-            T2 x[E];
+            // the chunk's loads are issued before its factors are formed, so that their latency
+            // overlaps that work (the compact counter leaves few chunks whose factors are all 1)
+            T2 x[E], f[E];
             ld8(psi + base, x);
+            const bool touched = chunk_factors<Real>(base, sg, count, nc, lane, f);
+            if (LEAD == 0 && !touched) continue;  // every factor of this chunk is 1: no store
             if (LEAD == 1) {
                 if (nc.lead_t == 0) lead_in_chunk<0, T2, Real>(x, L);
                 else if (nc.lead_t == 1) lead_in_chunk<1, T2, Real>(x, L);
