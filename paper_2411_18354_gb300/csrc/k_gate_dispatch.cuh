@@ -43,9 +43,18 @@ cudaError_t go(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cvals, cud
     const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)occ;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(need, cap));
     using T2 = typename CxT<Real>::T;
-    kern<<<grid, kGateThreads, 0, st>>>(reinterpret_cast<T2 *>(psi), make_dev<Real, Idx>(p, cmask, cvals),
-                                        (Idx)p.units, p.side);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kGateThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<T2 *>(psi), make_dev<Real, Idx>(p, cmask, cvals),
+                              (Idx)p.units, p.side);
 }
 
 template <typename Real, typename Idx, int NS, bool MASKED>
