@@ -1,5 +1,6 @@
 // k_tile.cu -- fused tile-pass kernels (forward, and adjoint over psi and lambda).
 #include <algorithm>
+#include <atomic>
 
 #include "k_tile_dev.cuh"
 
@@ -59,11 +60,15 @@ cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGroup *groups,
                size_t part_stride, cudaStream_t st) {
     auto kern = k_tile_pass<Real, ADJ>;
     const size_t smem = tile_smem_bytes(sizeof(Real) == 4 ? QS_C64 : QS_C128, p.k, ADJ);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
+    static std::atomic<size_t> configured[64];  // per device: dynamic shared memory allowed so far
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (smem > 48 * 1024 && smem > configured[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = smem;
+        size_t cur = configured[dev].load();
+        while (cur < smem && !configured[dev].compare_exchange_weak(cur, smem)) {
+        }
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTileThreads, smem) != cudaSuccess || occ < 1) occ = 1;

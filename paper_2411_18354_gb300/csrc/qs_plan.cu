@@ -1,6 +1,7 @@
 // qs_plan.cu -- host-side gate planning (argument checks, sorted insertion positions,
 // operation class and unit layout) and the launch entry points used by the C interface.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,15 +18,14 @@ cudaError_t launch_gate_c128(void *psi, const GatePlan &p, bool masked, uint64_t
 int device_sm_count() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-    static int cached_dev = -1;
-    static int cached_sms = 1;
-    if (dev != cached_dev) {
-        int sms = 1;
+    static std::atomic<int> sms_of[64];  // per device, 0 = not read yet (thread-safe)
+    if (dev < 0 || dev >= 64) dev = 0;
+    int sms = sms_of[dev].load(std::memory_order_relaxed);
+    if (sms == 0) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
-        cached_sms = sms;
-        cached_dev = dev;
+        sms_of[dev].store(sms, std::memory_order_relaxed);
     }
-    return cached_sms;
+    return sms;
 }
 
 static int ctz64(uint64_t v) { return __builtin_ctzll(v); }
