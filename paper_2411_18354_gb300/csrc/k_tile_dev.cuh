@@ -292,7 +292,7 @@ __device__ __forceinline__ void row_gate(T2 (&v)[RPT][1 << GB], T2 (&w)[RPT][ADJ
 
 // Register qubits per group: 4 for forward passes, 3 for the adjoint sweep (psi and lambda
 // rows both live in registers there).
-template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : 4; };
+template <bool ADJ> struct GroupBits { static constexpr int v = ADJ ? 3 : kGroupBits; };
 
 // Apply the pass's register groups to the tile tp (and lambda tile tl if ADJ) whose global
 // base index is `base`. Each thread holds RPT rows of 2^GB elements at a time. Adjoint: for a
