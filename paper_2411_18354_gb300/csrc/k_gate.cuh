@@ -159,9 +159,10 @@ k_gate(typename CxT<Real>::T *__restrict__ psi, const DevGate<Real, Idx> g, Idx 
     using T2 = typename CxT<Real>::T;
     constexpr int r = Log2<R>::v;
     constexpr int A = (LAY == LAY_ADJ) ? 2 * R : R;  // amplitudes per load group
-    // Launched as a programmatic dependent of the previous kernel on the stream: this block may
-    // start while that kernel drains; the state is touched only after it has completed and its
-    // writes are visible (grid dependency barrier). The next gate may be scheduled right away.
+    // When launched as a programmatic dependent of the previous kernel on the stream, this block
+    // may start while that kernel drains: the state is touched only after it has completed and
+    // its writes are visible (grid dependency barrier; immediate for a normal launch). The next
+    // gate may be scheduled right away.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const Idx step = (Idx)gridDim.x * kGateThreads * UNR;

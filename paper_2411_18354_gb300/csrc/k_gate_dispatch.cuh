@@ -43,6 +43,10 @@ cudaError_t go(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cvals, cud
     const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)occ;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(need, cap));
     using T2 = typename CxT<Real>::T;
+    // small gates (at most 16 grid-stride steps of work) start as programmatic dependents of the
+    // previous kernel, hiding their launch behind its tail; large ones launch normally (their
+    // blocks would only wait on the SMs while the previous gate drains)
+    const bool dependent = p.units <= 16ull * grid * per_block;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -52,7 +56,7 @@ cudaError_t go(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cvals, cud
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = dependent ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, reinterpret_cast<T2 *>(psi), make_dev<Real, Idx>(p, cmask, cvals),
                               (Idx)p.units, p.side);
 }
