@@ -119,6 +119,16 @@ qs_status qs_state_set_basis(qs_state *s, uint64_t k);
 qs_status qs_state_copy_to_host(const qs_state *s, void *dst, size_t bytes);
 qs_status qs_state_copy_from_host(qs_state *s, const void *src, size_t bytes);
 
+/* The same copies enqueued on the state's stream, in order with its gates; they return at
+ * once. The host buffer must stay valid and untouched until the stream reaches the copy (see
+ * qs_state_synchronize); with page-locked host memory the copy runs asynchronously and overlaps
+ * work on other streams, with pageable memory the CUDA runtime may stage it synchronously. */
+qs_status qs_state_copy_to_host_async(const qs_state *s, void *dst, size_t bytes);
+qs_status qs_state_copy_from_host_async(qs_state *s, const void *src, size_t bytes);
+
+/* Wait until everything enqueued on the state's stream has finished. */
+qs_status qs_state_synchronize(const qs_state *s);
+
 /* ------------------------------------------------------------------------------------ */
 /* Gates (Section III, Eq. 2 on the reduced iteration set of Section III-B)             */
 /* ------------------------------------------------------------------------------------ */

@@ -19,8 +19,8 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
     qs_state_alloc, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
     qs_set_l2_fetch_bytes, qs_set_tile_bits,
-    qs_state_copy_from_host, qs_state_copy_to_host, qs_state_free, qs_state_info, qs_state_set_basis,
-    qs_state_set_stream, qs_state_wrap,
+    qs_state_copy_from_host, qs_state_copy_from_host_async, qs_state_copy_to_host, qs_state_copy_to_host_async,
+    qs_state_free, qs_state_info, qs_state_set_basis, qs_state_set_stream, qs_state_synchronize, qs_state_wrap,
 )
 from .gates import GATE_DTYPE, as_gate_array  # noqa: F401
 

@@ -46,6 +46,9 @@ _SIGNATURES = [
     ("qs_state_set_basis", ctypes.c_int, [_c_state_p, _u64]),
     ("qs_state_copy_to_host", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
     ("qs_state_copy_from_host", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
+    ("qs_state_copy_to_host_async", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
+    ("qs_state_copy_from_host_async", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t]),
+    ("qs_state_synchronize", ctypes.c_int, [_c_state_p]),
     ("qs_apply_gate", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
     ("qs_apply_x", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64]),
     ("qs_apply_gate_masked", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
@@ -159,6 +162,26 @@ def qs_state_copy_to_host(h: int, dst: np.ndarray) -> None:
 def qs_state_copy_from_host(h: int, src: np.ndarray) -> None:
     src = np.ascontiguousarray(src)
     _check(lib().qs_state_copy_from_host(_c_state_p(h), _vp(src.ctypes.data), src.nbytes))
+
+
+def qs_state_copy_to_host_async(h: int, dst: np.ndarray) -> None:
+    """Enqueue the copy on the state's stream; dst (contiguous, page-locked for overlap) must
+    stay alive and untouched until qs_state_synchronize."""
+    if not dst.flags.c_contiguous:
+        raise ValueError("dst must be contiguous")
+    _check(lib().qs_state_copy_to_host_async(_c_state_p(h), _vp(dst.ctypes.data), dst.nbytes))
+
+
+def qs_state_copy_from_host_async(h: int, src: np.ndarray) -> None:
+    """Enqueue the copy on the state's stream; src must be contiguous (no temporary copy is
+    made) and stay alive and unchanged until qs_state_synchronize."""
+    if not src.flags.c_contiguous:
+        raise ValueError("src must be contiguous")
+    _check(lib().qs_state_copy_from_host_async(_c_state_p(h), _vp(src.ctypes.data), src.nbytes))
+
+
+def qs_state_synchronize(h: int) -> None:
+    _check(lib().qs_state_synchronize(_c_state_p(h)))
 
 
 def qs_apply_gate(h: int, target: int, ctrl_mask: int, ctrl_vals: int, U) -> None:

@@ -248,6 +248,34 @@ qs_status qs_state_copy_from_host(qs_state *s, const void *src, size_t bytes) {
     return QS_OK;
 }
 
+qs_status qs_state_copy_from_host_async(qs_state *s, const void *src, size_t bytes) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!src) return fail(QS_EINVAL, "src is NULL");
+    if (bytes != s->bytes) return fail(QS_EINVAL, "bytes=%zu, the state holds %zu", bytes, s->bytes);
+    cudaError_t e = cudaMemcpyAsync(s->psi, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy_from_host_async");
+    return QS_OK;
+}
+
+qs_status qs_state_copy_to_host_async(const qs_state *s, void *dst, size_t bytes) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!dst) return fail(QS_EINVAL, "dst is NULL");
+    if (bytes != s->bytes) return fail(QS_EINVAL, "bytes=%zu, the state holds %zu", bytes, s->bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, s->psi, bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy_to_host_async");
+    return QS_OK;
+}
+
+qs_status qs_state_synchronize(const qs_state *s) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "qs_state_synchronize");
+    return QS_OK;
+}
+
 qs_status qs_apply_gate(qs_state *s, int target, uint64_t ctrl_mask, uint64_t ctrl_vals, const double U[8]) {
     qs_status st = check_state(s);
     if (st != QS_OK) return st;

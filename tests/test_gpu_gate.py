@@ -285,3 +285,39 @@ def test_fused_ansatz_matches_unfused(qs, dtype):
         finally:
             st.close()
         assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype], flags
+
+
+def test_async_host_copies_on_two_streams(qs):
+    """qs_state_copy_from_host_async / _to_host_async / qs_state_synchronize: two states on two
+    streams each upload a page-locked input, apply gates and download, overlapped; the results
+    equal the synchronous path and the oracle. Wrong sizes are rejected before any copy."""
+    import torch
+
+    n = 16
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    states = [qs.State(n, "c64", stream=int(s.cuda_stream)) for s in streams]
+    try:
+        hosts = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        hnp = [h.numpy() for h in hosts]
+        psis = [random_state(n, "c64", 60 + i) for i in range(2)]
+        gates = [W.random_circuit(n, 40, 3, seed=61 + i) for i in range(2)]
+        for i in range(2):
+            hnp[i][:] = psis[i]
+        for i in range(2):
+            qs.qs_state_copy_from_host_async(states[i].h, hnp[i])
+            states[i].apply_circuit(gates[i])
+            qs.qs_state_copy_to_host_async(states[i].h, hnp[i])
+        for i in range(2):
+            qs.qs_state_synchronize(states[i].h)
+        for i in range(2):
+            ref = c128_of(psis[i]).copy()
+            oracle.run_circuit(ref, n, gates[i])
+            assert np.max(np.abs(c128_of(hnp[i]) - ref)) <= ATOL_CIRCUIT["c64"]
+            assert np.array_equal(hnp[i], states[i].to_numpy())
+        with pytest.raises(qs.QsError):
+            qs.qs_state_copy_from_host_async(states[0].h, hnp[0][:100])
+        with pytest.raises(qs.QsError):
+            qs.qs_state_copy_to_host_async(states[0].h, np.empty(3, dtype=np.complex64))
+    finally:
+        for s in states:
+            s.close()
