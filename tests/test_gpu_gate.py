@@ -321,3 +321,15 @@ def test_async_host_copies_on_two_streams(qs):
     finally:
         for s in states:
             s.close()
+
+
+def test_allocation_failure_is_reported_and_recoverable(qs):
+    """A state larger than the device (n = 40, complex128: 17.6 TB) fails with QS_ENOMEM and
+    leaves the library usable."""
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_state_alloc(40, qs.QS_C128)
+    assert e.value.status == qs._lib.QS_ENOMEM
+    with qs.State(10, "c64") as st:
+        st.apply_gate(0, W.H_MATRIX)
+        z, nrm = st.expect_z()
+    assert abs(nrm - 1.0) < 1e-6 and abs(z[0]) < 1e-6
