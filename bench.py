@@ -279,7 +279,7 @@ def measure_adjoint(qs, W, reps=3):
     out = {"tile_bits_c64": {"forward": tuned["fwd"]["tile_bits"], "adjoint": tuned["adj"]["tile_bits"]}}
     grads = {}
     for label, dtype, flags in (("c64_fused", "c64", qs.QS_FLAG_FUSE), ("c64_unfused", "c64", 0),
-                                ("c128_plain", "c128", 0)):
+                                ("c128_plain", "c128", 0), ("c128_fused", "c128", qs.QS_FLAG_FUSE)):
         st = qs.State(n, dtype)
         try:
             st.adjoint_grad(gates, th, flags)  # warm-up (allocates lambda and scratch)
@@ -295,7 +295,7 @@ def measure_adjoint(qs, W, reps=3):
                           "energy": e}
         finally:
             st.close()
-    for label in ("c64_fused", "c64_unfused"):
+    for label in ("c64_fused", "c64_unfused", "c128_fused"):
         out[f"max_abs_grad_err_{label}_vs_c128"] = float(np.max(np.abs(grads[label] - grads["c128_plain"])))
     out["speedup_c64_fused_vs_c128_plain"] = round(out["c128_plain"]["s_per_gradient"] /
                                                    out["c64_fused"]["s_per_gradient"], 2)
@@ -412,6 +412,48 @@ def measure_paper_circuits(qs, W, reps=3):
         torch.cuda.empty_cache()
     out["note"] = ("paper_s: Tables 2 and 4 (GTX Titan Black / Stratix V, one OpenCL compute unit), context only; "
                    "algorithmic_GB counts 2*2^(n-c)*8 bytes per gate")
+    return out
+
+
+def measure_precision(qs, W):
+    """The precision circuit at full size: n = 32 from H on every qubit, 2000 gates (0-6
+    controls, 25 % X / CNOT / Toffoli), complex128 (68.7 GB) and complex64 (34.4 GB, fused) on
+    the device; complex64 against complex128: max-abs amplitude error, norm drift, <Z_i>."""
+    import numpy as np
+    import torch
+
+    n = 32
+    gates = W.precision_circuit(n, 2000, seed=2)
+    prefix = W.gate_list([W.make_gate(q, W.H_MATRIX) for q in range(n)])
+    b128 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    b64 = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    out = {}
+    try:
+        s128 = qs.State.wrap(b128, n)
+        s64 = qs.State.wrap(b64, n)
+        for st, label, flags in ((s128, "c128", 0), (s64, "c64_fused", qs.QS_FLAG_FUSE)):
+            st.set_basis(0)
+            st.apply_circuit(prefix, flags=flags)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st.apply_circuit(gates, flags=flags)
+            torch.cuda.synchronize()
+            out[label] = {"s": round(time.perf_counter() - t0, 3)}
+        z128, n128 = s128.expect_z()
+        z64, n64 = s64.expect_z()
+        err = 0.0
+        for i in range(0, 1 << n, 1 << 26):
+            d = b64[i:i + (1 << 26)].to(torch.complex128) - b128[i:i + (1 << 26)]
+            err = max(err, float(d.abs().max()))
+        out.update({"max_abs_err_c64_vs_c128": err, "norm_drift_c64": abs(n64 - 1.0), "norm_drift_c128": abs(n128 - 1.0),
+                    "max_abs_z_diff": float(np.max(np.abs(np.asarray(z64) - np.asarray(z128)))),
+                    "z_c128_first4": [round(float(x), 8) for x in z128[:4]],
+                    "workload": "n=32, H on every qubit then 2000 gates (0-6 controls, 25% X/CNOT/Toffoli, seed 2)"})
+        s128.close()
+        s64.close()
+    finally:
+        del b128, b64
+        torch.cuda.empty_cache()
     return out
 
 
@@ -664,6 +706,7 @@ def run_ours(args, rank, world, local_rank):
         result["masked_over_reduced_time_by_c"] = measure_masked(qs, n, sched)
         result["batch"] = measure_batch(qs, W)
         result["paper_circuits"] = measure_paper_circuits(qs, W)
+        result["precision_n32"] = measure_precision(qs, W)
         result["cpu_baseline"] = cpu_oracle_sample(n, sched)
 
     if rank == 0:

@@ -7,10 +7,11 @@
 // of one full read + write of the state: a separate launch of a gate costs the fraction of
 // 64-byte DRAM units it touches; a pass costs the fraction of tiles it touches (union bound
 // over its gates' tile predicates) plus a per-gate compute cost inside the tile (measured:
-// about 0.15 for complex64, whose gates are memory-bound, and 0.6 for complex128, whose gates
-// are FP64-bound either way). A gate joins a pass only if that is cheaper than running it
-// alone, and a pass is kept only if it is cheaper than its gates run alone (unless every gate
-// must go into a pass). The local set is finally padded with the lowest free qubits up to k.
+// about 0.15 for complex64, whose gates are memory-bound; complex128 arithmetic gates are
+// FP64-bound alone or in a pass, so there mostly exchanges join passes). A gate joins a pass
+// only if that is cheaper than running it alone, and a pass is kept only if it is cheaper than
+// its gates run alone (unless every gate must go into a pass). The local set is finally padded
+// with the lowest free qubits up to k.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -218,7 +219,15 @@ static void make_pass(int n, uint64_t Lmask, TilePass *P) {
     P->ntiles = 1ull << (n - P->k);
 }
 
-static double pass_gate_cost(int dtype) { return dtype == QS_C64 ? 0.15 : 0.6; }
+// Compute cost a gate adds inside a pass, in units of one state read + write. complex64
+// (measured, n = 24): 8-13 us per gate against 45 us for the state's read + write -> ~0.2, the
+// gates being memory-bound alone. complex128 gates are FP64-bound alone and inside a pass
+// alike (a general 2x2 costs ~3 units either way), so only exchanges (no arithmetic, ~0.33)
+// gain from a pass.
+static double pass_gate_cost(int dtype, const GatePlan &p) {
+    if (dtype == QS_C64) return 0.15;
+    return p.op == OP_SWAP ? 0.33 : 3.0;
+}
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
@@ -300,8 +309,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             }
         }
         uint64_t L = low;
-        double frac = 0.0, singles = 0.0;
-        const double cc = pass_gate_cost(dtype);
+        double frac = 0.0, singles = 0.0, compute = 0.0;
         int nparam = 0;
         std::vector<int> members;
         size_t j = i;
@@ -321,8 +329,10 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             const double frac2 = std::min(1.0, frac + f);
             int real = 0;
             for (int mbr : members) real += mbr >= 0;
+            const double cc = pass_gate_cost(dtype, p);
             if (real > 0 && allow_single && frac2 + cc > frac + single_fraction(p, dtype)) break;
             frac = frac2;
+            compute += cc;
             singles += single_fraction(p, dtype);
             L = L2;
             members.push_back(seq[j]);
@@ -335,7 +345,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             i = std::max(j, i + 1);
             continue;
         }
-        if (allow_single && (real < 2 || frac + cc * real >= singles)) {  // not worth a pass: the first gate runs alone
+        if (allow_single && (real < 2 || frac + compute >= singles)) {  // not worth a pass: the first gate runs alone
             const int g = seq[i];
             const bool param = adjoint && (*dus)[g] != nullptr;
             if (plans[g].units != 0 || param) prog->ops.push_back({-1, g});

@@ -413,3 +413,27 @@ def test_fused_programs_at_the_smallest_sizes(qs, dtype):
             st.apply_circuit(W.gate_list([]), flags=qs.QS_FLAG_FUSE)
             assert np.array_equal(st.to_numpy(), psi0.astype(NP[dtype]))
         assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), n
+
+
+def test_complex128_passes_of_exchanges(qs):
+    """complex128 fused programs: arithmetic gates run alone (FP64-bound either way), runs of
+    exchanges go into tile passes, also behind an arithmetic first gate; against the oracle
+    (exchange-only runs bit for bit)."""
+    rng = np.random.default_rng(128)
+    n = 14
+    gl = []
+    for blk in range(6):
+        gl.append(W.make_gate(int(rng.integers(0, 6)), W.haar_2x2(rng)))
+        for _ in range(20):
+            t = int(rng.integers(0, 8))
+            c = [q for q in range(n) if q != t][int(rng.integers(0, n - 1))]
+            gl.append(W.make_gate(t, None, (c,) if rng.random() < 0.5 else (), kind=W.KIND_X))
+    gates = W.gate_list(gl)
+    psi0 = random_state(n, "c128", 129)
+    ref = psi0.copy()
+    oracle.run_circuit(ref, n, gates)
+    with qs.State(n, "c128") as st:
+        st.from_numpy(psi0)
+        st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE)
+        got = st.to_numpy()
+    assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT["c128"]
