@@ -194,8 +194,13 @@ def energy(n: int, gates, theta, psi0=None) -> float:
 
 
 def param_shift_grad(n: int, gates, theta, psi0=None) -> np.ndarray:
-    """dE/dtheta_p = [E(theta_p + pi/2) - E(theta_p - pi/2)] / 2, exact for RY/RZ gates
-    (generator with eigenvalues +-1/2) when each parameter drives one gate."""
+    """dE/dtheta_p = [E(theta_p + pi/2) - E(theta_p - pi/2)] / 2, exact for uncontrolled RY/RZ
+    gates (generator with eigenvalues +-1/2) when each parameter drives one gate. A controlled
+    rotation's generator also has eigenvalue 0, where the two-term rule does not hold: such
+    circuits are rejected (use fd_grad)."""
+    for g in gates:
+        if int(g["kind"]) in (KIND_RY, KIND_RZ) and int(g["ctrl_mask"]) != 0:
+            raise ValueError("param_shift_grad: the two-term shift rule needs uncontrolled rotations")
     theta = np.asarray(theta, dtype=np.float64)
     g = np.zeros_like(theta)
     for p in range(theta.size):

@@ -58,6 +58,11 @@ struct TileGroup {
     uint32_t qsw[kGroupBits];  // shared-memory offset (swizzled) of each group qubit's bit
     int32_t gate_begin, gate_count;  // into the RegGate table
     int32_t hctrl;             // some gate of the group has a non-local control
+    // Exchanges at the start / end of the group whose controls all sit in the group permute its
+    // elements; they are folded into the row copies: element e is read from offset gperm[e]
+    // (has_g) and written to offset sperm[e] (has_s) instead of its own position.
+    uint16_t gperm[1 << kGroupBits], sperm[1 << kGroupBits];
+    uint8_t has_g, has_s, pad[2];
 };
 
 struct TilePass {

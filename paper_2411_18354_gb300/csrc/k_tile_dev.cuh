@@ -309,7 +309,7 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     for (int gi = 0; gi < group_count; ++gi) {
         const TileGroup &Gr = groups[gi];
-        if (Gr.hctrl) {
+        if (Gr.hctrl && !Gr.has_g && !Gr.has_s) {  // (folded exchanges act on every tile)
             bool any = false;
             for (int g = 0; g < Gr.gate_count; ++g)
                 any |= (base & gates[Gr.gate_begin + g].hmask) == gates[Gr.gate_begin + g].hvals;
@@ -336,10 +336,12 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                 ra[j] = 0;
                 for (int s = 0; s < Gr.nrseg; ++s) ra[j] |= (rho << Gr.rshift[s]) & Gr.rmask[s];
                 rs[j] = tile_swizzle(ra[j], SW);
+                const bool gp = Gr.has_g;  // uniform: exchanges folded into the gather
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const uint32_t ps = rs[j] ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
-                                        ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u);
+                    const uint32_t ps = rs[j] ^ (gp ? (uint32_t)Gr.gperm[e]
+                                                    : (((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
+                                                       ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u)));
                     if (active[j] && e < (1 << r)) {
                         v[j][e] = tp[ps];
                         if (ADJ) w[j][e] = tl[ps];
@@ -369,12 +371,14 @@ __device__ __forceinline__ void apply_groups(typename TileT<Real>::T2 *tp, typen
                     if (lane == 0) acc[R.slot * nwarps + warp].add(d);
                 }
             }
+            const bool sp = Gr.has_s;  // uniform: exchanges folded into the scatter
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const uint32_t ps = rs[j] ^ ((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
-                                        ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u);
+                    const uint32_t ps = rs[j] ^ (sp ? (uint32_t)Gr.sperm[e]
+                                                    : (((e & 1) ? qs_[0] : 0u) ^ ((e & 2) ? qs_[1] : 0u) ^
+                                                       ((e & 4) ? qs_[2] : 0u) ^ ((e & 8) ? qs_[3] : 0u)));
                     if (active[j] && e < (1 << r)) {
                         tp[ps] = v[j][e];
                         if (ADJ) tl[ps] = w[j][e];

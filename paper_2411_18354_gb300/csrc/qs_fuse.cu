@@ -20,6 +20,10 @@
 #include "k_tile.cuh"
 #include "qs_fuse.cuh"
 
+#ifndef QS_FOLD_EXCHANGES
+#define QS_FOLD_EXCHANGES 1
+#endif
+
 namespace qs {
 
 static int popc(uint64_t v) { return __builtin_popcountll(v); }
@@ -115,6 +119,7 @@ static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> 
     const int sw = dtype == QS_C64 ? 4 : 3;
     P->group_begin = (int)prog->groups.size();
     P->gate_begin = (int)prog->gates.size();
+    bool folded = false;
     size_t i = 0;
     while (i < lg.size()) {
         uint32_t S = 0;
@@ -146,6 +151,9 @@ static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> 
             Gr.rshift[s] = (uint8_t)map.shift[s];
         }
         Gr.gate_begin = (int)prog->gates.size();
+        for (int q = 0; q < kGroupBits; ++q) Gr.qsw[q] = q < m ? tile_swizzle(1u << Gr.q[q], sw) : 0u;
+        std::vector<RegGate> rg;
+        std::vector<int> rsrc;
         for (size_t g = i; g < j; ++g) {
             const LocalGate &L = lg[g];
             RegGate R;
@@ -173,16 +181,57 @@ static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> 
                 std::memcpy(R.D, ds[g], sizeof(R.D));
                 for (int q = 0; q < 8; ++q) R.Df[q] = (float)R.D[q];
             }
-            prog->gates.push_back(R);
-            prog->gate_src.push_back(src[g]);
+            rg.push_back(R);
+            rsrc.push_back(src[g]);
+        }
+        // leading and trailing exchanges with all controls in the group: a permutation of the
+        // 2^m elements, applied by the row copies (gather / scatter offsets) instead of gates
+        auto foldable = [&](const RegGate &R) {
+            return QS_FOLD_EXCHANGES && m == r && m == group_bits && R.op == OP_SWAP && R.crm == 0 && R.hmask == 0 &&
+                   R.slot < 0;
+        };
+        size_t lead = 0, trail = 0;
+        while (lead < rg.size() && foldable(rg[lead])) ++lead;
+        while (trail < rg.size() - lead && foldable(rg[rg.size() - 1 - trail])) ++trail;
+        auto apply_x = [](const RegGate &R, uint32_t x) {
+            return ((x & R.cqm) == R.cqv) ? (x ^ (1u << R.p)) : x;
+        };
+        auto offset = [&](uint32_t x) {
+            uint32_t o = 0;
+            for (int q = 0; q < m; ++q)
+                if ((x >> q) & 1u) o ^= Gr.qsw[q];
+            return (uint16_t)o;
+        };
+        const uint32_t E = 1u << m;
+        if (lead > 0) {  // element e of the row receives the amplitude that the exchanges move to e
+            Gr.has_g = 1;
+            for (uint32_t x = 0; x < E; ++x) {
+                uint32_t y = x;
+                for (size_t g = 0; g < lead; ++g) y = apply_x(rg[g], y);
+                Gr.gperm[y] = offset(x);
+            }
+        }
+        if (trail > 0) {  // element e goes where the exchanges move it
+            Gr.has_s = 1;
+            for (uint32_t x = 0; x < E; ++x) {
+                uint32_t y = x;
+                for (size_t g = rg.size() - trail; g < rg.size(); ++g) y = apply_x(rg[g], y);
+                Gr.sperm[x] = offset(y);
+            }
+        }
+        for (size_t g = lead; g < rg.size() - trail; ++g) {
+            prog->gates.push_back(rg[g]);
+            prog->gate_src.push_back(rsrc[g]);
         }
         Gr.gate_count = (int)prog->gates.size() - Gr.gate_begin;
-        for (int q = 0; q < kGroupBits; ++q) Gr.qsw[q] = q < m ? tile_swizzle(1u << Gr.q[q], sw) : 0u;
         for (int g = Gr.gate_begin; g < Gr.gate_begin + Gr.gate_count; ++g) Gr.hctrl |= prog->gates[g].hmask != 0;
         P->hctrl |= Gr.hctrl;
+        folded |= Gr.has_g || Gr.has_s;
         prog->groups.push_back(Gr);
         i = j;
     }
+    // folded exchanges act on every tile: the pass may then skip no tile
+    if (folded) P->hctrl = 0;
     P->group_count = (int)prog->groups.size() - P->group_begin;
     P->gate_count = (int)prog->gates.size() - P->gate_begin;
 }

@@ -437,3 +437,42 @@ def test_complex128_passes_of_exchanges(qs):
         st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE)
         got = st.to_numpy()
     assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT["c128"]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("tile_bits", [6, 9])
+def test_folded_exchanges_with_tile_predicates(qs, dtype, tile_bits, monkeypatch):
+    """CNOT ladders inside register groups are folded into the row copies; the same passes
+    hold gates whose controls are not local (tiles they skip): every tile must still see the
+    folded exchanges. Forward against the oracle, gradient against its finite differences
+    (h = 1e-4, error O(h^2)), n = 15."""
+    monkeypatch.setenv("QS_TILE_BITS", str(tile_bits))
+    n, layers = 15, 3
+    rng = np.random.default_rng(tile_bits)
+    gl = []
+    p = 0
+    for _ in range(layers):
+        for q in range(n):
+            gl.append(W.make_gate(q, None, (), kind=W.KIND_RY, param=p))
+            p += 1
+        for q in range(n - 1):
+            gl.append(W.make_gate(q + 1, None, (q,), kind=W.KIND_X))
+        for _ in range(4):  # controlled rotations with a far, non-local control
+            t = int(rng.integers(0, 4))
+            gl.append(W.make_gate(t, None, (n - 1 - int(rng.integers(0, 3)),), kind=W.KIND_RZ, param=p))
+            p += 1
+        for q in range(n - 2, -1, -1):
+            gl.append(W.make_gate(q + 1, None, (q,), kind=W.KIND_X))
+    gates = W.gate_list(gl)
+    th = rng.uniform(0, 6.3, size=p)
+    psi0 = W.basis_state(n, 0, NP[dtype])
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates, th)
+    with qs.State(n, dtype) as st:
+        st.apply_circuit(gates, th, flags=qs.QS_FLAG_FUSE)
+        got = c128_of(st.to_numpy())
+    assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype]
+    fd = oracle.fd_grad(n, gates, th)  # controlled rotations: no two-term shift rule
+    with qs.State(n, dtype) as st:
+        e, g = st.adjoint_grad(gates, th, qs.QS_FLAG_FUSE)
+    assert np.max(np.abs(g - fd)) <= (1e-4 if dtype == "c64" else 1e-6)

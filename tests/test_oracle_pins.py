@@ -384,3 +384,23 @@ def test_param_shift_matches_finite_differences_on_ansatz():
     ps = oracle.param_shift_grad(n, gates, th)
     fd = oracle.fd_grad(n, gates, th, h=1e-4)
     assert np.max(np.abs(ps - fd)) < 1e-7
+
+
+def test_parameter_shift_rejects_controlled_rotations():
+    """The two-term shift rule holds for generators with eigenvalues +-1/2 only; a controlled
+    rotation's generator also has 0, so the oracle refuses rather than return a wrong value,
+    and its finite differences show the difference."""
+    n = 3
+    gl = [W.make_gate(q, None, (), kind=W.KIND_RY, param=q) for q in range(n)]
+    gl.append(W.make_gate(0, None, (2,), kind=W.KIND_RZ, param=3))  # RZ on q0, control q2
+    gl += [W.make_gate(q, None, (), kind=W.KIND_RY, param=4 + q) for q in range(n)]
+    gates = W.gate_list(gl)
+    th = np.array([0.7, 1.1, 0.4, 1.9, 0.5, 0.8, 1.2])
+    with pytest.raises(ValueError):
+        oracle.param_shift_grad(n, gates, th)
+    fd = oracle.fd_grad(n, gates, th)
+    tp, tm = th.copy(), th.copy()
+    tp[3] += np.pi / 2
+    tm[3] -= np.pi / 2
+    two_term = 0.5 * (oracle.energy(n, gates, tp) - oracle.energy(n, gates, tm))
+    assert abs(two_term - fd[3]) > 1e-2  # 0.220 against 0.159
