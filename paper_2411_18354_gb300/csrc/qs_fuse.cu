@@ -1,17 +1,17 @@
 // qs_fuse.cu -- host planner that groups consecutive gates into fused tile passes.
 //
-// Greedy, in execution order: a pass starts with the lowest b qubits local (b = 4 for
-// complex64, 3 for complex128, so that tile rows are 128 or 128 bytes of contiguous memory)
-// and takes the following gates while their targets fit in k local qubits. A gate's controls
-// need not be local: non-local controls become the gate's tile predicate. Costs are in units
-// of one full read + write of the state: a separate launch of a gate costs the fraction of
-// 64-byte DRAM units it touches; a pass costs the fraction of tiles it touches (union bound
-// over its gates' tile predicates) plus a per-gate compute cost inside the tile (measured:
-// about 0.15 for complex64, whose gates are memory-bound; complex128 arithmetic gates are
-// FP64-bound alone or in a pass, so there mostly exchanges join passes). A gate joins a pass
-// only if that is cheaper than running it alone, and a pass is kept only if it is cheaper than
-// its gates run alone (unless every gate must go into a pass). The local set is finally padded
-// with the lowest free qubits up to k.
+// A pass keeps the lowest b qubits local (b = 4 for complex64, 3 for complex128, so that tile
+// rows are 128 bytes of contiguous memory) and takes a run of consecutive gates whose targets
+// fit in k local qubits. A gate's controls need not be local: non-local controls become the
+// gate's tile predicate. Costs are in units of one full read + write of the state: a separate
+// launch of a gate costs the fraction of 64-byte DRAM units it touches; a pass costs the
+// fraction of tiles it touches (union bound over its gates' tile predicates) plus a per-gate
+// compute cost inside the tile (measured: about 0.15 for complex64, whose gates are
+// memory-bound; complex128 arithmetic gates are FP64-bound alone or in a pass, so there mostly
+// exchanges join passes). Between runs of diagonal gates the gate sequence is cut into passes
+// and single launches of least total cost (dynamic programming over where each pass ends);
+// where every gate must go into a pass, each pass takes as many gates as fit. The local set is
+// finally padded with the lowest free qubits up to k.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -303,6 +303,68 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             const GatePlan &p = plans[seq[j]];
             drun[j] = p.units == 0 ? drun[j + 1] : ((p.op == OP_DIAG || p.op == OP_SIDE) ? drun[j + 1] + 1 : 0);
         }
+    auto is_param = [&](int g) { return adjoint && (*dus)[g] != nullptr; };
+    // Take gates seq[i], seq[i + 1], ... (before `end`) into one pass while its targets fit in
+    // k local qubits and the gate and parameter limits allow; visit(j, frac, compute, real)
+    // after gate j joined: frac = fraction of tiles touched (union bound over the gates' tile
+    // predicates), compute = summed per-gate cost, real = non-identity gates so far.
+    auto extend = [&](size_t i0, size_t end, auto &&visit) {
+        uint64_t L = low;
+        double frac = 0.0, compute = 0.0;
+        int nparam = 0, real = 0, count = 0;
+        for (size_t j = i0; j < end && count < max_gates; ++j) {
+            const GatePlan &p = plans[seq[j]];
+            const bool param = is_param(seq[j]);
+            if (p.units != 0 || param) {
+                const uint64_t L2 = L | (1ull << p.t);
+                if (popc(L2) > k) break;
+                if (param && nparam >= kTileMaxParam) break;
+                frac = std::min(1.0, frac + std::ldexp(1.0, -popc(p.ctrl_mask & ~L2)));
+                compute += pass_gate_cost(dtype, p);
+                L = L2;
+                nparam += param;
+                ++real;
+            }
+            ++count;
+            visit(j, frac, compute, real);
+        }
+    };
+    // One pass of gates seq[a, b) (identities skipped), its local set padded with the lowest
+    // free qubits.
+    auto emit_pass = [&](size_t a, size_t b) {
+        uint64_t L = low;
+        for (size_t j = a; j < b; ++j)
+            if (plans[seq[j]].units != 0 || is_param(seq[j])) L |= 1ull << plans[seq[j]].t;
+        for (int q = 0; q < n && popc(L) < k; ++q) L |= 1ull << q;
+        int local_of[64];
+        for (int q = 0, l = 0; q < n; ++q) local_of[q] = ((L >> q) & 1ull) ? l++ : -1;
+        TilePass P;
+        make_pass(n, L, &P);
+        std::vector<LocalGate> lg;
+        std::vector<int> slots, src;
+        std::vector<const double *> ds;
+        for (size_t j = a; j < b; ++j) {
+            const int mbr = seq[j];
+            if (plans[mbr].units == 0 && !is_param(mbr)) continue;
+            LocalGate g = make_local_gate(plans[mbr], L, local_of);
+            const double *d = nullptr;
+            int slot = -1;
+            if (is_param(mbr)) {
+                if (g.op != OP_GEN && g.op != OP_DIAG && g.op != OP_REAL) g.op = OP_GEN;
+                d = (*dus)[mbr];
+                slot = P.nparam;
+                P.param_gslot[P.nparam++] = (*gslots)[mbr];
+            }
+            lg.push_back(g);
+            slots.push_back(slot);
+            ds.push_back(d);
+            src.push_back(mbr);
+        }
+        add_groups(lg, slots, ds, src, P.k, dtype, group_bits > 0 ? group_bits : (adjoint ? kGroupBitsAdjoint : kGroupBits),
+                   prog, &P);
+        prog->ops.push_back({(int)prog->passes.size(), -1});
+        prog->passes.push_back(P);
+    };
     size_t i = 0;
     while (i < seq.size()) {
         if (diag_runs) {
@@ -357,80 +419,53 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
                 continue;
             }
         }
-        uint64_t L = low;
-        double frac = 0.0, singles = 0.0, compute = 0.0;
-        int nparam = 0;
-        std::vector<int> members;
-        size_t j = i;
-        while (j < seq.size() && (int)members.size() < max_gates) {
+        // the gates up to the next diagonal run
+        size_t r1 = i + 1;
+        while (r1 < seq.size() && !(diag_runs && drun[r1] >= kDiagMinRun)) ++r1;
+        if (!allow_single) {  // every gate goes into a pass: each pass takes as many as fit
+            while (i < r1) {
+                size_t e = i;
+                extend(i, r1, [&](size_t j, double, double, int) { e = j; });
+                emit_pass(i, e + 1);
+                i = e + 1;
+            }
+            continue;
+        }
+        // least modelled cost of gates [j, r1): best[j - i]; the first segment ends before
+        // cut[j - i] and is a pass if is_pass[j - i]
+        const size_t m = r1 - i;
+        std::vector<double> best(m + 1, 0.0);
+        std::vector<size_t> cut(m + 1, r1);
+        std::vector<char> is_pass(m + 1, 0);
+        for (size_t j = r1; j-- > i;) {
             const GatePlan &p = plans[seq[j]];
-            if (diag_runs && j > i && drun[j] >= kDiagMinRun) break;  // a diagonal pass follows
-            const bool param = adjoint && (*dus)[seq[j]] != nullptr;
-            if (p.units == 0 && !param) {  // identity: nothing to apply
-                members.push_back(-1 - seq[j]);
-                ++j;
-                continue;
+            const double alone = (p.units == 0 && !is_param(seq[j])) ? 0.0 : single_fraction(p, dtype);
+            double b = alone + best[j + 1 - i];
+            size_t c = j + 1;
+            char ps = 0;
+            extend(j, r1, [&](size_t e, double frac, double compute, int real) {
+                if (real < 2) return;
+                const double v = frac + compute + best[e + 1 - i];
+                if (v < b - 1e-9) {
+                    b = v;
+                    c = e + 1;
+                    ps = 1;
+                }
+            });
+            best[j - i] = b;
+            cut[j - i] = c;
+            is_pass[j - i] = ps;
+        }
+        while (i < r1) {
+            const size_t c = cut[i - (r1 - m)];
+            if (is_pass[i - (r1 - m)]) {
+                emit_pass(i, c);
+            } else {
+                const int g = seq[i];
+                if (plans[g].units != 0 || is_param(g)) prog->ops.push_back({-1, g});
             }
-            const uint64_t L2 = L | (1ull << p.t);
-            if (popc(L2) > k) break;
-            if (param && nparam >= kTileMaxParam) break;
-            const double f = std::ldexp(1.0, -popc(p.ctrl_mask & ~L2));
-            const double frac2 = std::min(1.0, frac + f);
-            int real = 0;
-            for (int mbr : members) real += mbr >= 0;
-            const double cc = pass_gate_cost(dtype, p);
-            if (real > 0 && allow_single && frac2 + cc > frac + single_fraction(p, dtype)) break;
-            frac = frac2;
-            compute += cc;
-            singles += single_fraction(p, dtype);
-            L = L2;
-            members.push_back(seq[j]);
-            nparam += param;
-            ++j;
+            i = c;
         }
-        int real = 0;
-        for (int mbr : members) real += mbr >= 0;
-        if (real == 0) {  // only identity gates (j > i here: the first real gate always fits)
-            i = std::max(j, i + 1);
-            continue;
-        }
-        if (allow_single && (real < 2 || frac + compute >= singles)) {  // not worth a pass: the first gate runs alone
-            const int g = seq[i];
-            const bool param = adjoint && (*dus)[g] != nullptr;
-            if (plans[g].units != 0 || param) prog->ops.push_back({-1, g});
-            ++i;
-            continue;
-        }
-        // pad the local set with the lowest free qubits
-        for (int q = 0; q < n && popc(L) < k; ++q) L |= 1ull << q;
-        int local_of[64];
-        for (int q = 0, l = 0; q < n; ++q) local_of[q] = ((L >> q) & 1ull) ? l++ : -1;
-        TilePass P;
-        make_pass(n, L, &P);
-        std::vector<LocalGate> lg;
-        std::vector<int> slots, src;
-        std::vector<const double *> ds;
-        for (int mbr : members) {
-            if (mbr < 0) continue;
-            LocalGate g = make_local_gate(plans[mbr], L, local_of);
-            const double *d = nullptr;
-            int slot = -1;
-            if (adjoint && (*dus)[mbr]) {
-                if (g.op != OP_GEN && g.op != OP_DIAG && g.op != OP_REAL) g.op = OP_GEN;
-                d = (*dus)[mbr];
-                slot = P.nparam;
-                P.param_gslot[P.nparam++] = (*gslots)[mbr];
-            }
-            lg.push_back(g);
-            slots.push_back(slot);
-            ds.push_back(d);
-            src.push_back(mbr);
-        }
-        add_groups(lg, slots, ds, src, P.k, dtype, group_bits > 0 ? group_bits : (adjoint ? kGroupBitsAdjoint : kGroupBits),
-                   prog, &P);
-        prog->ops.push_back({(int)prog->passes.size(), -1});
-        prog->passes.push_back(P);
-        i = j;
     }
     return true;
 }
