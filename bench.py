@@ -637,42 +637,61 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.quick:
         # end to end through the C-ABI with host buffers: every step uploads its input state from
-        # page-locked host memory, applies the 27 gates and downloads the result. Two states on
-        # two streams alternate, so one step's download overlaps the next step's upload and gates
-        # (the host link carries both directions at once); each step still moves 2 x 8.6 GB.
+        # page-locked host memory, applies the 27 gates and downloads the result. Three states on
+        # three streams rotate, so while one state's gates run, the link carries another's upload
+        # and a third's download at once (both directions busy); each step still moves
+        # 2 x 8.6 GB.
         st.close()
         torch.cuda.empty_cache()
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        nbuf = 3
+        streams = [torch.cuda.Stream() for _ in range(nbuf)]
         states = [qs.State(n, "c64", stream=int(sm.cuda_stream)) for sm in streams]
-        hosts = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(2)]
+        hosts = [torch.empty(1 << n, dtype=torch.complex64).pin_memory() for _ in range(nbuf)]
         hnps = [h.numpy() for h in hosts]
-        for i in range(2):  # inputs: the uniform superposition, written through the library
+        for i in range(nbuf):  # inputs: the uniform superposition, written through the library
             for q in range(n):
                 states[i].apply_gate(q, W.H_MATRIX)
             qs.qs_state_copy_to_host_async(states[i].h, hnps[i])
             qs.qs_state_synchronize(states[i].h)
-        e2e_steps = 4
+        e2e_steps = 9
 
-        def e2e_step(k):
-            i = k % 2
+        phase_ev = []  # per timed step: events before the upload, after it, after the gates, after the download
+
+        def e2e_step(k, record=False):
+            i = k % nbuf
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+            if record:
+                ev[0].record(streams[i])
             qs.qs_state_copy_from_host_async(states[i].h, hnps[i])
+            if record:
+                ev[1].record(streams[i])
             for (c, t, m, v, U) in sched[k % SETS]:
                 qs._lib.qs_apply_gate(states[i].h, t, m, v, U)
+            if record:
+                ev[2].record(streams[i])
             qs.qs_state_copy_to_host_async(states[i].h, hnps[i])
+            if record:
+                ev[3].record(streams[i])
+                phase_ev.append(ev)
 
-        for k in range(2):  # warm-up
+        for k in range(nbuf):  # warm-up
             e2e_step(k)
-        for i in range(2):
+        for i in range(nbuf):
             qs.qs_state_synchronize(states[i].h)
         t0 = time.perf_counter()
         for k in range(e2e_steps):
-            e2e_step(k)
-        for i in range(2):
+            e2e_step(k, record=True)
+        for i in range(nbuf):
             qs.qs_state_synchronize(states[i].h)
         e2e_s = time.perf_counter() - t0
+        med = lambda xs: round(sorted(xs)[len(xs) // 2], 2)
+        phases = {"h2d_ms": med([e[0].elapsed_time(e[1]) for e in phase_ev]),
+                  "gates_ms": med([e[1].elapsed_time(e[2]) for e in phase_ev]),
+                  "d2h_ms": med([e[2].elapsed_time(e[3]) for e in phase_ev])}
         result["e2e"] = {"value": round(world * e2e_steps * step_bytes / e2e_s / 1e9, 2), "unit": "GB/s",
                          "h2d_bytes_per_step": int(hnps[0].nbytes), "d2h_bytes_per_step": int(hnps[0].nbytes),
-                         "steps": e2e_steps, "pipeline": "2 states on 2 streams, async copies from page-locked memory"}
+                         "steps": e2e_steps, "pipeline": f"{nbuf} states on {nbuf} streams, async copies from page-locked memory",
+                         "median_phase_ms": phases}
         for x in states:
             x.close()
         del hosts, hnps
