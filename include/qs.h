@@ -153,14 +153,41 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
 
 /* Apply `count` gates in order (gates run serially, Section III). RY/RZ gates read
  * theta[param] (theta may be NULL when no gate is parameterised; n_theta is its length).
- * All gates are validated before anything is launched. flags: QS_FLAG_FUSE runs maximal
- * runs of consecutive gates whose target and controls are below the tile size in one
- * HBM round trip; QS_FLAG_GRAPH records the launches into a CUDA graph and launches it.
+ * All gates are validated before anything is launched. flags: QS_FLAG_FUSE runs runs of
+ * consecutive gates whose targets fit in one shared-memory tile in one HBM round trip (a tile
+ * pass; controls outside the tile select the tiles a gate changes) and runs of diagonal
+ * gates in one pass each, as qs_circuit_schedule plans them; QS_FLAG_GRAPH records the
+ * launches into a CUDA graph and launches it.
  * QS_FLAG_MASKED runs every gate with the baseline schedule of Section III-A instead (all
  * 2^(n-1) pair iterations, controls tested per pair, the general 2x2 update), the
  * comparator of qs_apply_gate_masked for whole circuits; QS_EINVAL with QS_FLAG_FUSE. */
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
                            const double *theta, size_t n_theta, int flags);
+
+/* The launch schedule qs_apply_circuit would use for `count` gates on an n-qubit state of
+ * precision `dtype` with `flags`, computed on the host: no state, device or CUDA call is
+ * needed. Gates and flags are validated as by qs_apply_circuit (QS_EINVAL, nothing filled).
+ * With QS_FLAG_FUSE this is the fusion planner's result (gate fusion is the optimisation
+ * the paper's conclusion proposes): the gates, after same-target merging, cut into single
+ * launches, tile passes and diagonal runs of least modelled cost. model_cost is that cost
+ * in units of one read + write of the whole state (the planner's estimate, not a
+ * measurement): per launch the fraction of the state it moves, the per-gate work inside a
+ * pass, and ~2 us of launch latency; without QS_FLAG_FUSE the fraction is each gate's own
+ * (1 per gate with QS_FLAG_MASKED). pass_gates does not count exchanges folded into a
+ * register group's row copies. */
+typedef struct {
+    int32_t launches;      /* kernel launches */
+    int32_t single_gates;  /* launches of one gate */
+    int32_t tile_passes;   /* fused passes over shared-memory tiles */
+    int32_t diag_runs;     /* passes that apply a run of diagonal gates */
+    int32_t gates;         /* gates after same-target merging (identities included) */
+    int32_t pass_gates;    /* gates applied inside tile passes */
+    double model_cost;
+} qs_schedule;
+
+qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
+                              const double *theta, size_t n_theta, int flags,
+                              qs_schedule *out);
 
 /* Tile size of the fused passes (QS_FLAG_FUSE) for one precision, forward (adjoint = 0) or
  * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, 5..14, or 0 for the

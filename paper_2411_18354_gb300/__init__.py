@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     QS_C64, QS_C128, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_MASKED, QS_FLAG_OUT_DEVICE, QS_GATE_U,
-    QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate,
+    QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_schedule,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
     qs_state_alloc, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
     qs_set_l2_fetch_bytes, qs_set_tile_bits,
@@ -26,6 +26,12 @@ from .gates import GATE_DTYPE, as_gate_array  # noqa: F401
 
 _DT = {"c64": QS_C64, "complex64": QS_C64, "c128": QS_C128, "complex128": QS_C128}
 _NP = {QS_C64: np.complex64, QS_C128: np.complex128}
+
+
+def circuit_schedule(n: int, gates, theta=None, flags: int = QS_FLAG_FUSE, dtype="c64") -> dict:
+    """Launch schedule of ``State(n, dtype).apply_circuit(gates, theta, flags)``: launches,
+    single gates, tile passes, diagonal runs and the planner's modelled cost (host only)."""
+    return qs_circuit_schedule(n, _DT[dtype], gates, theta, flags)
 
 
 def _current_stream() -> int:

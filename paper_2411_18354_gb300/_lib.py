@@ -53,6 +53,8 @@ _SIGNATURES = [
     ("qs_apply_x", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64]),
     ("qs_apply_gate_masked", ctypes.c_int, [_c_state_p, ctypes.c_int, _u64, _u64, _dp]),
     ("qs_apply_circuit", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, ctypes.c_int]),
+    ("qs_circuit_schedule", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
+                                           ctypes.c_int, _vp]),
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
     ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
@@ -216,6 +218,23 @@ def qs_apply_circuit(h: int, gates, theta=None, flags: int = 0) -> None:
     g, gp = _gates_arg(gates)
     t, tp, nt = _theta_arg(theta)
     _check(lib().qs_apply_circuit(_c_state_p(h), gp, g.size, tp, nt, flags))
+
+
+class QsSchedule(ctypes.Structure):
+    """``qs_schedule`` of include/qs.h."""
+
+    _fields_ = [("launches", ctypes.c_int32), ("single_gates", ctypes.c_int32), ("tile_passes", ctypes.c_int32),
+                ("diag_runs", ctypes.c_int32), ("gates", ctypes.c_int32), ("pass_gates", ctypes.c_int32),
+                ("model_cost", ctypes.c_double)]
+
+
+def qs_circuit_schedule(n: int, dtype: int, gates, theta=None, flags: int = 0) -> dict:
+    """The launch schedule qs_apply_circuit would use (host only, no device needed)."""
+    g, gp = _gates_arg(gates)
+    t, tp, nt = _theta_arg(theta)
+    out = QsSchedule()
+    _check(lib().qs_circuit_schedule(n, dtype, gp, g.size, tp, nt, flags, _vp(ctypes.addressof(out))))
+    return {name: getattr(out, name) for name, _ in QsSchedule._fields_}
 
 
 def qs_expect_z(h: int, flags: int = 0, out=None, out_norm2=None):

@@ -9,6 +9,9 @@ namespace {
 
 using namespace tiledev;
 
+static_assert(sizeof(TileGroup) % 16 == 0 && sizeof(SGate<float>) % 16 == 0 && sizeof(SGate<double>) % 16 == 0,
+              "per-pass shared-memory tables keep 16-byte alignment");
+
 template <typename Real, bool ADJ>
 __global__ void __launch_bounds__(kTileThreads, (ADJ && sizeof(Real) == 8) ? 1 : 2)
 k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2 *__restrict__ lam, const TilePass P,
@@ -21,8 +24,8 @@ k_tile_pass(typename TileT<Real>::T2 *__restrict__ psi, typename TileT<Real>::T2
     T2 *tl = tp + T;  // adjoint: lambda tile
     Acc<Real> *acc = reinterpret_cast<Acc<Real> *>(smem_raw + (ADJ ? 2 : 1) * (size_t)T * sizeof(T2));  // [kTileMaxParam][8]
     TileGroup *sgroups = reinterpret_cast<TileGroup *>(acc + (ADJ ? kTileMaxParam * (kTileThreads / 32) : 0));
-    SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + kTileMaxGates);
-    uint64_t *g_j = reinterpret_cast<uint64_t *>(sgates + kTileMaxGates);
+    SGate<Real> *sgates = reinterpret_cast<SGate<Real> *>(sgroups + P.group_count);  // tables sized for this pass
+    uint64_t *g_j = reinterpret_cast<uint64_t *>(sgates + P.gate_count);
     uint32_t *s_j = reinterpret_cast<uint32_t *>(g_j + kTileMaxSteps);
     const int tid = threadIdx.x;
     if (ADJ)
@@ -59,7 +62,7 @@ template <typename Real, bool ADJ>
 cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGroup *groups, const RegGate *gates, double *part,
                size_t part_stride, cudaStream_t st) {
     auto kern = k_tile_pass<Real, ADJ>;
-    const size_t smem = tile_smem_bytes(sizeof(Real) == 4 ? QS_C64 : QS_C128, p.k, ADJ);
+    const size_t smem = tile_smem_bytes(sizeof(Real) == 4 ? QS_C64 : QS_C128, p.k, ADJ, p.group_count, p.gate_count);
     static std::atomic<size_t> configured[64];  // per device: dynamic shared memory allowed so far
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
@@ -83,11 +86,11 @@ cudaError_t go(void *psi, void *lam, const TilePass &p, const TileGroup *groups,
 
 }  // namespace
 
-size_t tile_smem_bytes(int dtype, int k, bool adjoint) {
+size_t tile_smem_bytes(int dtype, int k, bool adjoint, int groups, int gates) {
     const size_t es = dtype == QS_C64 ? 8 : 16;
     const size_t sg = dtype == QS_C64 ? sizeof(SGate<float>) : sizeof(SGate<double>);
     return (adjoint ? 2 : 1) * (size_t(1) << k) * es + (adjoint ? kTileMaxParam * (kTileThreads / 32) * sizeof(double) : 0) +
-           kTileMaxGates * (sizeof(TileGroup) + sg) + kTileMaxSteps * (sizeof(uint64_t) + sizeof(uint32_t));
+           (size_t)groups * sizeof(TileGroup) + (size_t)gates * sg + kTileMaxSteps * (sizeof(uint64_t) + sizeof(uint32_t));
 }
 
 cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,

@@ -24,7 +24,8 @@ constexpr int kTileMaxBits = 14;
 constexpr int kGroupBits = 4;      // register qubits per group, at most (16 amplitudes per row)
 constexpr int kGroupBitsAdjoint = 3;  // in the adjoint sweep (psi and lambda rows in registers)
 constexpr int kTileMaxParam = 64;  // parameterised gates per adjoint pass
-constexpr int kTileMaxGates = 64;  // gates (and so at most as many groups) per pass
+constexpr int kTileMaxGates = 64;   // gates (and so at most as many groups) per pass of the batched kernel
+constexpr int kPassMaxGates = 128;  // the same for a single-state tile pass (tables sized per pass)
 constexpr int kTileThreads = 256;
 
 // One gate inside a register group.
@@ -84,7 +85,7 @@ struct TilePass {
 // `part` the gradient partial array [slot][part_stride] (adjoint only).
 cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,
                              const RegGate *gates, double *part, size_t part_stride, cudaStream_t st);
-size_t tile_smem_bytes(int dtype, int k, bool adjoint);
+size_t tile_smem_bytes(int dtype, int k, bool adjoint, int groups, int gates);
 
 // Shared-memory position of local index a (XOR swizzle of the low `sw` bits with the folded
 // higher bits; sw = 4 for complex64, 3 for complex128). A bijection on [0, 2^k).

@@ -137,7 +137,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     const int es = (int)elem_bytes(dtype);
     if (small_bits <= 0) small_bits = dtype == QS_C64 ? 12 : 11;
     if (tile_bits <= 0) tile_bits = dtype == QS_C64 ? 11 : 10;
-    if (max_pass_gates <= 0) max_pass_gates = kTileMaxGates;
+    if (max_pass_gates <= 0 || max_pass_gates > kTileMaxGates) max_pass_gates = kTileMaxGates;  // its tables' size
     if (small_bits > kTileMaxBits || tile_bits > kTileMaxBits || tile_bits < 5)
         return set_error(QS_EINVAL, "qs_batch_create: small_bits / tile_bits out of range (tile_bits 5..14)");
     if (gate_offsets[0] != 0 || param_offsets[0] != 0) return set_error(QS_EINVAL, "qs_batch_create: offsets must start at 0");

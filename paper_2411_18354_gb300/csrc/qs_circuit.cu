@@ -285,6 +285,56 @@ qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits) {
 
 int qs_get_tile_bits(qs_dtype dtype, int adjoint) { return tile_bits(dtype, adjoint != 0); }
 
+qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count, const double *theta,
+                              size_t n_theta, int flags, qs_schedule *out) {
+    if (!out) return set_error(QS_EINVAL, "qs_circuit_schedule: out is NULL");
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_circuit_schedule: bad dtype");
+    if (n < 1 || n > kMaxQubits) return set_error(QS_EINVAL, "qs_circuit_schedule: n out of range");
+    if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_circuit_schedule: gates is NULL");
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED))
+        return set_error(QS_EINVAL, "qs_circuit_schedule: unknown flags");
+    if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
+        return set_error(QS_EINVAL, "qs_circuit_schedule: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
+    qs_state shape;  // planning reads only the state's size and precision
+    shape.n = n;
+    shape.dtype = dtype;
+    std::vector<GatePlan> plans(count);
+    char err[256];
+    for (size_t i = 0; i < count; ++i)
+        if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
+            return set_error(QS_EINVAL, err);
+    const bool masked = (flags & QS_FLAG_MASKED) != 0;
+    if (!masked) merge_runs(&shape, plans);
+    qs_schedule r;
+    std::memset(&r, 0, sizeof(r));
+    r.gates = (int32_t)plans.size();
+    if (flags & QS_FLAG_FUSE) {
+        std::vector<int> seq(plans.size());
+        for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
+        FusedProgram prog;
+        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog);
+        for (const FusedOp &op : prog.ops) {
+            if (op.drun >= 0)
+                ++r.diag_runs;
+            else if (op.pass >= 0)
+                ++r.tile_passes;
+            else
+                ++r.single_gates;
+        }
+        for (const TilePass &P : prog.passes) r.pass_gates += P.gate_count;
+        r.model_cost = prog.model_cost;
+    } else {
+        for (const GatePlan &p : plans) {
+            if (p.units == 0) continue;
+            ++r.single_gates;
+            r.model_cost += (masked ? 1.0 : single_launch_cost(p, dtype)) + launch_latency_cost(n, dtype);
+        }
+    }
+    r.launches = r.single_gates + r.tile_passes + r.diag_runs;
+    *out = r;
+    return QS_OK;
+}
+
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
                            int flags) {
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");

@@ -8,10 +8,12 @@
 // fraction of tiles it touches (union bound over its gates' tile predicates) plus a per-gate
 // compute cost inside the tile (measured: about 0.15 for complex64, whose gates are
 // memory-bound; complex128 arithmetic gates are FP64-bound alone or in a pass, so there mostly
-// exchanges join passes). Between runs of diagonal gates the gate sequence is cut into passes
-// and single launches of least total cost (dynamic programming over where each pass ends);
-// where every gate must go into a pass, each pass takes as many gates as fit. The local set is
-// finally padded with the lowest free qubits up to k.
+// exchanges join passes). A run of diagonal gates can also go to one k_diag_run launch (up to
+// 64 gates; an uncontrolled gate just before the run can lead it), which costs one read +
+// write of the chunks the run can change. The gate sequence is cut into single launches,
+// passes and diagonal runs of least total modelled cost (dynamic programming over where each
+// segment ends); where every gate must go into a pass, each pass takes as many gates as fit.
+// The local set is finally padded with the lowest free qubits up to k.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -30,7 +32,14 @@ static int popc(uint64_t v) { return __builtin_popcountll(v); }
 
 // Fraction of the state a separate k_gate launch moves, counted in 64-byte DRAM units:
 // controls on the qubits inside one unit do not reduce it.
-static double single_fraction(const GatePlan &p, int dtype) {
+// Every launch also pays ~2 us of fixed latency (start and drain, back to back in a graph): in
+// units of one state read + write at ~6 TB/s it decides small states (one pass for a whole
+// state that fits a tile) and hardly matters from n ~ 24 on.
+double launch_latency_cost(int n, int dtype) {
+    return 2e-6 / (std::ldexp(2.0 * (dtype == QS_C64 ? 8.0 : 16.0), n) / 6.0e12);
+}
+
+double single_launch_cost(const GatePlan &p, int dtype) {
     const int unit_bits = dtype == QS_C64 ? 3 : 2;
     const uint64_t high = p.ctrl_mask & ~((1ull << unit_bits) - 1ull);
     return std::ldexp(1.0, -popc(high));
@@ -268,15 +277,22 @@ static void make_pass(int n, uint64_t Lmask, TilePass *P) {
     P->ntiles = 1ull << (n - P->k);
 }
 
-// Compute cost a gate adds inside a pass, in units of one state read + write. complex64
-// (measured, n = 24): 8-13 us per gate against 45 us for the state's read + write -> ~0.2, the
-// gates being memory-bound alone. complex128 gates are FP64-bound alone and inside a pass
+// Compute cost a gate adds inside a pass, in units of one state read + write. complex64,
+// measured at n = 24 (2^12-amplitude tiles, one state read + write = 45 us): 8-13 us per gate
+// whatever its kind (general 11.3, real 9.1, exchange 8.2 unless folded into a register
+// group's gather / scatter, diagonal about as much: the interpreter's per-gate work, not the
+// arithmetic, sets it), also for gates whose non-local controls select only some tiles;
+// 0.15 fits the measured plans best. complex128 gates are FP64-bound alone and inside a pass
 // alike (a general 2x2 costs ~3 units either way), so only exchanges (no arithmetic, ~0.33)
 // gain from a pass.
 static double pass_gate_cost(int dtype, const GatePlan &p) {
     if (dtype == QS_C64) return 0.15;
     return p.op == OP_SWAP ? 0.33 : 3.0;
 }
+
+// Compute cost of one diagonal gate inside a k_diag_run launch (its factor is formed once per
+// chunk of 8 amplitudes, or once per warp): small against the launch's state read + write.
+static double diag_run_gate_cost(int dtype) { return dtype == QS_C64 ? 0.005 : 0.02; }
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
@@ -288,7 +304,8 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     prog->gate_src.clear();
     prog->druns.clear();
     prog->dgates.clear();
-    max_gates = std::max(1, std::min(max_gates, kTileMaxGates));
+    prog->model_cost = 0.0;
+    max_gates = std::max(1, std::min(max_gates, kPassMaxGates));
     // k >= b0 + 1 so that any single target fits next to the b0 low qubits (n permitting)
     const int b0 = dtype == QS_C64 ? 4 : 3;
     k = std::min(std::min(std::max(k, b0 + 1), kTileMaxBits), n);
@@ -296,13 +313,6 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     const uint64_t low = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
     const bool adjoint = dus != nullptr;
     const bool diag_runs = !adjoint && allow_single && n >= kDiagChunkBits;
-    // drun[j]: diagonal gates in the run of diagonal gates (identities included) starting at j
-    std::vector<int> drun(seq.size() + 1, 0);
-    if (diag_runs)
-        for (size_t j = seq.size(); j-- > 0;) {
-            const GatePlan &p = plans[seq[j]];
-            drun[j] = p.units == 0 ? drun[j + 1] : ((p.op == OP_DIAG || p.op == OP_SIDE) ? drun[j + 1] + 1 : 0);
-        }
     auto is_param = [&](int g) { return adjoint && (*dus)[g] != nullptr; };
     // Take gates seq[i], seq[i + 1], ... (before `end`) into one pass while its targets fit in
     // k local qubits and the gate and parameter limits allow; visit(j, frac, compute, real)
@@ -365,106 +375,140 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         prog->ops.push_back({(int)prog->passes.size(), -1});
         prog->passes.push_back(P);
     };
-    size_t i = 0;
-    while (i < seq.size()) {
-        if (diag_runs) {
-            // a run of diagonal gates (identities included) goes to one k_diag pass per
-            // kDiagMaxGates gates: it commutes, and a chunk's factor costs a few operations
-            size_t j = i;
-            int real = 0;
-            while (j < seq.size()) {
-                const GatePlan &p = plans[seq[j]];
-                if (p.units == 0) {
-                    ++j;
-                    continue;
+    auto is_diag = [&](int g) { return plans[g].op == OP_DIAG || plans[g].op == OP_SIDE; };
+    // Diagonal gates seq[a, b) (identities skipped) in k_diag_run launches of at most
+    // kDiagMaxGates gates; lead >= 0: that uncontrolled gate goes first in the first launch.
+    auto emit_diag = [&](size_t a, size_t b, int lead) {
+        std::vector<DiagGate> run;
+        for (size_t q = a; q < b; ++q) {
+            const GatePlan &p = plans[seq[q]];
+            if (p.units == 0) continue;
+            DiagGate dg;
+            make_diag_gate(p, &dg);
+            run.push_back(dg);
+        }
+        for (size_t q0 = 0; q0 < run.size(); q0 += kDiagMaxGates) {
+            const size_t q1 = std::min(run.size(), q0 + kDiagMaxGates);
+            DiagRun r;
+            r.begin = (int)prog->dgates.size();
+            r.count = (int)(q1 - q0);
+            const int lt = (q0 == 0 && lead >= 0) ? plans[lead].t : -1;
+            r.nc = assign_diag_classes(run.data() + q0, r.count, n, lt);
+            if (lt >= 0) std::memcpy(r.nc.lu, plans[lead].Ufull, sizeof(r.nc.lu));
+            prog->dgates.insert(prog->dgates.end(), run.begin() + q0, run.begin() + q1);
+            prog->ops.push_back({-1, -1, (int)prog->druns.size()});
+            prog->druns.push_back(r);
+        }
+    };
+    const size_t N = seq.size();
+    if (!allow_single) {  // every gate goes into a pass: each pass takes as many as fit
+        size_t i = 0;
+        while (i < N) {
+            size_t e = i;
+            double cost = 0.0;
+            extend(i, N, [&](size_t j, double frac, double compute, int) {
+                e = j;
+                cost = frac + compute;
+            });
+            emit_pass(i, e + 1);
+            prog->model_cost += cost;
+            i = e + 1;
+        }
+        return true;
+    }
+    // Least modelled cost of gates [j, N): best[j]. The first segment is [j, cut[j]) of kind
+    // kind[j]: a single launch, a tile pass, a diagonal run, or an uncontrolled gate leading a
+    // diagonal run. A pass may end wherever its targets still fit; a diagonal run of up to
+    // kDiagMaxGates gates costs one read + write of the chunks it can change (all of them with
+    // a leading gate; else those whose bits >= 3 match the controls every gate of the run
+    // shares).
+    enum { SEG_SINGLE, SEG_PASS, SEG_DIAG, SEG_LEAD_DIAG };
+    const double launch_cost = launch_latency_cost(n, dtype);
+    std::vector<double> best(N + 1, 0.0);
+    std::vector<size_t> cut(N + 1, N);
+    std::vector<char> kind(N + 1, SEG_SINGLE);
+    const uint64_t chunk_low = (1ull << kDiagChunkBits) - 1ull;
+    // fraction of the state a diagonal run over seq[a, e] changes (no leading gate)
+    auto diag_span = [&](size_t a, size_t end, bool lead, auto &&visit) {
+        uint64_t fm = ~0ull, fv = 0;
+        bool first = true;
+        int real = 0;
+        for (size_t e = a; e < end; ++e) {
+            const int g = seq[e];
+            const GatePlan &p = plans[g];
+            if (p.units != 0) {
+                if (!is_diag(g) || real >= kDiagMaxGates) break;
+                if (first) {
+                    fm = p.ctrl_mask & ~chunk_low;
+                    fv = p.ctrl_vals & fm;
+                    first = false;
+                } else {
+                    fm &= p.ctrl_mask & ~((p.ctrl_vals ^ fv) | chunk_low);
+                    fv &= fm;
                 }
-                if (p.op != OP_DIAG && p.op != OP_SIDE) break;
                 ++real;
-                ++j;
             }
-            if (real >= kDiagMinRun) {
-                std::vector<DiagGate> run;
-                for (size_t q = i; q < j; ++q) {
-                    const GatePlan &p = plans[seq[q]];
-                    if (p.units == 0) continue;
-                    DiagGate dg;
-                    make_diag_gate(p, &dg);
-                    run.push_back(dg);
-                }
-                // an uncontrolled arithmetic gate launched alone just before the run goes into the
-                // run's first pass (applied first): one read + write instead of two
-                int lead = -1;
-                if (!prog->ops.empty() && prog->ops.back().pass < 0 && prog->ops.back().drun < 0 &&
-                    n >= kDiagChunkBits + 1) {
-                    const GatePlan &lp = plans[prog->ops.back().gate];
-                    if (lp.ctrl_mask == 0 && lp.op != OP_SWAP && lp.op != OP_DIAG && lp.op != OP_SIDE) {
-                        lead = prog->ops.back().gate;
-                        prog->ops.pop_back();
-                    }
-                }
-                // the gates commute: each launch's gates are ordered by class for the kernel
-                for (size_t q0 = 0; q0 < run.size(); q0 += kDiagMaxGates) {
-                    const size_t q1 = std::min(run.size(), q0 + kDiagMaxGates);
-                    DiagRun r;
-                    r.begin = (int)prog->dgates.size();
-                    r.count = (int)(q1 - q0);
-                    const int lt = (q0 == 0 && lead >= 0) ? plans[lead].t : -1;
-                    r.nc = assign_diag_classes(run.data() + q0, r.count, n, lt);
-                    if (lt >= 0) std::memcpy(r.nc.lu, plans[lead].Ufull, sizeof(r.nc.lu));
-                    prog->dgates.insert(prog->dgates.end(), run.begin() + q0, run.begin() + q1);
-                    prog->ops.push_back({-1, -1, (int)prog->druns.size()});
-                    prog->druns.push_back(r);
-                }
-                i = j;
-                continue;
-            }
+            const double frac = lead ? 1.0 : std::ldexp(1.0, -std::min(popc(fm), kDiagMaxFixed));
+            visit(e, frac, real);
         }
-        // the gates up to the next diagonal run
-        size_t r1 = i + 1;
-        while (r1 < seq.size() && !(diag_runs && drun[r1] >= kDiagMinRun)) ++r1;
-        if (!allow_single) {  // every gate goes into a pass: each pass takes as many as fit
-            while (i < r1) {
-                size_t e = i;
-                extend(i, r1, [&](size_t j, double, double, int) { e = j; });
-                emit_pass(i, e + 1);
-                i = e + 1;
+    };
+    for (size_t j = N; j-- > 0;) {
+        const int g0 = seq[j];
+        const GatePlan &p0 = plans[g0];
+        const double alone = (p0.units == 0 && !is_param(g0)) ? 0.0 : single_launch_cost(p0, dtype) + launch_cost;
+        double bv = alone + best[j + 1];
+        size_t bc = j + 1;
+        char bk = SEG_SINGLE;
+        extend(j, N, [&](size_t e, double frac, double compute, int real) {
+            if (real < 2) return;
+            const double v = launch_cost + frac + compute + best[e + 1];
+            if (v < bv - 1e-9) {
+                bv = v;
+                bc = e + 1;
+                bk = SEG_PASS;
             }
-            continue;
-        }
-        // least modelled cost of gates [j, r1): best[j - i]; the first segment ends before
-        // cut[j - i] and is a pass if is_pass[j - i]
-        const size_t m = r1 - i;
-        std::vector<double> best(m + 1, 0.0);
-        std::vector<size_t> cut(m + 1, r1);
-        std::vector<char> is_pass(m + 1, 0);
-        for (size_t j = r1; j-- > i;) {
-            const GatePlan &p = plans[seq[j]];
-            const double alone = (p.units == 0 && !is_param(seq[j])) ? 0.0 : single_fraction(p, dtype);
-            double b = alone + best[j + 1 - i];
-            size_t c = j + 1;
-            char ps = 0;
-            extend(j, r1, [&](size_t e, double frac, double compute, int real) {
+        });
+        if (diag_runs && p0.units != 0 && is_diag(g0)) {
+            diag_span(j, N, false, [&](size_t e, double frac, int real) {
                 if (real < 2) return;
-                const double v = frac + compute + best[e + 1 - i];
-                if (v < b - 1e-9) {
-                    b = v;
-                    c = e + 1;
-                    ps = 1;
+                const double v = launch_cost + frac + real * diag_run_gate_cost(dtype) + best[e + 1];
+                if (v < bv - 1e-9) {
+                    bv = v;
+                    bc = e + 1;
+                    bk = SEG_DIAG;
                 }
             });
-            best[j - i] = b;
-            cut[j - i] = c;
-            is_pass[j - i] = ps;
         }
-        while (i < r1) {
-            const size_t c = cut[i - (r1 - m)];
-            if (is_pass[i - (r1 - m)]) {
-                emit_pass(i, c);
-            } else {
-                const int g = seq[i];
-                if (plans[g].units != 0 || is_param(g)) prog->ops.push_back({-1, g});
-            }
-            i = c;
+        if (diag_runs && n >= kDiagChunkBits + 1 && p0.units != 0 && p0.ctrl_mask == 0 && p0.op != OP_SWAP &&
+            !is_diag(g0) && j + 1 < N) {
+            diag_span(j + 1, N, true, [&](size_t e, double frac, int real) {
+                if (real < 1) return;
+                const double v = launch_cost + frac + real * diag_run_gate_cost(dtype) + best[e + 1];
+                if (v < bv - 1e-9) {
+                    bv = v;
+                    bc = e + 1;
+                    bk = SEG_LEAD_DIAG;
+                }
+            });
+        }
+        best[j] = bv;
+        cut[j] = bc;
+        kind[j] = bk;
+    }
+    prog->model_cost = best[0];
+    for (size_t i = 0; i < N; i = cut[i]) {
+        switch (kind[i]) {
+        case SEG_PASS:
+            emit_pass(i, cut[i]);
+            break;
+        case SEG_DIAG:
+            emit_diag(i, cut[i], -1);
+            break;
+        case SEG_LEAD_DIAG:
+            emit_diag(i + 1, cut[i], seq[i]);
+            break;
+        default:
+            if (plans[seq[i]].units != 0 || is_param(seq[i])) prog->ops.push_back({-1, seq[i]});
         }
     }
     return true;

@@ -27,7 +27,13 @@ struct FusedProgram {
     std::vector<int> gate_src;      // plan index each RegGate came from
     std::vector<DiagRun> druns;
     std::vector<DiagGate> dgates;   // all diagonal runs' gates
+    double model_cost = 0.0;        // planner's cost estimate (units of one state read + write)
 };
+
+// Modelled cost of launching gate p alone (fraction of the state it moves), and the fixed
+// latency of one launch on an n-qubit state, both in units of one state read + write.
+double single_launch_cost(const GatePlan &p, int dtype);
+double launch_latency_cost(int n, int dtype);
 
 // Byte size and packing of a program's device table: groups, then gates, then the diagonal
 // runs' gates (each part 16-byte aligned).
@@ -45,11 +51,10 @@ const DiagGate *table_dgates(const FusedProgram &p, const void *dev_base);
 // goes into a pass, also when the pass holds only that gate.
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates = kTileMaxGates, bool allow_single = true, int group_bits = 0);
+                int max_gates = kPassMaxGates, bool allow_single = true, int group_bits = 0);
 // group_bits: register qubits per group; 0 = kGroupBits for forward programs and
 // kGroupBitsAdjoint when dus != nullptr. The kernel that runs the program must use the same.
-// Forward programs with allow_single (not the batched kernel) also turn runs of at least
-// kDiagMinRun consecutive diagonal gates into diagonal-run ops.
-constexpr int kDiagMinRun = 4;
+// Forward programs with allow_single (not the batched kernel) may also put consecutive
+// diagonal gates, optionally after one uncontrolled gate, into diagonal-run ops.
 
 }  // namespace qs
