@@ -299,8 +299,17 @@ def measure_adjoint(qs, W, reps=3):
         out[f"max_abs_grad_err_{label}_vs_c128"] = float(np.max(np.abs(grads[label] - grads["c128_plain"])))
     out["speedup_c64_fused_vs_c128_plain"] = round(out["c128_plain"]["s_per_gradient"] /
                                                    out["c64_fused"]["s_per_gradient"], 2)
+    _reset_tile_bits(qs)
     out["workload"] = "HEA n=24, 20 layers (RY,RZ per qubit + CNOT ladder), 960 params, observable sum Z_i"
     return out
+
+
+def _reset_tile_bits(qs):
+    """Back to the library's default tile sizes, so that no measurement inherits the tile size
+    another one tuned (the autotuner applies its choice process-wide)."""
+    for dt in (qs.QS_C64, qs.QS_C128):
+        for adj in (0, 1):
+            qs.qs_set_tile_bits(dt, adj, 0)
 
 
 def measure_fused(qs, W):
@@ -324,17 +333,20 @@ def measure_fused(qs, W):
     out["scale_circuit_n30_c64"] = {"gates": 1000, "unfused_gates_per_s": round(1000 / (t_unf * 1e-3), 1),
                                     "fused_gates_per_s": round(1000 / (t_fus * 1e-3), 1),
                                     "tile_bits": tb["tile_bits"]}
+    _reset_tile_bits(qs)
     n, layers = 24, 20
     g = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
     st = qs.State(n, "c64")
     try:
         t_unf = _events_ms(lambda: st.apply_circuit(g, th), 3)
+        tb2 = autotune.tune_fused(n, "c64", g, th, adjoint=False, candidates=(12, 13), use_cache=False, reps=1)
         t_fus = _events_ms(lambda: st.apply_circuit(g, th, qs.QS_FLAG_FUSE), 3)
     finally:
         st.close()
+        _reset_tile_bits(qs)
     out["ansatz_n24_c64"] = {"gates": int(len(g)), "unfused_ms": round(t_unf, 3), "fused_ms": round(t_fus, 3),
-                             "fused_gates_per_s": round(len(g) / (t_fus * 1e-3), 1)}
+                             "fused_gates_per_s": round(len(g) / (t_fus * 1e-3), 1), "tile_bits": tb2["tile_bits"]}
     return out
 
 
@@ -392,6 +404,8 @@ def measure_paper_circuits(qs, W, reps=3):
     tile passes. Device time per circuit (CUDA events, state 4.3 GB > L2)."""
     import torch
 
+    from paper_2411_18354_gb300 import autotune
+
     n = 29
     out = {}
     st = qs.State(n, "c64")
@@ -401,9 +415,13 @@ def measure_paper_circuits(qs, W, reps=3):
                  "algorithmic_GB": round(sum(2.0 * (1 << (n - bin(int(g["ctrl_mask"])).count("1"))) * 8
                                              for g in gates) / 1e9, 3)}
             for label, flags in (("masked", qs.QS_FLAG_MASKED), ("reduced", 0), ("fused", qs.QS_FLAG_FUSE)):
+                if flags & qs.QS_FLAG_FUSE:
+                    r["fused_tile_bits"] = autotune.tune_fused(n, "c64", gates, adjoint=False, candidates=(12, 13),
+                                                               use_cache=False, reps=1)["tile_bits"]
                 st.set_basis(0)
                 ms = _events_ms(lambda: st.apply_circuit(gates, flags=flags | qs.QS_FLAG_GRAPH), reps)
                 r[f"{label}_ms"] = round(ms, 3)
+                _reset_tile_bits(qs)
             r["masked_over_reduced"] = round(r["masked_ms"] / r["reduced_ms"], 2)
             r["paper_s"] = PAPER_TIMES_S[name]
             out[name] = r
@@ -439,6 +457,7 @@ def measure_precision(qs, W):
             st.apply_circuit(gates, flags=flags)
             torch.cuda.synchronize()
             out[label] = {"s": round(time.perf_counter() - t0, 3)}
+        out["c64_fused"]["tile_bits"] = qs.qs_get_tile_bits(qs.QS_C64, 0)  # the library default
         z128, n128 = s128.expect_z()
         z64, n64 = s64.expect_z()
         err = 0.0
@@ -653,7 +672,7 @@ def run_ours(args, rank, world, local_rank):
                 states[i].apply_gate(q, W.H_MATRIX)
             qs.qs_state_copy_to_host_async(states[i].h, hnps[i])
             qs.qs_state_synchronize(states[i].h)
-        e2e_steps = 9
+        e2e_steps = 18
 
         phase_ev = []  # per timed step: events before the upload, after it, after the gates, after the download
 
