@@ -190,9 +190,11 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
                               qs_schedule *out);
 
 /* Tile size of the fused passes (QS_FLAG_FUSE) for one precision, forward (adjoint = 0) or
- * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, 5..14, or 0 for the
- * library default (complex64: 12; complex128: 11 forward, 10 adjoint). Process-wide; normally
- * set from the autotuner's cache. The QS_TILE_BITS environment variable overrides it. */
+ * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, or 0 for the
+ * library default (complex64: 12; complex128: 11 forward, 10 adjoint). Valid: 5 up to the
+ * largest tile whose block fits one SM's shared memory (complex64 14 forward / 13 adjoint,
+ * complex128 13 / 12); EINVAL otherwise. Process-wide; normally set from the autotuner's
+ * cache. The QS_TILE_BITS environment variable overrides it (capped at that largest tile). */
 qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits);
 /* The tile size the next fused call will use. */
 int qs_get_tile_bits(qs_dtype dtype, int adjoint);

@@ -85,7 +85,10 @@ struct TilePass {
 // `part` the gradient partial array [slot][part_stride] (adjoint only).
 cudaError_t launch_tile_pass(int dtype, void *psi, void *lam, const TilePass &p, const TileGroup *groups,
                              const RegGate *gates, double *part, size_t part_stride, cudaStream_t st);
+// Dynamic shared memory of one k_tile_pass block: the 2^k-amplitude tile (psi and lambda for
+// the adjoint), the adjoint's accumulators, and the pass's group and gate tables.
 size_t tile_smem_bytes(int dtype, int k, bool adjoint, int groups, int gates);
+constexpr size_t kTileMaxSmem = 227 * 1024;  // opt-in shared memory per block
 
 // Shared-memory position of local index a (XOR swizzle of the low `sw` bits with the folded
 // higher bits; sw = 4 for complex64, 3 for complex128). A bijection on [0, 2^k).

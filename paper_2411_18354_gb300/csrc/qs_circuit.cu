@@ -193,14 +193,22 @@ static qs_status launch_plans(qs_state *s, const std::vector<GatePlan> &plans, c
 // Tuned tile sizes per (dtype, adjoint), set by qs_set_tile_bits (0 = default).
 static std::atomic<int> g_tile_bits[2][2] = {{{0}, {0}}, {{0}, {0}}};
 
+// Largest tile (local qubits) whose block fits the shared memory of one SM with the longest
+// pass's gate tables: complex64 14 forward / 13 adjoint, complex128 13 / 12.
+static int max_tile_bits(int dtype, bool adjoint) {
+    int k = kTileMaxBits;
+    while (k > 5 && tile_smem_bytes(dtype, k, adjoint, kPassMaxGates, kPassMaxGates) > kTileMaxSmem) --k;
+    return k;
+}
+
 // Local qubits per tile of a fused pass (shared memory per CTA: 2^k amplitudes, twice that
-// for the adjoint's psi and lambda tiles): QS_TILE_BITS if set, else the tuned value, else
-// the default.
+// for the adjoint's psi and lambda tiles): QS_TILE_BITS if set (at most the largest tile that
+// fits), else the tuned value, else the default.
 static int tile_bits(int dtype, bool adjoint) {
     const char *env = std::getenv("QS_TILE_BITS");
     if (env && *env) {
         const int v = std::atoi(env);
-        if (v >= 2 && v <= kTileMaxBits) return v;
+        if (v >= 2 && v <= kTileMaxBits) return std::min(v, max_tile_bits(dtype, adjoint));
     }
     const int tuned = g_tile_bits[dtype == QS_C64 ? 0 : 1][adjoint ? 1 : 0].load();
     if (tuned > 0) return tuned;
@@ -278,7 +286,12 @@ extern "C" {
 
 qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits) {
     if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_set_tile_bits: bad dtype");
-    if (bits != 0 && (bits < 5 || bits > kTileMaxBits)) return set_error(QS_EINVAL, "qs_set_tile_bits: bits must be 0 or 5..14");
+    if (bits != 0 && (bits < 5 || bits > max_tile_bits(dtype, adjoint != 0))) {
+        char msg[128];
+        std::snprintf(msg, sizeof(msg), "qs_set_tile_bits: bits must be 0 or 5..%d for this precision and direction",
+                      max_tile_bits(dtype, adjoint != 0));
+        return set_error(QS_EINVAL, msg);
+    }
     g_tile_bits[dtype == QS_C64 ? 0 : 1][adjoint ? 1 : 0].store(bits);
     return QS_OK;
 }

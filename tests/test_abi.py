@@ -160,6 +160,14 @@ def test_tile_bits_setting_is_validated_on_host():
     assert qs.qs_get_tile_bits(qs.QS_C64, 1) == 9
     qs.qs_set_tile_bits(qs.QS_C64, 1, 0)
     assert qs.qs_get_tile_bits(qs.QS_C64, 1) == 12
+    # a block holds 2^bits amplitudes (twice for the adjoint's psi and lambda) and the pass's
+    # gate tables in at most 227 KB of shared memory
+    for dt, adj, largest in ((qs.QS_C64, 0, 14), (qs.QS_C64, 1, 13), (qs.QS_C128, 0, 13), (qs.QS_C128, 1, 12)):
+        qs.qs_set_tile_bits(dt, adj, largest)
+        assert qs.qs_get_tile_bits(dt, adj) == largest
+        with pytest.raises(qs.QsError):
+            qs.qs_set_tile_bits(dt, adj, largest + 1)
+        qs.qs_set_tile_bits(dt, adj, 0)
 
 
 def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
