@@ -98,7 +98,10 @@ def tune_fused(n: int, dtype: str, gates, theta=None, adjoint: bool = False, can
     results = {}
     with State(n, dtype) as st:
         for k in candidates:
-            _lib.qs_set_tile_bits(dt, int(adjoint), k)
+            try:
+                _lib.qs_set_tile_bits(dt, int(adjoint), k)
+            except _lib.QsError:  # a tile whose block does not fit this precision / direction
+                continue
             if adjoint:
                 fn = lambda: (st.set_basis(0), st.adjoint_grad(g, theta, QS_FLAG_FUSE))  # noqa: E731
             else:
