@@ -16,6 +16,12 @@
 // terms), the running sum over a block's tiles is a compensated (Kahan) float32 sum, and the
 // sum over blocks is float64. Complex128: float64 everywhere. The result does not depend on
 // scheduling (fixed tile-to-block assignment and fixed summation order).
+// Complex128 is bound by the FP64 pipe (GB300 issues about 2 FP64 operations per SM per clock),
+// so its sums are arranged for fewer operations: a thread's 16 values go through a pairwise
+// tree whose partial sums also give the four j-bit sums (26 adds instead of 48); the warp
+// forms the lane-bit sums on the way while it reduces the total (a butterfly: 15 shuffles and
+// adds instead of 25) and reduces the four j-bit sums by a transposed reduce-scatter that
+// leaves each in its own lanes (6 instead of 20).
 #include <algorithm>
 
 #include "k_gate.cuh"
@@ -59,7 +65,7 @@ k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t nt
     Acc<Real> acc{};  // output `tid` of this block, over its tiles
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         A tot = 0, sv = 0, sj[4] = {0, 0, 0, 0};
-        if (VB == 1) {
+        if constexpr (VB == 1) {
             const float4 *base = reinterpret_cast<const float4 *>(psi) + (tile << (TB - 1));
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -80,38 +86,74 @@ k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t nt
                 }
             }
         } else {
+            // complex128: |psi|^2 of the thread's 16 values, a pairwise tree, per-warp sums
             const double2 *base = reinterpret_cast<const double2 *>(psi) + (tile << TB);
+            double p[kJ];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 double2 q[kJ / 2];
 #pragma unroll
                 for (int jj = 0; jj < kJ / 2; ++jj) q[jj] = base[(h * (kJ / 2) + jj) * kRedThreads + tid];
 #pragma unroll
-                for (int jj = 0; jj < kJ / 2; ++jj) {
-                    const int j = h * (kJ / 2) + jj;
-                    const A s = (A)fma(q[jj].x, q[jj].x, q[jj].y * q[jj].y);
-                    tot += s;
-#pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if ((j >> b) & 1) sj[b] += s;
-                }
+                for (int jj = 0; jj < kJ / 2; ++jj) p[h * (kJ / 2) + jj] = fma(q[jj].x, q[jj].x, q[jj].y * q[jj].y);
             }
+            double a[8], b4[4], c2[2];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = p[2 * i] + p[2 * i + 1];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b4[i] = a[2 * i] + a[2 * i + 1];
+            c2[0] = b4[0] + b4[1];
+            c2[1] = b4[2] + b4[3];
+            double t = c2[0] + c2[1];
+            double sjt[4];  // sum over the thread's j with bit b set
+            sjt[3] = c2[1];
+            sjt[2] = b4[1] + b4[3];
+            sjt[1] = (a[1] + a[3]) + (a[5] + a[7]);
+            sjt[0] = ((p[1] + p[3]) + (p[5] + p[7])) + ((p[9] + p[11]) + (p[13] + p[15]));
+            // butterfly over the lane bits: before step b, t sums the 2^b lanes that differ from
+            // this one below bit b; the half with bit b set is this lane's t or its partner's
+            double lb[5];
+#pragma unroll
+            for (int b = 0; b < 5; ++b) {
+                const double pt = __shfl_xor_sync(0xffffffffu, t, 1 << b);
+#pragma unroll
+                for (int c = 0; c < b; ++c) lb[c] += __shfl_xor_sync(0xffffffffu, lb[c], 1 << b);
+                lb[b] = ((lane >> b) & 1) ? t : pt;
+                t += pt;
+            }
+            // j-bit sums: lanes with lane bit 4 = 0 keep sums 0, 1 and lanes with bit 4 = 1 keep
+            // 2, 3; then bit 3 splits those; bits 2..0 finish each sum. Sum q ends in the lanes
+            // with (lane >> 3) == q.
+            const bool h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1;
+            const double k0 = (h4 ? sjt[2] : sjt[0]) + __shfl_xor_sync(0xffffffffu, h4 ? sjt[0] : sjt[2], 16);
+            const double k1 = (h4 ? sjt[3] : sjt[1]) + __shfl_xor_sync(0xffffffffu, h4 ? sjt[1] : sjt[3], 16);
+            double vj = (h3 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h3 ? k0 : k1, 8);
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) vj += __shfl_xor_sync(0xffffffffu, vj, o);
+            if (lane == 0) {
+                wpart[warp][0] = (A)t;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) wpart[warp][5 + b] = (A)lb[b];
+            }
+            if ((lane & 7) == 0) wpart[warp][1 + (lane >> 3)] = (A)vj;
         }
-        // lane-bit sums before the total is reduced
-        A sl[5];
+        if constexpr (VB == 1) {
+            // lane-bit sums before the total is reduced
+            A sl[5];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) sl[b] = warp_sum<A>(((lane >> b) & 1) ? tot : (A)0);
-        tot = warp_sum<A>(tot);
-        if (VB) sv = warp_sum<A>(sv);
+            for (int b = 0; b < 5; ++b) sl[b] = warp_sum<A>(((lane >> b) & 1) ? tot : (A)0);
+            tot = warp_sum<A>(tot);
+            sv = warp_sum<A>(sv);
 #pragma unroll
-        for (int b = 0; b < 4; ++b) sj[b] = warp_sum<A>(sj[b]);
-        if (lane == 0) {
-            wpart[warp][0] = tot;
-            if (VB) wpart[warp][1] = sv;
+            for (int b = 0; b < 4; ++b) sj[b] = warp_sum<A>(sj[b]);
+            if (lane == 0) {
+                wpart[warp][0] = tot;
+                wpart[warp][1] = sv;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) wpart[warp][1 + VB + b] = sj[b];
+                for (int b = 0; b < 4; ++b) wpart[warp][1 + VB + b] = sj[b];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) wpart[warp][5 + VB + b] = sl[b];
+                for (int b = 0; b < 5; ++b) wpart[warp][5 + VB + b] = sl[b];
+            }
         }
         __syncthreads();
         if (tid <= n) {
