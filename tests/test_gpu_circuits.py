@@ -329,7 +329,7 @@ def _diag_gate(rng, n, t, ctrls, vals):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_diagonal_runs_match_oracle(qs, dtype):
-    """Fused programs turn runs of >= 4 diagonal gates into one pass (k_diag): targets and
+    """Fused programs put runs of diagonal gates into diagonal-run passes (k_diag): targets and
     controls on the lowest three qubits (inside a chunk) and above, control values 0 and 1,
     one-sided / general / identity diagonals, runs longer than one launch (64 gates), mixed
     with non-diagonal gates; n = 3..16 against the oracle."""
@@ -381,6 +381,45 @@ def test_diagonal_runs_match_oracle(qs, dtype):
                 st.apply_circuit(gates, flags=flags)
                 got = c128_of(st.to_numpy())
             assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), (n, flags)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_short_diagonal_runs_match_oracle(qs, dtype, monkeypatch):
+    """Runs of only 2 or 3 diagonal gates, after an uncontrolled gate (which can lead the run)
+    or after a doubly controlled X (which cannot): the planner gives them diagonal-run passes
+    (checked on its schedule; complex64 with 2^6-amplitude tiles, so that tile passes cannot
+    hold a block) and the result matches the oracle, n = 20."""
+    if dtype == "c64":
+        monkeypatch.setenv("QS_TILE_BITS", "6")
+    n = 20
+    rng = np.random.default_rng(77)
+    gl = []
+    for blk in range(16):
+        if blk % 2:
+            t = int(rng.integers(0, n))
+            c = sorted(int(q) for q in rng.choice([q for q in range(n) if q != t], size=2, replace=False))
+            gl.append(W.make_gate(t, None, c, kind=W.KIND_X))
+        else:
+            gl.append(W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng)))
+        for _ in range(2 + blk % 3 // 2):
+            t = int(rng.integers(0, n))
+            others = [q for q in range(n) if q != t]
+            c = int(rng.integers(0, 3))
+            ctrls = sorted(int(q) for q in rng.choice(others, size=c, replace=False)) if c else []
+            vals = [int(b) for b in rng.integers(0, 2, size=c)]
+            gl.append(_diag_gate(rng, n, t, ctrls, vals))
+    gates = W.gate_list(gl)
+    sched = qs.circuit_schedule(n, gates, dtype=dtype)
+    assert sched["diag_runs"] >= 3, sched
+    psi0 = random_state(n, dtype, 77)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates)
+    for flags in (qs.QS_FLAG_FUSE, qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH):
+        with qs.State(n, dtype) as st:
+            st.from_numpy(psi0)
+            st.apply_circuit(gates, flags=flags)
+            got = c128_of(st.to_numpy())
+        assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype] * max(1.0, np.max(np.abs(ref))), flags
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
