@@ -107,11 +107,16 @@ __global__ void k_sum_vec(const double *__restrict__ z, int n, double *__restric
 
 // slot_sum[s] = sum over blocks of part[s][b] (fixed order).
 __global__ void k_slot_sums(const double *__restrict__ part, int nslots, double *__restrict__ slot_sum) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nslots) return;
+    // a warp per slot: lane l adds blocks l, l + 32, ... (coalesced), then a fixed-order
+    // shuffle reduction
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= nslots) return;  // uniform over the warp
     double v = 0.0;
-    for (int b = 0; b < kAdjMaxBlocks; ++b) v += part[(size_t)s * kAdjMaxBlocks + b];
-    slot_sum[s] = v;
+    for (int b = lane; b < kAdjMaxBlocks; b += 32) v += part[(size_t)s * kAdjMaxBlocks + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) slot_sum[s] = v;
 }
 
 // grad[p] = 2 * sum of slot sums whose parameter is p (slots in gate order).
@@ -222,7 +227,7 @@ cudaError_t launch_sum_vec(const double *z, int n, double *out, cudaStream_t st)
 cudaError_t launch_grad_final(const double *part, int nslots, double *slot_sum, const int *slot_param,
                               double *grad, int nparams, cudaStream_t st) {
     if (nslots > 0) {
-        k_slot_sums<<<(nslots + 127) / 128, 128, 0, st>>>(part, nslots, slot_sum);
+        k_slot_sums<<<(nslots + 7) / 8, 256, 0, st>>>(part, nslots, slot_sum);  // 8 slots (warps) per block
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

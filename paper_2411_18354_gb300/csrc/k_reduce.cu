@@ -178,21 +178,26 @@ k_expz_tiles(const typename RedT<Real>::T2 *__restrict__ psi, int n, uint64_t nt
         }
         __syncthreads();
     }
-    if (tid <= n) partials[(size_t)blockIdx.x * (n + 1) + tid] = acc.value();
+    if (tid <= n) partials[(size_t)tid * gridDim.x + blockIdx.x] = acc.value();  // output-major
 }
 
-// Fixed-order sum of the per-block partials; one block.
+// Fixed-order sum of the per-block partials (output-major: partials[b * nblocks + g]); one
+// block, a warp per output: lane l adds blocks l, l + 32, ... and the warp combines its lanes
+// in a fixed shuffle order.
 __global__ void k_expz_final(const double *__restrict__ partials, int nblocks, int n,
                              double *__restrict__ out_z, double *__restrict__ out_norm2) {
-    __shared__ double tot;
-    const int b = threadIdx.x;
-    double s = 0.0;
-    if (b <= n)
-        for (int g = 0; g < nblocks; ++g) s += partials[(size_t)g * (n + 1) + b];
-    if (b == n) tot = s;
+    __shared__ double sums[kMaxQubits + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int b = warp; b <= n; b += nw) {
+        double v = 0.0;
+        for (int g = lane; g < nblocks; g += 32) v += partials[(size_t)b * nblocks + g];
+        v = warp_sum<double>(v);
+        if (lane == 0) sums[b] = v;
+    }
     __syncthreads();
-    if (b < n && out_z) out_z[b] = tot - 2.0 * s;
-    if (b == n && out_norm2) *out_norm2 = s;
+    const int b = threadIdx.x;
+    if (b < n && out_z) out_z[b] = sums[n] - 2.0 * sums[b];
+    if (b == n && out_norm2) *out_norm2 = sums[n];
 }
 
 // Small states (fewer amplitudes than one tile): one block, float64 per amplitude.
@@ -257,7 +262,7 @@ cudaError_t expect_z_impl(const void *psi, int n, double *scratch, double *out_z
     k_expz_tiles<Real><<<grid, kRedThreads, 0, st>>>(p, n, ntiles, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_expz_final<<<1, 64, 0, st>>>(scratch, grid, n, out_z, out_norm2);
+    k_expz_final<<<1, 1024, 0, st>>>(scratch, grid, n, out_z, out_norm2);
     return cudaGetLastError();
 }
 
