@@ -178,11 +178,9 @@ cudaError_t by_shape(void *psi, void *lam, const GatePlan &p, const double *dU, 
     }
     if (p.layout == LAY_SPLIT) {
         if (p.r == 0) { QS_ADJ_OPS(LAY_SPLIT, 1) }
-        else if (p.r == 1) { QS_ADJ_OPS(LAY_SPLIT, 2) }
-        else if (p.r == 2 && F) { QS_ADJ_OPS(LAY_SPLIT, (F ? 4 : 2)) }
-    } else {
-        if (p.r == 0) { QS_ADJ_OPS(LAY_ADJ, 1) }
-        else if (p.r == 1 && F) { QS_ADJ_OPS(LAY_ADJ, (F ? 2 : 1)) }
+        else if (p.r == 1 && F) { QS_ADJ_OPS(LAY_SPLIT, 2) }
+    } else if (p.r == 0) {
+        QS_ADJ_OPS(LAY_ADJ, 1)
     }
 #undef QS_ADJ_OPS
     return cudaErrorInvalidValue;

@@ -35,7 +35,8 @@ int occupancy_of(K kern) {
 
 template <typename Real, typename Idx, int NS, int LAY, int R, int OP, bool MASKED>
 cudaError_t go(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cvals, cudaStream_t st) {
-    constexpr int UNR = 2;
+    // units in flight per thread: 2 with a vector on each side, 4 with one vector per unit
+    constexpr int UNR = (LAY == LAY_ADJ || OP == OP_SIDE) ? 4 : 2;
     auto kern = k_gate<Real, Idx, NS, LAY, R, OP, MASKED, UNR>;
     static const int occ = occupancy_of(kern);
     const uint64_t per_block = (uint64_t)kGateThreads * UNR;
@@ -43,10 +44,10 @@ cudaError_t go(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cvals, cud
     const uint64_t cap = (uint64_t)device_sm_count() * (uint64_t)occ;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min(need, cap));
     using T2 = typename CxT<Real>::T;
-    // small gates (at most 16 grid-stride steps of work) start as programmatic dependents of the
-    // previous kernel, hiding their launch behind its tail; large ones launch normally (their
-    // blocks would only wait on the SMs while the previous gate drains)
-    const bool dependent = p.units <= 16ull * grid * per_block;
+    // small gates (at most 2^15 pair counters per block of the grid: c >= 4 at n = 30) start as
+    // programmatic dependents of the previous kernel, hiding their launch behind its tail; large
+    // ones launch normally (their blocks would only wait on the SMs while the previous gate drains)
+    const bool dependent = (p.units << p.r) <= (uint64_t)grid << 15;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -76,11 +77,9 @@ cudaError_t by_shape(void *psi, const GatePlan &p, uint64_t cmask, uint64_t cval
     }
     if (p.layout == LAY_SPLIT) {
         if (p.r == 0) { QS_OPS(LAY_SPLIT, 1) }
-        else if (p.r == 1) { QS_OPS(LAY_SPLIT, 2) }
-        else if (p.r == 2 && F) { QS_OPS(LAY_SPLIT, (F ? 4 : 2)) }
-    } else {
-        if (p.r == 0) { QS_OPS(LAY_ADJ, 1) }
-        else if (p.r == 1 && F) { QS_OPS(LAY_ADJ, (F ? 2 : 1)) }
+        else if (p.r == 1 && F) { QS_OPS(LAY_SPLIT, 2) }
+    } else if (p.r == 0) {
+        QS_OPS(LAY_ADJ, 1)
     }
 #undef QS_OPS
     return cudaErrorInvalidValue;
