@@ -356,6 +356,23 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
     if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
         return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
+    // CUDA graph: one per distinct (gates, theta, flags, buffer, tile size). A recorded one is
+    // launched before any validation or planning (its gates passed both when it was recorded).
+    uint64_t key = 1469598103934665603ull;
+    if (flags & QS_FLAG_GRAPH) {
+        if (count > 0) key = fnv1a(key, gates, count * sizeof(qs_gate));
+        if (theta) key = fnv1a(key, theta, n_theta * sizeof(double));
+        key = fnv1a(key, &flags, sizeof(flags));
+        key = fnv1a(key, &s->psi, sizeof(s->psi));
+        const int tb = tile_bits(s->dtype, false);
+        key = fnv1a(key, &tb, sizeof(tb));
+        for (auto &g : s->graphs)
+            if (g.key == key) {
+                cudaError_t e = cudaGraphLaunch(g.exec, s->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+                return QS_OK;
+            }
+    }
     std::vector<GatePlan> plans(count);
     char err[256];
     for (size_t i = 0; i < count; ++i)
@@ -398,18 +415,9 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         return launch_program(s, prog, plans, s->tile_table, nullptr, nullptr, nullptr, nullptr, 0, s->stream);
     }
 
-    // CUDA graph: record once per distinct (gates, theta, flags, buffer), then replay.
-    uint64_t key = 1469598103934665603ull;
-    key = fnv1a(key, gates, count * sizeof(qs_gate));
-    if (theta) key = fnv1a(key, theta, n_theta * sizeof(double));
-    key = fnv1a(key, &flags, sizeof(flags));
-    key = fnv1a(key, &s->psi, sizeof(s->psi));
-    const int tb = tile_bits(s->dtype, false);
-    key = fnv1a(key, &tb, sizeof(tb));
+    // CUDA graph not recorded yet (the lookup above missed): record it, keep it, launch it.
     cudaGraphExec_t exec = nullptr;
-    for (auto &g : s->graphs)
-        if (g.key == key) exec = g.exec;
-    if (!exec) {
+    {
         cudaError_t e;
         void *table = nullptr;
         if (table_bytes) {
