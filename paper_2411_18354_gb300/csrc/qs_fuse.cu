@@ -406,12 +406,16 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         while (i < N) {
             size_t e = i;
             double cost = 0.0;
-            extend(i, N, [&](size_t j, double frac, double compute, int) {
+            int nreal = 0;
+            extend(i, N, [&](size_t j, double frac, double compute, int real) {
                 e = j;
                 cost = frac + compute;
+                nreal = real;
             });
-            emit_pass(i, e + 1);
-            prog->model_cost += cost;
+            if (nreal > 0) {  // identity gates alone need no pass
+                emit_pass(i, e + 1);
+                prog->model_cost += cost;
+            }
             i = e + 1;
         }
         return true;
