@@ -123,3 +123,18 @@ def test_complex128_arithmetic_gates_stay_out_of_passes(qs):
     gl = [W.make_gate(int(rng.integers(0, n)), W.haar_2x2(rng), ()) for _ in range(30)]
     s = qs.circuit_schedule(n, W.gate_list(gl), dtype="c128")
     assert s["tile_passes"] == 0 and s["launches"] == s["gates"]
+
+
+def test_identity_gates_launch_nothing(qs):
+    """Exact identities (U = I, controlled or not, and RZ(0)) need no launch, fused or not; they
+    do not split a pass either."""
+    n = 16
+    gl = [W.make_gate(q, np.eye(2), ([q + 1] if q < n - 1 else [])) for q in range(n)]
+    gl.append(W.make_gate(3, None, (), kind=W.KIND_RZ, param=0))
+    th = np.zeros(1)
+    for flags in (0, qs.QS_FLAG_FUSE):
+        s = qs.circuit_schedule(n, W.gate_list(gl), th, flags=flags)
+        assert s["launches"] == 0, (flags, s)
+    mixed = [W.make_gate(0, W.H_MATRIX, ()), W.make_gate(5, np.eye(2), ()), W.make_gate(1, W.H_MATRIX, ())]
+    s = qs.circuit_schedule(20, W.gate_list(mixed))
+    assert s["launches"] == 1 and s["tile_passes"] == 1, s
