@@ -554,6 +554,18 @@ def job_value(world: int, steps: int, step_bytes: float, total_ms: float) -> flo
     return world * steps * step_bytes / (total_ms * 1e-3) / 1e9
 
 
+def sweep_config(n, world, gates_per_step):
+    """The workload keys of the headline line, shared by both arms."""
+    state_gb = (1 << n) * 8 / 1e9
+    return {"workload": f"single-gate sweep: n={n} complex64 state, Haar gates with c=0..8 controls on random "
+                        f"qubits, targets {'/'.join(str(t) for t in targets_for(n))}, 8 rotating control sets "
+                        f"({gates_per_step} gates/step)",
+            "n": n, "gates_per_step": gates_per_step, "bytes_counted": "2*2^(n-c)*8 per gate",
+            "l2": (f"inputs larger than L2 ({state_gb:.1f} GB state)" if state_gb > 0.13
+                   else f"state of {state_gb * 1e3:.1f} MB fits in L2"),
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def run_reference(args, rank, world):
     """--impl reference: the CPU oracle on the host cores, same metric/unit/config."""
     if rank != 0:
@@ -585,10 +597,10 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(vals),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"single-gate sweep n={n}, c=0..8, t=0/15/29 (one target per step)",
-                   "state": "uniform superposition", "l2": "state larger than L2"},
+        "config": sweep_config(n, world, len(sched[0])),
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"per step 9 gates (one target, c=0..8) on an n={n} float64 state"},
+                         "sample": f"per step 9 of the sweep's gates (one target, c=0..8) on an n={n} float64 "
+                                   f"state (uniform superposition), oracle loop over all 2^n indices"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -638,10 +650,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32 arithmetic)", "data": "synthetic",
-        "config": {"workload": f"single-gate sweep: n={n} complex64 state, Haar gates with c=0..8 controls on random "
-                               f"qubits, targets 0/15/29, 8 rotating control sets (27 gates/step)",
-                   "n": n, "gates_per_step": len(sched[0]), "bytes_counted": "2*2^(n-c)*8 per gate",
-                   "l2": "inputs larger than L2 (8.6 GB state)", "parallelism": "replicas" if world > 1 else "1 GPU",
+        "config": {**sweep_config(n, world, len(sched[0])),
                    "l2_fetch_bytes": qs.qs_get_l2_fetch_bytes(),
                    "per_c": "steady state: the 24 gates of each c back to back, timed as a block",
                    "sector_adjusted": f"{SECTOR_BYTES}-byte sectors holding a selected amplitude"},
