@@ -138,3 +138,15 @@ def test_identity_gates_launch_nothing(qs):
     mixed = [W.make_gate(0, W.H_MATRIX, ()), W.make_gate(5, np.eye(2), ()), W.make_gate(1, W.H_MATRIX, ())]
     s = qs.circuit_schedule(20, W.gate_list(mixed))
     assert s["launches"] == 1 and s["tile_passes"] == 1, s
+
+
+def test_schedule_validates_theta(qs):
+    """Parameter indices past theta and non-finite angles are rejected as by qs_apply_circuit;
+    RY(0) is an exact identity and needs no launch."""
+    g = W.gate_list([W.make_gate(0, None, (), kind=W.KIND_RY, param=3)])
+    with pytest.raises(qs.QsError):
+        qs.circuit_schedule(4, g, np.zeros(2))
+    with pytest.raises(qs.QsError):
+        qs.circuit_schedule(4, g, np.array([0.0, 0.0, 0.0, np.nan]))
+    assert qs.circuit_schedule(4, g, np.zeros(4))["launches"] == 0
+    assert qs.circuit_schedule(4, g, np.full(4, 0.3))["launches"] == 1
