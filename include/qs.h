@@ -157,7 +157,10 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
  * consecutive gates whose targets fit in one shared-memory tile in one HBM round trip (a tile
  * pass; controls outside the tile select the tiles a gate changes) and runs of diagonal
  * gates in one pass each, as qs_circuit_schedule plans them; QS_FLAG_GRAPH records the
- * launches into a CUDA graph and launches it.
+ * launches into a CUDA graph and launches it. Each state keeps up to 16 recorded graphs; a
+ * call whose gate records, theta, flags, state buffer and tile size equal a recorded graph's
+ * byte for byte replays it without validating or planning again (the hash that finds the
+ * candidate is always confirmed by comparing the stored bytes).
  * QS_FLAG_MASKED runs every gate with the baseline schedule of Section III-A instead (all
  * 2^(n-1) pair iterations, controls tested per pair, the general 2x2 update), the
  * comparator of qs_apply_gate_masked for whole circuits; QS_EINVAL with QS_FLAG_FUSE. */
@@ -230,13 +233,16 @@ qs_status qs_expect_z(const qs_state *s, double *out, double *out_norm2, int fla
  * no counterpart; this is an interface addition.)
  *  - psi: device pointer to 2^n amplitudes of `dtype` (16-byte aligned), read only.
  *  - out_z (n doubles) / out_norm2 (1 double): device pointers, either may be NULL (not both).
+ *  - psi, out_z and out_norm2 must be device (or managed) memory of the current device:
+ *    host memory or another device's memory is rejected with QS_EINVAL before any launch.
  *  - Enqueued on `stream`; returns without waiting.
  *  - The per-block partial sums go to one fixed device array inside the library
  *    (1024 * 41 doubles = 335,872 bytes per device, held until the process exits), which
  *    covers every n <= 40; larger requests are rejected with QS_EINVAL.
  *  - The first call on a device looks up that array's device address (a runtime query,
  *    done once per device with the device current); make that first call before any
- *    stream capture.
+ *    stream capture. The address is kept for the life of the process: after a
+ *    cudaDeviceReset of that device, do not call this entry point again in the process.
  *  - All calls on a device share the array. Calls that may run at the same time on the GPU
  *    (other streams, other host threads) overwrite each other's partial sums: serialise
  *    them. Nothing needs clearing between calls: each call writes every slot it reads. */

@@ -121,6 +121,37 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
     return h;
 }
 
+static int tile_bits(int dtype, bool adjoint);
+
+// The bytes a recorded graph depends on: the gate records, the parameters, the flags, the
+// state buffer and the tile size, each run preceded by its length so that different splits
+// of the same bytes differ.
+static void graph_key_bytes(const qs_state *s, const qs_gate *gates, size_t count, const double *theta,
+                            size_t n_theta, int flags, std::vector<unsigned char> *out) {
+    const int tb = tile_bits(s->dtype, false);
+    const uint64_t nt = theta ? (uint64_t)n_theta : 0, ng = (uint64_t)count;
+    out->clear();
+    auto put = [out](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        out->insert(out->end(), b, b + n);
+    };
+    put(&ng, sizeof(ng));
+    if (count > 0) put(gates, count * sizeof(qs_gate));
+    put(&nt, sizeof(nt));
+    if (nt > 0) put(theta, n_theta * sizeof(double));
+    put(&flags, sizeof(flags));
+    put(&s->psi, sizeof(s->psi));
+    put(&tb, sizeof(tb));
+}
+
+// FNV-1a over the key bytes. QS_TEST_GRAPH_KEY (a test hook) replaces the hash with a fixed
+// value so that a test can make different circuits collide on it.
+static uint64_t graph_key_hash(const std::vector<unsigned char> &bytes) {
+    const char *forced = std::getenv("QS_TEST_GRAPH_KEY");
+    if (forced && *forced) return std::strtoull(forced, nullptr, 0);
+    return fnv1a(1469598103934665603ull, bytes.data(), bytes.size());
+}
+
 // Forward application only: runs of consecutive gates with the same target and the same
 // controls act on the same pairs, so their product (U_last ... U_first, formed in double
 // precision) replaces them; e.g. RY then RZ on one qubit become one launch or one tile-pass
@@ -357,17 +388,15 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
         return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
     // CUDA graph: one per distinct (gates, theta, flags, buffer, tile size). A recorded one is
-    // launched before any validation or planning (its gates passed both when it was recorded).
-    uint64_t key = 1469598103934665603ull;
+    // launched before any validation or planning (its gates passed both when it was recorded):
+    // the hash picks the candidate, the stored key bytes must then match exactly.
+    std::vector<unsigned char> key_bytes;
+    uint64_t key = 0;
     if (flags & QS_FLAG_GRAPH) {
-        if (count > 0) key = fnv1a(key, gates, count * sizeof(qs_gate));
-        if (theta) key = fnv1a(key, theta, n_theta * sizeof(double));
-        key = fnv1a(key, &flags, sizeof(flags));
-        key = fnv1a(key, &s->psi, sizeof(s->psi));
-        const int tb = tile_bits(s->dtype, false);
-        key = fnv1a(key, &tb, sizeof(tb));
+        graph_key_bytes(s, gates, count, theta, n_theta, flags, &key_bytes);
+        key = graph_key_hash(key_bytes);
         for (auto &g : s->graphs)
-            if (g.key == key) {
+            if (g.key == key && g.bytes == key_bytes) {
                 cudaError_t e = cudaGraphLaunch(g.exec, s->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
                 return QS_OK;
@@ -466,7 +495,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
             if (s->graphs.front().table) cudaFree(s->graphs.front().table);
             s->graphs.erase(s->graphs.begin());
         }
-        s->graphs.push_back({key, exec, table});
+        s->graphs.push_back({key, std::move(key_bytes), exec, table});
     }
     cudaError_t e = cudaGraphLaunch(exec, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");

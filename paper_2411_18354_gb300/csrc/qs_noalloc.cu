@@ -20,6 +20,11 @@
 // cleared between calls. Calls that can overlap on the GPU (different streams, or the same
 // array used from several host threads on different streams) race on the array and give
 // wrong results: serialise them.
+//
+// The looked-up address belongs to the device's current CUDA context. A cudaDeviceReset
+// destroys that context (and the array with it); the cached address is not looked up again,
+// so after a reset this entry point must not be called again in the same process.
+#include <cstdio>
 #include <mutex>
 
 #include "qs_internal.cuh"
@@ -59,6 +64,29 @@ qs_status scratch_for_current_device(double **out) {
     return QS_OK;
 }
 
+// The kernels read `p` (or write it) from the current device: it must be device memory (or
+// managed memory) of that device. A host pointer, or memory of another device, would make the
+// kernels fault instead of failing cleanly, so both are rejected before anything is launched.
+// cudaPointerGetAttributes is a host-side query; it allocates nothing.
+qs_status check_device_pointer(const void *p, int dev, const char *what) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char msg[160];
+        std::snprintf(msg, sizeof(msg), "qs_expect_z_noalloc: %s is not a pointer the CUDA runtime knows", what);
+        return set_error(QS_EINVAL, msg);
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != dev) {
+        char msg[200];
+        std::snprintf(msg, sizeof(msg),
+                      "qs_expect_z_noalloc: %s must be device (or managed) memory of the current device %d", what,
+                      dev);
+        return set_error(QS_EINVAL, msg);
+    }
+    return QS_OK;
+}
+
 }  // namespace
 
 extern "C" qs_status qs_expect_z_noalloc(const void *psi, int n, qs_dtype dtype, void *stream, double *out_z,
@@ -71,8 +99,15 @@ extern "C" qs_status qs_expect_z_noalloc(const void *psi, int n, qs_dtype dtype,
     if (reduce_scratch_doubles(n) > kNoAllocScratchDoubles)
         return set_error(QS_EINVAL, "qs_expect_z_noalloc: the partial sums for this n do not fit the fixed "
                                     "scratch array of 1024 * 41 doubles");
+    int dev = 0;
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return cuda_fail(ge, "qs_expect_z_noalloc: cudaGetDevice");
+    qs_status st = check_device_pointer(psi, dev, "psi");
+    if (st == QS_OK && out_z) st = check_device_pointer(out_z, dev, "out_z");
+    if (st == QS_OK && out_norm2) st = check_device_pointer(out_norm2, dev, "out_norm2");
+    if (st != QS_OK) return st;
     double *scratch = nullptr;
-    qs_status st = scratch_for_current_device(&scratch);
+    st = scratch_for_current_device(&scratch);
     if (st != QS_OK) return st;
     cudaError_t e = launch_expect_z(dtype, psi, n, scratch, out_z, out_norm2, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "qs_expect_z_noalloc launch");

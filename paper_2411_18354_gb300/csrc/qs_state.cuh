@@ -13,7 +13,8 @@ namespace qs {
 constexpr uint32_t kStateMagic = 0x51535354u;  // "QSST"
 
 struct GraphCacheEntry {
-    uint64_t key;
+    uint64_t key;                 // hash of `bytes` (the lookup key)
+    std::vector<unsigned char> bytes;  // everything the key hashes, compared on a hash hit
     cudaGraphExec_t exec;
     void *table;  // device gate table of the fused passes recorded in the graph (or null)
 };

@@ -110,3 +110,31 @@ def test_parameterised_gates_in_every_schedule(qs, dtype):
             st.apply_circuit(gates, th, flags)
             got = c128_of(st.to_numpy())
         assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype], flags
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_graph_cache_key_collision(qs, dtype, monkeypatch):
+    """QS_TEST_GRAPH_KEY forces every recorded graph onto one hash value: a second circuit
+    whose hash collides with a recorded one must not replay that graph but be validated,
+    planned and recorded itself (the cache compares the stored key bytes). Then both
+    circuits are replayed again; every result against the oracle. A circuit that differs
+    only in theta, or only in its gate count (a prefix), collides the same way."""
+    monkeypatch.setenv("QS_TEST_GRAPH_KEY", "0x5eed")
+    n = 11
+    a = W.random_circuit(n, 40, 3, seed=901)
+    b = W.random_circuit(n, 40, 3, seed=902)
+    prefix = a[:25]
+    rng = np.random.default_rng(903)
+    rot = W.gate_list([W.make_gate(q, None, (), kind=W.KIND_RY, param=q) for q in range(n)])
+    th1 = rng.uniform(0, 6.3, size=n)
+    th2 = th1.copy()
+    th2[3] += 0.5
+    for flags in (qs.QS_FLAG_GRAPH, qs.QS_FLAG_GRAPH | qs.QS_FLAG_FUSE):
+        ref = W.basis_state(n, 0)
+        with qs.State(n, dtype) as st:
+            for gates, th in ((a, None), (b, None), (prefix, None), (rot, th1), (rot, th2), (a, None), (b, None),
+                              (rot, th1)):
+                st.apply_circuit(gates, th, flags=flags)
+                oracle.run_circuit(ref, n, gates, th)
+                got = c128_of(st.to_numpy())
+                assert np.max(np.abs(got - ref)) <= 4 * ATOL_CIRCUIT[dtype], flags

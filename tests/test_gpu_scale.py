@@ -1,0 +1,110 @@
+"""Whole-vector parity of the 1000-gate random circuit at its full size (n = 30).
+
+The workload: a 30-qubit state, 1000 Haar-random 2x2 gates on uniformly random targets with
+0-8 controls on |1> drawn from the other qubits (seed 1), as in the scale-circuit recipe.
+The start state is a product state with distinct amplitudes (RY(alpha_q) then RZ(beta_q) on
+every qubit from |0...0>), prepared by the same gate records on both sides. The oracle applies
+all 1060 gates to a complex128 vector on the host (17.2 GB, Eq. 2 per selected pair); the GPU
+runs complex64 and complex128, one launch per gate and fused, and the whole output vector is
+compared chunk by chunk on the device.
+
+Bounds: the stated targets (complex64 max-abs <= 3e-5 and norm drift <= 1e-5; complex128
+max-abs <= 1e-12), and because the amplitudes of a 30-qubit state are only ~3e-5 in size, a
+bound on the 2-norm of the error vector as well: one update rounds each output to within
+~8u(|x| + |y|), so a unitary gate adds at most ~11u to the error norm and 1060 gates at most
+~1.2e4 u (complex64 7e-4, complex128 1.3e-12; a random walk gives far less)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import rotations
+
+pytestmark = pytest.mark.gpu
+
+N = 30
+ERR_NORM = {"c64": 1e-3, "c128": 2e-12}
+MAX_ABS = {"c64": 3e-5, "c128": 1e-12}
+NORM_DRIFT = {"c64": 1e-5, "c128": 1e-12}
+
+
+def _mem_available_gb() -> float:
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except OSError:
+        pass
+    return 0.0
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import paper_2411_18354_gb300 as q
+
+    q.build()
+    return q
+
+
+@pytest.fixture(scope="module")
+def scale_case():
+    # the oracle's complex128 vector plus the chunked comparison need ~20 GB of host memory
+    if _mem_available_gb() < 40.0:
+        pytest.skip("fewer than 40 GB of host memory available for the 17.2 GB oracle state")
+    al, be = rotations(N, 3001)
+    prefix = []
+    for q in range(N):
+        prefix.append(W.make_gate(q, oracle.ry(al[q])))
+        prefix.append(W.make_gate(q, oracle.rz(be[q])))
+    prefix = W.gate_list(prefix)
+    gates = W.scale_circuit(N, 1000, seed=1)
+    ref = np.zeros(1 << N, dtype=np.complex128)
+    ref[0] = 1.0
+    oracle.run_circuit(ref, N, prefix)
+    oracle.run_circuit(ref, N, gates)
+    yield prefix, gates, ref
+    del ref
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("fuse", [False, True])
+def test_scale_circuit_n30_whole_vector(qs, scale_case, dtype, fuse):
+    import torch
+
+    prefix, gates, ref = scale_case
+    flags = qs.QS_FLAG_FUSE if fuse else 0
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    buf = torch.empty(1 << N, dtype=tdt, device="cuda")
+    st = qs.State.wrap(buf, N)
+    try:
+        st.set_basis(0)
+        st.apply_circuit(prefix, flags=flags)
+        st.apply_circuit(gates, flags=flags)
+        z, nrm = st.expect_z()
+        torch.cuda.synchronize()
+        max_abs = 0.0
+        err2 = 0.0
+        ref_max = 0.0
+        chunk = 1 << 26
+        for i in range(0, 1 << N, chunk):
+            r = torch.from_numpy(ref[i:i + chunk]).cuda()
+            d = buf[i:i + chunk].to(torch.complex128) - r
+            max_abs = max(max_abs, float(d.abs().max()))
+            err2 += float((d.abs() ** 2).sum())
+            ref_max = max(ref_max, float(r.abs().max()))
+            del r, d
+        err_norm = float(np.sqrt(err2))
+        print(f"n=30 {dtype} fuse={fuse}: max-abs {max_abs:.3e} (max |amp| {ref_max:.3e}), "
+              f"error norm {err_norm:.3e}, norm drift {abs(nrm - 1.0):.3e}")
+        assert max_abs <= MAX_ABS[dtype], max_abs
+        assert err_norm <= ERR_NORM[dtype], err_norm
+        assert abs(nrm - 1.0) <= NORM_DRIFT[dtype], nrm
+        # <Z_i> of the result against the oracle's vector (each within the error norm's reach)
+        zr = oracle.expect_z(ref, N) if dtype == "c128" and not fuse else None
+        if zr is not None:
+            assert np.max(np.abs(np.asarray(z) - zr)) <= 2.0 * err_norm + 1e-12
+    finally:
+        st.close()
+        del buf
+        torch.cuda.empty_cache()

@@ -62,3 +62,21 @@ def test_noalloc_rejects_bad_arguments(qs):
     assert "out of range" in str(e.value)
     with pytest.raises(qs.QsError):
         qs.qs_expect_z_noalloc(d.data_ptr(), 2, qs.QS_C64, 0, 0, 0)  # no output
+    # host buffers are rejected on the host, before any launch (a kernel given one would fault)
+    host_out = np.zeros(4, dtype=np.float64)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_expect_z_noalloc(d.data_ptr(), 2, qs.QS_C64, 0, host_out.ctypes.data, 0)
+    assert "device" in str(e.value)
+    host_psi = np.zeros(8, dtype=np.complex64)
+    with pytest.raises(qs.QsError):
+        qs.qs_expect_z_noalloc(host_psi.ctypes.data, 3, qs.QS_C64, 0, d.data_ptr(), 0)
+    pinned = torch.zeros(4, dtype=torch.float64).pin_memory()
+    with pytest.raises(qs.QsError):
+        qs.qs_expect_z_noalloc(d.data_ptr(), 2, qs.QS_C64, 0, 0, pinned.data_ptr())
+    # the entry point still works after the rejections
+    z = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    psi = torch.zeros(4, dtype=torch.complex64, device="cuda")
+    psi[0] = 1.0
+    qs.qs_expect_z_noalloc(psi.data_ptr(), 2, qs.QS_C64, torch.cuda.current_stream().cuda_stream, z.data_ptr(), 0)
+    torch.cuda.synchronize()
+    assert z.cpu().tolist() == [1.0, 1.0]
