@@ -865,13 +865,17 @@ def run_tile_costs(args):
     out = {}
     with qs.State(n, "c64") as st:
         st.apply_gate(0, W.H_MATRIX)
-        for kind in ("real", "diagonal", "general", "exchange", "cnot_in_row", "controlled_general_in_row"):
-            t = {}
-            for cnt in (1, 16, 64):
-                g = circ(kind, cnt)
-                t[cnt] = _events_ms(lambda: st.apply_circuit(g, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH), 10)
-            out[kind] = {"pass_us": {str(k): round(v * 1e3, 1) for k, v in t.items()},
-                         "us_per_gate": round((t[64] - t[16]) / 48 * 1e3, 2)}
+        for label, extra in (("interpreted", 0), ("compiled", qs.QS_FLAG_JIT)):
+            res = {}
+            for kind in ("real", "diagonal", "general", "exchange", "cnot_in_row", "controlled_general_in_row"):
+                t = {}
+                for cnt in (1, 16, 64):
+                    g = circ(kind, cnt)
+                    fl = qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH | extra
+                    t[cnt] = _events_ms(lambda: st.apply_circuit(g, flags=fl), 10)
+                res[kind] = {"pass_us": {str(k): round(v * 1e3, 1) for k, v in t.items()},
+                             "us_per_gate": round((t[64] - t[16]) / 48 * 1e3, 2)}
+            out[label] = res
     print(json.dumps({"tile_costs_n24_c64": out}), flush=True)
 
 

@@ -63,7 +63,9 @@ enum {
     QS_FLAG_FUSE = 1,        /* group runs of low-target gates into one tile pass      */
     QS_FLAG_GRAPH = 2,       /* launch the whole sequence as one CUDA graph            */
     QS_FLAG_OUT_DEVICE = 4,  /* energy / grad / expectation outputs are device pointers */
-    QS_FLAG_MASKED = 8       /* qs_apply_circuit: baseline schedule (comparator only)   */
+    QS_FLAG_MASKED = 8,      /* qs_apply_circuit: baseline schedule (comparator only)   */
+    QS_FLAG_JIT = 16         /* with QS_FLAG_FUSE: tile passes as kernels compiled for
+                                their exact shape (see qs_circuit_compile)             */
 };
 
 /* One gate (96 bytes, naturally aligned). Section III-A: target t, controls, matrix. */
@@ -191,6 +193,23 @@ typedef struct {
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
                               const double *theta, size_t n_theta, int flags,
                               qs_schedule *out);
+
+/* Compile the tile-pass kernels that qs_apply_circuit (adjoint = 0) or qs_adjoint_grad
+ * (adjoint = 1: the forward and the reverse-sweep programs) would launch for these gates with
+ * QS_FLAG_FUSE | QS_FLAG_JIT, without running anything; needs no device or state.
+ * With QS_FLAG_JIT a fused pass is not interpreted gate by gate: the library writes the CUDA
+ * source of one kernel for the pass's exact shape (its tile map, register groups, and every
+ * gate's operation, target and controls as constants; the matrices stay kernel parameters),
+ * compiles it for sm_103a with NVRTC and caches it for the life of the process by its source
+ * text. Circuits with the same structure (e.g. the layers of a parameterised ansatz at other
+ * angles) reuse the compiled kernels; the first call that needs a new shape compiles it,
+ * which takes a fraction of a second to seconds. This call moves that cost out of the timed
+ * or latency-critical path. *compile_seconds (may be NULL) receives the compile time of this
+ * call (0 when everything was cached), *passes (may be NULL) the number of tile passes.
+ * QS_EINVAL for invalid gates (as qs_apply_circuit), QS_ECUDA if compilation fails. */
+qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
+                             const double *theta, size_t n_theta, int flags, int adjoint,
+                             double *compile_seconds, int *passes);
 
 /* Tile size of the fused passes (QS_FLAG_FUSE) for one precision, forward (adjoint = 0) or
  * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, or 0 for the

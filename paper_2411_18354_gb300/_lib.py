@@ -17,7 +17,7 @@ from .build import LIB_PATH
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
 QS_GATE_U, QS_GATE_X, QS_GATE_RY, QS_GATE_RZ = 0, 1, 2, 3
-QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED = 1, 2, 4, 8
+QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED, QS_FLAG_JIT = 1, 2, 4, 8, 16
 
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EUNSUPPORTED"}
 
@@ -55,6 +55,8 @@ _SIGNATURES = [
     ("qs_apply_circuit", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, ctypes.c_int]),
     ("qs_circuit_schedule", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
                                            ctypes.c_int, _vp]),
+    ("qs_circuit_compile", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
+                                          ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]),
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
     ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
@@ -235,6 +237,19 @@ def qs_circuit_schedule(n: int, dtype: int, gates, theta=None, flags: int = 0) -
     out = QsSchedule()
     _check(lib().qs_circuit_schedule(n, dtype, gp, g.size, tp, nt, flags, _vp(ctypes.addressof(out))))
     return {name: getattr(out, name) for name, _ in QsSchedule._fields_}
+
+
+def qs_circuit_compile(n: int, dtype: int, gates, theta=None, flags: int = QS_FLAG_FUSE | QS_FLAG_JIT,
+                       adjoint: bool = False) -> dict:
+    """Compile the shape-specialised tile-pass kernels of a fused circuit (or of its gradient's
+    forward and sweep programs) without running them; no device needed."""
+    g, gp = _gates_arg(gates)
+    t, tp, nt = _theta_arg(theta)
+    secs = ctypes.c_double(0.0)
+    passes = ctypes.c_int(0)
+    _check(lib().qs_circuit_compile(n, dtype, gp, g.size, tp, nt, flags, 1 if adjoint else 0, ctypes.byref(secs),
+                                    ctypes.byref(passes)))
+    return {"compile_seconds": secs.value, "passes": passes.value}
 
 
 def qs_expect_z(h: int, flags: int = 0, out=None, out_norm2=None):

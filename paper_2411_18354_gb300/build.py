@@ -71,7 +71,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     with cf.ThreadPoolExecutor(workers) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
     tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+    # NVRTC compiles the shape-specialised tile passes at run time (QS_FLAG_JIT)
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker", f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

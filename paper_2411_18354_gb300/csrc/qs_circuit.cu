@@ -11,6 +11,7 @@
 
 #include "qs_fuse.cuh"
 #include "qs_internal.cuh"
+#include "qs_jit.cuh"
 #include "qs_state.cuh"
 
 namespace qs {
@@ -270,7 +271,8 @@ static qs_status ensure_device(void **buf, size_t *cap, size_t bytes, cudaStream
 // kernel with dus[g] / part + slot * P, passes use the adjoint tile kernel.
 static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std::vector<GatePlan> &plans,
                                 const void *dev_table, void *lam, const std::vector<const double *> *dus,
-                                const std::vector<int> *slots, double *part, size_t P, cudaStream_t st) {
+                                const std::vector<int> *slots, double *part, size_t P, cudaStream_t st,
+                                const std::vector<JitPass> *jit = nullptr) {
     const TileGroup *groups = dev_table ? table_groups(prog, dev_table) : nullptr;
     const RegGate *gates = dev_table ? table_gates(prog, dev_table) : nullptr;
     const DiagGate *dgates = dev_table ? table_dgates(prog, dev_table) : nullptr;
@@ -283,6 +285,8 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
         if (op.drun >= 0) {
             const DiagRun &r = prog.druns[op.drun];
             e = launch_diag_run(s->dtype, s->psi, s->n, dgates + r.begin, r.count, r.nc, st);
+        } else if (op.pass >= 0 && jit) {
+            e = launch_jit_pass(s->dtype, (*jit)[op.pass], prog, op.pass, s->psi, lam, part, P, st);
         } else if (op.pass >= 0) {
             e = launch_tile_pass(s->dtype, s->psi, lam, prog.passes[op.pass], groups, gates, part, P, st);
         } else if (!lam) {
@@ -307,6 +311,80 @@ static qs_status launch_program(qs_state *s, const FusedProgram &prog, const std
         }
     }
     return QS_OK;
+}
+
+// Plans of one gradient: the forward gates (same-target runs merged), the sweep's gates
+// (U^dagger, and dU/dtheta for parameterised ones with their gradient slots) and, with
+// QS_FLAG_FUSE, the fused forward and sweep programs.
+struct AdjPlan {
+    std::vector<GatePlan> fwd, adj;
+    std::vector<int> slot_of, slot_param;
+    std::vector<double> dus;  // 8 doubles per slot
+    std::vector<const double *> dusp;
+    FusedProgram pf, pa;
+};
+
+static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
+                         int flags, AdjPlan *ap, char *err, size_t errlen) {
+    std::vector<GatePlan> &fwd = ap->fwd, &adj = ap->adj;
+    fwd.assign(count, GatePlan{});
+    adj.assign(count, GatePlan{});
+    ap->slot_of.assign(count, -1);
+    std::vector<int> &slot_of = ap->slot_of, &slot_param = ap->slot_param;
+    std::vector<double> &dus = ap->dus;
+    slot_param.clear();
+    dus.clear();
+    char e2[200];
+    for (size_t i = 0; i < count; ++i) {
+        const qs_gate &g = gates[i];
+        if (!plan_record(s, g, theta, n_theta, i, &fwd[i], err, errlen)) return false;
+        double U[8], Ud[8];
+        int force = -1;
+        if (g.kind == QS_GATE_X) {
+            force = OP_SWAP;
+            std::memset(Ud, 0, sizeof(Ud));
+            Ud[2] = 1.0;
+            Ud[4] = 1.0;
+        } else {
+            if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) rot_matrix(g.kind, theta[g.param], U);
+            else std::memcpy(U, g.U, sizeof(U));
+            dagger(U, Ud);
+            if (g.kind == QS_GATE_RY) force = OP_REAL;
+            else if (g.kind == QS_GATE_RZ) force = OP_DIAG;
+        }
+        if (!plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, force, &adj[i], e2,
+                       sizeof(e2))) {
+            std::snprintf(err, errlen, "%s", e2);
+            return false;
+        }
+        if (adj[i].op == OP_SIDE) {  // the sweep kernels scale both sides
+            GatePlan q;
+            plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, OP_DIAG, &q, e2, sizeof(e2));
+            adj[i] = q;
+        }
+        if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) {
+            slot_of[i] = (int)slot_param.size();
+            slot_param.push_back(g.param);
+            double D[8];
+            rot_derivative(g.kind, theta[g.param], D);
+            dus.insert(dus.end(), D, D + 8);
+        }
+    }
+    const bool fuse = (flags & QS_FLAG_FUSE) != 0;
+    ap->dusp.assign(count, nullptr);
+    merge_runs(s, fwd);  // the forward pass needs no per-gate state
+    if (fuse) {
+        std::vector<int> seq(fwd.size());
+        for (size_t i = 0; i < fwd.size(); ++i) seq[i] = (int)i;
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &ap->pf);
+        seq.resize(count);
+        for (size_t i = 0; i < count; ++i) {
+            seq[i] = (int)(count - 1 - i);
+            if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
+        }
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &ap->dusp, &slot_of, &ap->pa);
+    }
+    return true;
 }
 
 }  // namespace qs
@@ -335,7 +413,7 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
     if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_circuit_schedule: bad dtype");
     if (n < 1 || n > kMaxQubits) return set_error(QS_EINVAL, "qs_circuit_schedule: n out of range");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_circuit_schedule: gates is NULL");
-    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED))
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED | QS_FLAG_JIT))
         return set_error(QS_EINVAL, "qs_circuit_schedule: unknown flags");
     if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
         return set_error(QS_EINVAL, "qs_circuit_schedule: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
@@ -379,14 +457,68 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
     return QS_OK;
 }
 
+qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t count, const double *theta,
+                             size_t n_theta, int flags, int adjoint, double *compile_seconds, int *passes) {
+    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_circuit_compile: bad dtype");
+    if (n < 1 || n > kMaxQubits) return set_error(QS_EINVAL, "qs_circuit_compile: n out of range");
+    if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_circuit_compile: gates is NULL");
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_JIT | QS_FLAG_OUT_DEVICE))
+        return set_error(QS_EINVAL, "qs_circuit_compile: unknown flags");
+    qs_state shape;  // planning reads only the state's size and precision
+    shape.n = n;
+    shape.dtype = dtype;
+    std::vector<const FusedProgram *> progs;
+    std::vector<bool> adj_of;
+    char err[256];
+    std::vector<GatePlan> plans;
+    FusedProgram prog;
+    AdjPlan ap;
+    const int fl = flags | QS_FLAG_FUSE;
+    if (!adjoint) {
+        plans.resize(count);
+        for (size_t i = 0; i < count; ++i)
+            if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
+                return set_error(QS_EINVAL, err);
+        merge_runs(&shape, plans);
+        std::vector<int> seq(plans.size());
+        for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
+        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog);
+        progs.push_back(&prog);
+        adj_of.push_back(false);
+    } else {
+        if (!plan_adjoint(&shape, gates, count, theta, n_theta, fl, &ap, err, sizeof(err)))
+            return set_error(QS_EINVAL, err);
+        progs.push_back(&ap.pf);
+        adj_of.push_back(false);
+        progs.push_back(&ap.pa);
+        adj_of.push_back(true);
+    }
+    double secs = 0.0;
+    int np = 0;
+    for (size_t i = 0; i < progs.size(); ++i) {
+        std::vector<JitPass> jit;
+        std::string jerr;
+        double t = 0.0;
+        if (!jit_prepare_program(dtype, adj_of[i], *progs[i], &jit, &jerr, &t))
+            return set_error(QS_ECUDA, ("qs_circuit_compile: " + jerr).c_str());
+        secs += t;
+        np += (int)progs[i]->passes.size();
+    }
+    if (compile_seconds) *compile_seconds = secs;
+    if (passes) *passes = np;
+    return QS_OK;
+}
+
 qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
                            int flags) {
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_apply_circuit: gates is NULL");
-    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED))
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED | QS_FLAG_JIT))
         return set_error(QS_EINVAL, "qs_apply_circuit: unknown flags");
     if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
         return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
+    if ((flags & QS_FLAG_JIT) && !(flags & QS_FLAG_FUSE))
+        return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_JIT needs QS_FLAG_FUSE");
     // CUDA graph: one per distinct (gates, theta, flags, buffer, tile size). A recorded one is
     // launched before any validation or planning (its gates passed both when it was recorded):
     // the hash picks the candidate, the stored key bytes must then match exactly.
@@ -426,6 +558,13 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
         plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog);
     }
+    std::vector<JitPass> jit;
+    if (flags & QS_FLAG_JIT) {
+        std::string jerr;
+        if (!jit_prepare_program(s->dtype, false, prog, &jit, &jerr))
+            return set_error(QS_ECUDA, ("qs_apply_circuit: " + jerr).c_str());
+    }
+    const std::vector<JitPass> *jp = (flags & QS_FLAG_JIT) ? &jit : nullptr;
     const size_t table_bytes = fuse ? program_table_bytes(prog) : 0;
     std::vector<char> table_host(table_bytes);
     if (table_bytes) pack_program_table(prog, table_host.data());
@@ -441,7 +580,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
                                             s->stream);
             if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit: gate table upload");
         }
-        return launch_program(s, prog, plans, s->tile_table, nullptr, nullptr, nullptr, nullptr, 0, s->stream);
+        return launch_program(s, prog, plans, s->tile_table, nullptr, nullptr, nullptr, nullptr, 0, s->stream, jp);
     }
 
     // CUDA graph not recorded yet (the lookup above missed): record it, keep it, launch it.
@@ -474,7 +613,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
             return cuda_fail(e, "cudaStreamBeginCapture");
         }
         qs_status st = fuse ? launch_program(s, prog, plans, table, nullptr, nullptr, nullptr, nullptr, 0,
-                                             s->capture_stream)
+                                             s->capture_stream, jp)
                             : launch_plans(s, plans, s->capture_stream, masked);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(s->capture_stream, &graph);
@@ -506,66 +645,32 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
                           double *energy, double *grad, int flags) {
     if (!s || s->magic != kStateMagic) return set_error(QS_EINVAL, "state is NULL or not valid");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_adjoint_grad: gates is NULL");
-    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_OUT_DEVICE))
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_OUT_DEVICE | QS_FLAG_JIT))
         return set_error(QS_EINVAL, "qs_adjoint_grad: unknown flags");
+    if ((flags & QS_FLAG_JIT) && !(flags & QS_FLAG_FUSE))
+        return set_error(QS_EINVAL, "qs_adjoint_grad: QS_FLAG_JIT needs QS_FLAG_FUSE");
     if (n_theta > 0 && !grad) return set_error(QS_EINVAL, "qs_adjoint_grad: grad is NULL");
     if (n_theta > (size_t)(1 << 24)) return set_error(QS_EINVAL, "qs_adjoint_grad: n_theta too large");
     const bool on_dev = (flags & QS_FLAG_OUT_DEVICE) != 0;
-
-    // Plans: forward, and for the sweep U^dagger (+ dU for parameterised gates).
-    std::vector<GatePlan> fwd(count), adj(count);
-    std::vector<int> slot_of(count, -1);
-    std::vector<int> slot_param;
-    std::vector<double> dus;  // 8 doubles per slot
-    char err[256], e2[200];
-    for (size_t i = 0; i < count; ++i) {
-        const qs_gate &g = gates[i];
-        if (!plan_record(s, g, theta, n_theta, i, &fwd[i], err, sizeof(err))) return set_error(QS_EINVAL, err);
-        double U[8], Ud[8];
-        int force = -1;
-        if (g.kind == QS_GATE_X) {
-            force = OP_SWAP;
-            std::memset(Ud, 0, sizeof(Ud));
-            Ud[2] = 1.0;
-            Ud[4] = 1.0;
-        } else {
-            if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) rot_matrix(g.kind, theta[g.param], U);
-            else std::memcpy(U, g.U, sizeof(U));
-            dagger(U, Ud);
-            if (g.kind == QS_GATE_RY) force = OP_REAL;
-            else if (g.kind == QS_GATE_RZ) force = OP_DIAG;
-        }
-        if (!plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, force, &adj[i], e2,
-                       sizeof(e2)))
-            return set_error(QS_EINVAL, e2);
-        if (adj[i].op == OP_SIDE) {  // the sweep kernels scale both sides
-            GatePlan q;
-            plan_gate(s->n, s->dtype, g.target, g.ctrl_mask, g.ctrl_vals, Ud, QS_GATE_U, OP_DIAG, &q, e2, sizeof(e2));
-            adj[i] = q;
-        }
-        if (g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ) {
-            slot_of[i] = (int)slot_param.size();
-            slot_param.push_back(g.param);
-            double D[8];
-            rot_derivative(g.kind, theta[g.param], D);
-            dus.insert(dus.end(), D, D + 8);
-        }
+    AdjPlan ap;
+    {
+        char err[256];
+        if (!plan_adjoint(s, gates, count, theta, n_theta, flags, &ap, err, sizeof(err)))
+            return set_error(QS_EINVAL, err);
     }
+    std::vector<GatePlan> &fwd = ap.fwd, &adj = ap.adj;
+    std::vector<int> &slot_of = ap.slot_of, &slot_param = ap.slot_param;
+    std::vector<double> &dus = ap.dus;
+    std::vector<const double *> &dusp = ap.dusp;
+    FusedProgram &pf = ap.pf, &pa = ap.pa;
     const int nslots = (int)slot_param.size();
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
-    FusedProgram pf, pa;
-    std::vector<const double *> dusp(count, nullptr);
-    merge_runs(s, fwd);  // the forward pass needs no per-gate state
-    if (fuse) {
-        std::vector<int> seq(fwd.size());
-        for (size_t i = 0; i < fwd.size(); ++i) seq[i] = (int)i;
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &pf);
-        seq.resize(count);
-        for (size_t i = 0; i < count; ++i) {
-            seq[i] = (int)(count - 1 - i);
-            if (slot_of[i] >= 0) dusp[i] = &dus[8 * slot_of[i]];
-        }
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &dusp, &slot_of, &pa);
+    std::vector<JitPass> jf, ja;
+    const bool use_jit = (flags & QS_FLAG_JIT) != 0;
+    if (use_jit) {
+        std::string jerr;
+        if (!jit_prepare_program(s->dtype, false, pf, &jf, &jerr) || !jit_prepare_program(s->dtype, true, pa, &ja, &jerr))
+            return set_error(QS_ECUDA, ("qs_adjoint_grad: " + jerr).c_str());
     }
 
     // Buffers: lambda, partials [nslots][P], slot sums, slot->param map, outputs.
@@ -617,7 +722,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     const void *tab_f = s->tile_table;
     const void *tab_a = tab_f ? static_cast<const char *>(tab_f) + bf : nullptr;
     // Forward pass.
-    st = fuse ? launch_program(s, pf, fwd, tab_f, nullptr, nullptr, nullptr, nullptr, 0, stm)
+    st = fuse ? launch_program(s, pf, fwd, tab_f, nullptr, nullptr, nullptr, nullptr, 0, stm, use_jit ? &jf : nullptr)
               : launch_plans(s, fwd, stm);
     if (st != QS_OK) return st;
     // Energy and lambda = O psi.
@@ -632,7 +737,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     if (e != cudaSuccess) return cuda_fail(e, "qs_adjoint_grad setup");
     // Reverse sweep.
     if (fuse) {
-        st = launch_program(s, pa, adj, tab_a, s->lam, &dusp, &slot_of, part, P, stm);
+        st = launch_program(s, pa, adj, tab_a, s->lam, &dusp, &slot_of, part, P, stm, use_jit ? &ja : nullptr);
         if (st != QS_OK) return st;
     } else {
         for (size_t ii = count; ii-- > 0;) {

@@ -1,0 +1,559 @@
+// qs_jit.cu -- tile passes generated for their exact shape and compiled at run time (NVRTC).
+//
+// What a generated kernel computes is what k_tile_pass computes for the same TilePass, groups
+// and gates (the same tile map, swizzle, register groups, folded exchanges, predicates and
+// pair updates, Section III Eq. 2 per selected pair); only the per-gate interpretation is
+// gone. See qs_jit.cuh.
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "k_tile.cuh"
+#include "qs_jit.cuh"
+
+namespace qs {
+
+int device_sm_count();
+
+namespace {
+
+struct Out {
+    std::string s;
+    void f(const char *fmt, ...) {
+        char buf[1024];
+        va_list ap;
+        va_start(ap, fmt);
+        const int m = std::vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        if (m < (int)sizeof(buf)) {
+            s += buf;
+        } else {
+            std::vector<char> big((size_t)m + 1);
+            va_start(ap, fmt);
+            std::vsnprintf(big.data(), big.size(), fmt, ap);
+            va_end(ap);
+            s += big.data();
+        }
+    }
+};
+
+// Local tile offset o -> global amplitude offset (the pass's runs of consecutive local bits).
+uint64_t scatter_host(const TilePass &P, uint32_t o) {
+    uint64_t g = 0;
+    for (int r = 0; r < P.nruns; ++r)
+        g |= (uint64_t)((o >> P.run_src[r]) & ((1u << P.run_len[r]) - 1u)) << P.run_dst[r];
+    return g;
+}
+
+// Types, copies and pair updates shared by every generated kernel (one precision).
+void preamble(Out &o, bool dbl) {
+    o.f("typedef unsigned int u32;\ntypedef unsigned long long u64;\n");
+    if (dbl) {
+        o.f("typedef double R;\nstruct alignas(16) T2 { double x, y; };\n");
+        o.f("__device__ __forceinline__ R F(R a, R b, R c) { return __fma_rn(a, b, c); }\n");
+    } else {
+        o.f("typedef float R;\nstruct alignas(8) T2 { float x, y; };\nstruct alignas(16) T4 { float x, y, z, w; };\n");
+        o.f("__device__ __forceinline__ R F(R a, R b, R c) { return __fmaf_rn(a, b, c); }\n");
+    }
+    // the same operation order as the interpreted pass (k_gate.cuh cmac / cmul / pair_update)
+    o.f("__device__ __forceinline__ void u_gen(T2 &x, T2 &y, const R *m) {\n"
+        "  T2 a, b;\n"
+        "  a.x = F(m[0], x.x, F(-m[1], x.y, F(m[2], y.x, -m[3] * y.y)));\n"
+        "  a.y = F(m[0], x.y, F(m[1], x.x, F(m[2], y.y, m[3] * y.x)));\n"
+        "  b.x = F(m[4], x.x, F(-m[5], x.y, F(m[6], y.x, -m[7] * y.y)));\n"
+        "  b.y = F(m[4], x.y, F(m[5], x.x, F(m[6], y.y, m[7] * y.x)));\n"
+        "  x = a; y = b;\n}\n");
+    o.f("__device__ __forceinline__ void u_real(T2 &x, T2 &y, const R *m) {\n"
+        "  T2 a, b;\n"
+        "  a.x = F(m[0], x.x, m[2] * y.x); a.y = F(m[0], x.y, m[2] * y.y);\n"
+        "  b.x = F(m[4], x.x, m[6] * y.x); b.y = F(m[4], x.y, m[6] * y.y);\n"
+        "  x = a; y = b;\n}\n");
+    o.f("__device__ __forceinline__ void u_mul(T2 &x, R ar, R ai) {\n"
+        "  T2 a; a.x = F(ar, x.x, -ai * x.y); a.y = F(ar, x.y, ai * x.x); x = a;\n}\n");
+    o.f("__device__ __forceinline__ void u_diag(T2 &x, T2 &y, const R *m) { u_mul(x, m[0], m[1]); u_mul(y, m[6], m[7]); }\n");
+    o.f("__device__ __forceinline__ void u_swap(T2 &x, T2 &y) { T2 t = x; x = y; y = t; }\n");
+    o.f("__device__ __forceinline__ void cp8(void *s, const void *g) {\n"
+        "  asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\\n\" :: \"r\"((u32)__cvta_generic_to_shared(s)), "
+        "\"l\"(g) : \"memory\");\n}\n");
+    o.f("__device__ __forceinline__ void cp16(void *s, const void *g) {\n"
+        "  asm volatile(\"cp.async.cg.shared.global [%%0], [%%1], 16;\\n\" :: \"r\"((u32)__cvta_generic_to_shared(s)), "
+        "\"l\"(g) : \"memory\");\n}\n");
+    o.f("__device__ __forceinline__ void cpwait() {\n"
+        "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n}\n");
+}
+
+// Expression of the tile swizzle of `a` (the same bijection as tile_swizzle, k_tile.cuh).
+std::string swz_expr(const char *a, int sw) {
+    std::string x = std::string("(") + a + " >> " + std::to_string(sw) + ")";
+    std::string f = x;
+    for (int i = sw; i < kTileMaxBits; i += sw) f += " ^ (" + x + " >> " + std::to_string(i) + ")";
+    return std::string("(") + a + " ^ ((" + f + ") & " + std::to_string((1u << sw) - 1u) + "u))";
+}
+
+// Tile predicate of a set of gates: "" if some gate has no non-local control (every tile
+// is selected), else the condition that one of them selects the tile at `base`.
+std::string any_selects(const RegGate *g, int count) {
+    std::vector<std::pair<uint64_t, uint64_t>> seen;
+    std::string c;
+    for (int i = 0; i < count; ++i) {
+        if (g[i].hmask == 0) return "";
+        bool dup = false;
+        for (auto &s : seen) dup |= s.first == g[i].hmask && s.second == g[i].hvals;
+        if (dup) continue;
+        seen.push_back({g[i].hmask, g[i].hvals});
+        char b[96];
+        std::snprintf(b, sizeof(b), "%s((base & 0x%llxull) == 0x%llxull)", c.empty() ? "" : " || ",
+                      (unsigned long long)g[i].hmask, (unsigned long long)g[i].hvals);
+        c += b;
+    }
+    return c;
+}
+
+// The pair updates of one gate on row registers v (and, adjoint, w with the derivative dot).
+void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, int slot, const char *v, const char *w) {
+    const int p = G.p;
+    int dop = G.op == OP_DIAG ? OP_DIAG : (G.op == OP_REAL ? OP_REAL : OP_GEN);
+    for (int e = 0; e < E; ++e) {
+        if ((e >> p) & 1) continue;
+        if ((e & G.cqm) != G.cqv) continue;
+        const int e2 = e | (1 << p);
+        auto op = [&](const char *a) {
+            switch (G.op) {
+            case OP_GEN: o.f("u_gen(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
+            case OP_REAL: o.f("u_real(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
+            case OP_DIAG: o.f("u_diag(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
+            case OP_SWAP: o.f("u_swap(%s[%d], %s[%d]);\n", a, e, a, e2); break;
+            case OP_SIDE: o.f("u_mul(%s[%d], a.m[%d][0], a.m[%d][1]);\n", a, G.side ? e2 : e, gi, gi); break;
+            default: break;
+            }
+        };
+        op(v);
+        if (adjoint) {
+            if (slot >= 0) {
+                o.f("{ T2 mx = %s[%d], my = %s[%d]; ", v, e, v, e2);
+                o.f("%s(mx, my, a.d[%d]); ", dop == OP_DIAG ? "u_diag" : (dop == OP_REAL ? "u_real" : "u_gen"), slot);
+                o.f("dot += %s[%d].x * mx.x + %s[%d].y * mx.y + %s[%d].x * my.x + %s[%d].y * my.y; }\n", w, e, w, e, w,
+                    e2, w, e2);
+            }
+            op(w);
+        }
+    }
+}
+
+}  // namespace
+
+std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups,
+                            const RegGate *gates, const char *kname) {
+    const bool dbl = dtype == QS_C128;
+    const int SW = dbl ? 3 : 4;
+    const int VEC = dbl ? 1 : 2;
+    const int T = kTileThreads;
+    const int k = P.k;
+    const uint32_t nvec = (1u << k) / VEC;
+    const uint32_t steps = (nvec + T - 1) / T;
+    const int G = P.gate_count;
+    const int NP = adjoint ? P.nparam : 0;
+    Out o;
+    preamble(o, dbl);
+    // parameter block: the matrices of the pass's gates (U, or U^dagger in the adjoint sweep),
+    // the derivatives of its parameterised gates, their global gradient slots, the partials
+    o.f("struct alignas(16) A {\n  R m[%d][8];\n", G > 0 ? G : 1);
+    if (adjoint) o.f("  R d[%d][8];\n  int gs[%d];\n", NP > 0 ? NP : 1, NP > 0 ? NP : 1);
+    o.f("};\n");
+    o.f("__device__ __forceinline__ u32 swz(u32 a) { return %s; }\n", swz_expr("a", SW).c_str());
+    const int minb = (adjoint && dbl) ? 1 : 2;
+    if (adjoint)
+        o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, T2 *__restrict__ lam, "
+            "double *__restrict__ part, u64 part_stride, const __grid_constant__ A a) {\n",
+            T, minb, kname);
+    else
+        o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, const __grid_constant__ A a) {\n",
+            T, minb, kname);
+    o.f("  extern __shared__ __align__(16) unsigned char sm_[];\n");
+    o.f("  T2 *tp = reinterpret_cast<T2 *>(sm_);\n");
+    if (adjoint) {
+        o.f("  T2 *tl = tp + %u;\n", 1u << k);
+        o.f("  R *acc_s = reinterpret_cast<R *>(tl + %u);\n", 1u << k);
+        o.f("  R *acc_c = acc_s + %d;\n", (NP > 0 ? NP : 1) * (T / 32));
+        o.f("  for (int i = threadIdx.x; i < %d; i += %d) { acc_s[i] = 0; acc_c[i] = 0; }\n", (NP > 0 ? NP : 1) * (T / 32), T);
+        o.f("  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n");
+    }
+    o.f("  const u32 tid = threadIdx.x;\n");
+    // this thread's part of the copy addresses (XOR-linear in the element index)
+    o.f("  const u32 o_t = tid * %d;\n", VEC);
+    {
+        std::string g = "0ull";
+        for (int r = 0; r < P.nruns; ++r) {
+            char b[160];
+            std::snprintf(b, sizeof(b), " | ((u64)((o_t >> %d) & %uu) << %d)", P.run_src[r], (1u << P.run_len[r]) - 1u,
+                          P.run_dst[r]);
+            g += b;
+        }
+        o.f("  const u64 g_t = %s;\n", g.c_str());
+    }
+    o.f("  const u32 s_t = swz(o_t);\n");
+    const bool cp_guard = nvec < (uint32_t)T;
+    o.f("  const u64 ntiles = %lluull;\n", (unsigned long long)P.ntiles);
+    o.f("  for (u64 tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n");
+    {
+        std::string b = "0ull";
+        for (int s = 0; s < P.tnseg; ++s) {
+            char t[96];
+            std::snprintf(t, sizeof(t), " | ((tau << %d) & 0x%llxull)", P.tshift[s], (unsigned long long)P.tmask[s]);
+            b += t;
+        }
+        o.f("    const u64 base = %s;\n", b.c_str());
+    }
+    if (P.hctrl) {
+        const std::string c = any_selects(gates + P.gate_begin, G);
+        if (!c.empty()) o.f("    if (!(%s)) continue;\n", c.c_str());
+    }
+    // tile load (asynchronous copies into swizzled shared-memory positions)
+    const uint32_t s1 = tile_swizzle(1u, SW);
+    auto copies = [&](bool load, const char *gname, const char *tname) {
+        if (cp_guard) o.f("    if (tid < %uu) {\n", nvec);
+        for (uint32_t j = 0; j < steps; ++j) {
+            const uint32_t oj = j * T * VEC;
+            const unsigned long long gj = (unsigned long long)scatter_host(P, oj);
+            const uint32_t sj = tile_swizzle(oj, SW);
+            if (load && !dbl)
+                o.f("    { const T2 *g = %s + (base | g_t | 0x%llxull); const u32 s = s_t ^ %uu; "
+                    "cp8(%s + s, g); cp8(%s + (s ^ %uu), g + 1); }\n",
+                    gname, gj, sj, tname, tname, s1);
+            else if (load)
+                o.f("    cp16(%s + (s_t ^ %uu), %s + (base | g_t | 0x%llxull));\n", tname, sj, gname, gj);
+            else if (!dbl)
+                o.f("    { const u32 s = s_t ^ %uu; const T2 x0 = %s[s], x1 = %s[s ^ %uu]; T4 q; q.x = x0.x; "
+                    "q.y = x0.y; q.z = x1.x; q.w = x1.y; *reinterpret_cast<T4 *>(%s + (base | g_t | 0x%llxull)) = q; }\n",
+                    sj, tname, tname, s1, gname, gj);
+            else
+                o.f("    %s[base | g_t | 0x%llxull] = %s[s_t ^ %uu];\n", gname, gj, tname, sj);
+        }
+        if (cp_guard) o.f("    }\n");
+    };
+    auto emit_copies = [&](bool load, const char *gname, const char *tname) { copies(load, gname, tname); };
+    emit_copies(true, "psi", "tp");
+    if (adjoint) emit_copies(true, "lam", "tl");
+    o.f("    cpwait();\n    __syncthreads();\n");
+
+    const RegGate *pg = gates + P.gate_begin;
+    for (int gi_ = 0; gi_ < P.group_count; ++gi_) {
+        const TileGroup &Gr = groups[P.group_begin + gi_];
+        const int r = Gr.r;
+        const int E = 1 << r;
+        const uint32_t rows = 1u << (k - r);
+        const uint32_t rblocks = (rows + T - 1) / T;
+        const int gb = Gr.gate_begin - P.gate_begin;  // pass-relative
+        o.f("    // register group %d: qubits", gi_);
+        for (int q = 0; q < r; ++q) o.f(" %d", Gr.q[q]);
+        o.f(", %d gates\n", Gr.gate_count);
+        std::string gcond;
+        if (Gr.hctrl && !Gr.has_g && !Gr.has_s) gcond = any_selects(pg + gb, Gr.gate_count);
+        o.f("    if (%s) {\n", gcond.empty() ? "true" : gcond.c_str());
+        // element offsets of the gather and the scatter
+        std::vector<uint32_t> og(E), os(E);
+        for (int e = 0; e < E; ++e) {
+            uint32_t off = 0;
+            for (int q = 0; q < r; ++q)
+                if ((e >> q) & 1) off ^= Gr.qsw[q];
+            og[e] = Gr.has_g ? Gr.gperm[e] : off;
+            os[e] = Gr.has_s ? Gr.sperm[e] : off;
+        }
+        for (uint32_t rb = 0; rb < rblocks; ++rb) {
+            o.f("    {\n      const u32 rho = %uu + tid;\n", rb * T);
+            const bool guard = rows < (rb + 1) * (uint32_t)T;
+            std::string ra = "0u";
+            for (int s = 0; s < Gr.nrseg; ++s) {
+                char t[80];
+                std::snprintf(t, sizeof(t), " | ((rho << %d) & 0x%xu)", Gr.rshift[s], Gr.rmask[s]);
+                ra += t;
+            }
+            o.f("      const u32 ra = %s;\n      const u32 rs = swz(ra);\n", ra.c_str());
+            o.f("      const bool act = %s;\n", guard ? (std::string("rho < ") + std::to_string(rows) + "u").c_str() : "true");
+            o.f("      T2 v[%d]%s;\n", E, adjoint ? "" : "");
+            if (adjoint) o.f("      T2 w[%d];\n", E);
+            o.f("      if (act) {\n");
+            for (int e = 0; e < E; ++e) {
+                o.f("        v[%d] = tp[rs ^ %uu];\n", e, og[e]);
+                if (adjoint) o.f("        w[%d] = tl[rs ^ %uu];\n", e, og[e]);
+            }
+            o.f("      } else {\n");
+            for (int e = 0; e < E; ++e) {
+                o.f("        v[%d].x = 0; v[%d].y = 0;\n", e, e);
+                if (adjoint) o.f("        w[%d].x = 0; w[%d].y = 0;\n", e, e);
+            }
+            o.f("      }\n");
+            for (int g = 0; g < Gr.gate_count; ++g) {
+                const RegGate &R = pg[gb + g];
+                const int gi = gb + g;  // index into a.m
+                const int slot = adjoint ? R.slot : -1;
+                o.f("      // gate %d: op %d, place %d, cq %x/%x, rows %x/%x\n", gi, R.op, R.p, R.cqm, R.cqv, R.crm, R.crv);
+                const bool tile_guard = R.hmask != 0;
+                if (tile_guard)
+                    o.f("      if ((base & 0x%llxull) == 0x%llxull) {\n", (unsigned long long)R.hmask,
+                        (unsigned long long)R.hvals);
+                else
+                    o.f("      {\n");
+                if (slot >= 0) o.f("        R dot = 0;\n");
+                std::string rc = "act";
+                if (R.crm) {
+                    char t[80];
+                    std::snprintf(t, sizeof(t), "act && ((ra & 0x%xu) == 0x%xu)", R.crm, R.crv);
+                    rc = t;
+                }
+                const bool need_rc = guard || R.crm;
+                if (need_rc) o.f("        if (%s) {\n", rc.c_str());
+                emit_gate_pairs(o, R, gi, E, adjoint, slot, "v", "w");
+                if (need_rc) o.f("        }\n");
+                if (slot >= 0) {
+                    o.f("        for (int of = 16; of > 0; of >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, of);\n");
+                    o.f("        if (lane == 0) { R *s_ = acc_s + %d * %d + warp, *c_ = acc_c + %d * %d + warp; "
+                        "const R y = dot - *c_; const R t = *s_ + y; *c_ = (t - *s_) - y; *s_ = t; }\n",
+                        slot, T / 32, slot, T / 32);
+                }
+                o.f("      }\n");
+            }
+            o.f("      if (act) {\n");
+            for (int e = 0; e < E; ++e) {
+                o.f("        tp[rs ^ %uu] = v[%d];\n", os[e], e);
+                if (adjoint) o.f("        tl[rs ^ %uu] = w[%d];\n", os[e], e);
+            }
+            o.f("      }\n    }\n");
+        }
+        o.f("    }\n    __syncthreads();\n");
+    }
+    emit_copies(false, "psi", "tp");
+    if (adjoint) emit_copies(false, "lam", "tl");
+    o.f("    __syncthreads();\n  }\n");
+    if (adjoint && NP > 0) {
+        o.f("  __syncthreads();\n");
+        o.f("  for (int p = threadIdx.x; p < %d; p += %d) {\n", NP, T);
+        o.f("    double s = 0.0;\n");
+        o.f("    for (int w_ = 0; w_ < %d; ++w_) s += (double)acc_s[p * %d + w_] - (double)acc_c[p * %d + w_];\n", T / 32,
+            T / 32, T / 32);
+        o.f("    part[(u64)a.gs[p] * part_stride + blockIdx.x] = s;\n  }\n");
+    }
+    o.f("}\n");
+    return o.s;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Compile cache
+// ---------------------------------------------------------------------------------------------
+
+struct Module {
+    std::string source;       // all kernels of the module
+    std::vector<char> cubin;
+    std::vector<std::string> names;
+    cudaLibrary_t lib = nullptr;  // loaded on first launch
+    std::vector<cudaKernel_t> kernels;
+    std::vector<size_t> smem_set[64];  // per device: dynamic shared memory configured per kernel
+    std::vector<int> occ[64];          // per device: resident blocks per SM per kernel (0 = unknown)
+};
+
+std::mutex g_mu;
+std::vector<std::unique_ptr<Module>> g_modules;
+std::unordered_map<std::string, std::pair<int, int>> g_by_source;  // kernel source -> (module, kernel)
+
+bool compile_cubin(const std::string &src, std::vector<char> *cubin, std::string *err) {
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "qs_jit_pass.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS) {
+        *err = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
+        return false;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=true", "-DQS_JIT=1"};
+    r = nvrtcCompileProgram(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+    if (r != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        nvrtcGetProgramLogSize(prog, &ls);
+        std::string log(ls, '\0');
+        if (ls) nvrtcGetProgramLog(prog, &log[0]);
+        *err = std::string("NVRTC compile failed: ") + nvrtcGetErrorString(r) + "\n" + log.substr(0, 4000);
+        nvrtcDestroyProgram(&prog);
+        return false;
+    }
+    size_t n = 0;
+    r = nvrtcGetCUBINSize(prog, &n);
+    if (r == NVRTC_SUCCESS) {
+        cubin->resize(n);
+        r = nvrtcGetCUBIN(prog, cubin->data());
+    }
+    nvrtcDestroyProgram(&prog);
+    if (r != NVRTC_SUCCESS) {
+        *err = std::string("nvrtcGetCUBIN: ") + nvrtcGetErrorString(r);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std::vector<JitPass> *out,
+                         std::string *err, double *compile_seconds, int *compiled_modules) {
+    out->assign(prog.passes.size(), JitPass{});
+    if (compile_seconds) *compile_seconds = 0.0;
+    if (compiled_modules) *compiled_modules = 0;
+    const size_t es = dtype == QS_C64 ? 8 : 16, rs = dtype == QS_C64 ? 4 : 8;
+    // one source per pass (kernel name fixed: the source text alone keys the cache)
+    std::vector<std::string> srcs(prog.passes.size());
+    for (size_t p = 0; p < prog.passes.size(); ++p)
+        srcs[p] = jit_pass_source(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data(), "qs_pass");
+    std::lock_guard<std::mutex> lock(g_mu);
+    // passes whose source is not cached yet go into one new module (renamed kernels)
+    std::vector<int> missing;
+    std::unordered_map<std::string, int> first_of;
+    for (size_t p = 0; p < srcs.size(); ++p) {
+        if (g_by_source.count(srcs[p])) continue;
+        if (first_of.count(srcs[p])) continue;
+        first_of[srcs[p]] = (int)p;
+        missing.push_back((int)p);
+    }
+    if (!missing.empty()) {
+        auto t0 = std::chrono::steady_clock::now();
+        auto m = std::make_unique<Module>();
+        // each pass source is self-contained; a module concatenates them inside namespaces
+        for (size_t i = 0; i < missing.size(); ++i) {
+            const std::string nm = "qs_pass_" + std::to_string(i);
+            std::string s = srcs[missing[i]];
+            const size_t at = s.find(" qs_pass(");
+            s.replace(at, 9, " " + nm + "(");
+            m->source += "namespace m" + std::to_string(i) + " {\n" + s + "}\n";
+            m->names.push_back(nm);
+        }
+        // QS_JIT_DUMP=<directory>: write each compiled module's source there (diagnostics)
+        if (const char *dir = std::getenv("QS_JIT_DUMP")) {
+            if (*dir) {
+                const std::string path = std::string(dir) + "/qs_jit_module_" + std::to_string(g_modules.size()) + ".cu";
+                if (FILE *f = std::fopen(path.c_str(), "w")) {
+                    std::fwrite(m->source.data(), 1, m->source.size(), f);
+                    std::fclose(f);
+                }
+            }
+        }
+        if (!compile_cubin(m->source, &m->cubin, err)) return false;
+        const int mi = (int)g_modules.size();
+        for (size_t i = 0; i < missing.size(); ++i) g_by_source[srcs[missing[i]]] = {mi, (int)i};
+        g_modules.push_back(std::move(m));
+        if (compile_seconds)
+            *compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (compiled_modules) *compiled_modules = 1;
+    }
+    for (size_t p = 0; p < srcs.size(); ++p) {
+        const auto &mk = g_by_source.at(srcs[p]);
+        JitPass &j = (*out)[p];
+        j.entry = mk.first;
+        j.kernel = mk.second;
+        const TilePass &P = prog.passes[p];
+        const size_t T = size_t(1) << P.k;
+        j.smem = (adjoint ? 2 : 1) * T * es +
+                 (adjoint ? 2 * (size_t)(P.nparam > 0 ? P.nparam : 1) * (kTileThreads / 32) * rs : 0);
+        const size_t G = P.gate_count > 0 ? P.gate_count : 1;
+        size_t bytes = G * 8 * rs;
+        if (adjoint) {
+            const size_t NP = P.nparam > 0 ? P.nparam : 1;
+            bytes += NP * 8 * rs;
+            bytes += NP * sizeof(int);
+        }
+        j.arg_bytes = (bytes + 15) & ~size_t(15);
+    }
+    return true;
+}
+
+cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
+                            double *part, size_t part_stride, cudaStream_t st) {
+    Module *m;
+    cudaKernel_t kern;
+    int occ = 1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (jp.entry < 0 || jp.entry >= (int)g_modules.size()) return cudaErrorInvalidValue;
+        m = g_modules[jp.entry].get();
+        if (!m->lib) {
+            cudaError_t e = cudaLibraryLoadData(&m->lib, m->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+            if (e != cudaSuccess) return e;
+            m->kernels.resize(m->names.size());
+            for (size_t i = 0; i < m->names.size(); ++i) {
+                e = cudaLibraryGetKernel(&m->kernels[i], m->lib, m->names[i].c_str());
+                if (e != cudaSuccess) return e;
+            }
+        }
+        kern = m->kernels[jp.kernel];
+        auto &ss = m->smem_set[dev];
+        auto &oc = m->occ[dev];
+        if (ss.size() < m->kernels.size()) {
+            ss.resize(m->kernels.size(), 0);
+            oc.resize(m->kernels.size(), 0);
+        }
+        if (jp.smem > 48 * 1024 && ss[jp.kernel] < jp.smem) {
+            cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(kern),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jp.smem);
+            if (e != cudaSuccess) return e;
+            ss[jp.kernel] = jp.smem;
+            oc[jp.kernel] = 0;
+        }
+        if (oc[jp.kernel] == 0) {
+            int v = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, reinterpret_cast<const void *>(kern), kTileThreads,
+                                                              jp.smem) != cudaSuccess ||
+                v < 1) {
+                cudaGetLastError();
+                v = 1;
+            }
+            oc[jp.kernel] = v;
+        }
+        occ = oc[jp.kernel];
+    }
+    const TilePass &P = prog.passes[p];
+    const bool adjoint = lam != nullptr;
+    // parameter block: matrices (state precision), derivatives, gradient slots
+    std::vector<unsigned char> blk(jp.arg_bytes, 0);
+    const int G = P.gate_count;
+    const RegGate *g = prog.gates.data() + P.gate_begin;
+    const size_t rs = dtype == QS_C64 ? 4 : 8;
+    const size_t G1 = G > 0 ? G : 1;
+    for (int i = 0; i < G; ++i) {
+        if (dtype == QS_C64)
+            std::memcpy(&blk[(size_t)i * 8 * rs], g[i].Uf, 8 * rs);
+        else
+            std::memcpy(&blk[(size_t)i * 8 * rs], g[i].U, 8 * rs);
+    }
+    if (adjoint) {
+        const size_t NP1 = P.nparam > 0 ? P.nparam : 1;
+        unsigned char *d = &blk[G1 * 8 * rs];
+        for (int i = 0; i < G; ++i) {
+            if (g[i].slot < 0) continue;
+            if (dtype == QS_C64)
+                std::memcpy(d + (size_t)g[i].slot * 8 * rs, g[i].Df, 8 * rs);
+            else
+                std::memcpy(d + (size_t)g[i].slot * 8 * rs, g[i].D, 8 * rs);
+        }
+        int *gs = reinterpret_cast<int *>(d + NP1 * 8 * rs);
+        for (int i = 0; i < P.nparam; ++i) gs[i] = P.param_gslot[i];
+    }
+    uint64_t cap = (uint64_t)device_sm_count() * occ;
+    if (adjoint) cap = std::min<uint64_t>(cap, part_stride);
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(P.ntiles, cap));
+    unsigned long long stride = part_stride;
+    void *args_fwd[] = {&psi, blk.data()};
+    void *args_adj[] = {&psi, &lam, &part, &stride, blk.data()};
+    return cudaLaunchKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kTileThreads),
+                            adjoint ? args_adj : args_fwd, jp.smem, st);
+}
+
+}  // namespace qs

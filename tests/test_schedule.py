@@ -150,3 +150,26 @@ def test_schedule_validates_theta(qs):
         qs.circuit_schedule(4, g, np.array([0.0, 0.0, 0.0, np.nan]))
     assert qs.circuit_schedule(4, g, np.zeros(4))["launches"] == 0
     assert qs.circuit_schedule(4, g, np.full(4, 0.3))["launches"] == 1
+
+
+def test_circuit_compile_caches_by_shape(qs):
+    """qs_circuit_compile generates and compiles the shape-specialised pass kernels on the
+    host (NVRTC, no device): a second call with the same structure at other angles is served
+    from the cache (no compile time); invalid gates are rejected as by qs_apply_circuit."""
+    import numpy as np
+    import workloads as W
+
+    q = qs
+    n, layers = 12, 2
+    g = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=3)
+    r1 = q.qs_circuit_compile(n, q.QS_C64, g, th)
+    assert r1["passes"] > 0
+    r2 = q.qs_circuit_compile(n, q.QS_C64, g, th + 0.5)
+    assert r2["passes"] == r1["passes"] and r2["compile_seconds"] == 0.0
+    ra = q.qs_circuit_compile(n, q.QS_C128, g, th, adjoint=True)
+    assert ra["passes"] > 0
+    bad = g.copy()
+    bad[0]["target"] = n
+    with pytest.raises(q.QsError):
+        q.qs_circuit_compile(n, q.QS_C64, bad, th)
