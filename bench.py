@@ -71,9 +71,21 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-# FP64 ALU peak of GB300: 1.25 TFLOP/s dense (NVIDIA's published FP64 figure for the part;
-# 152 SMs at 2.07 GHz -> ~4 flops/clk/SM, i.e. 2 double FMA per clock per SM).
-FP64_PEAK_TFLOPS = 1.25
+# FP64 ALU peak: measured on the device by the library's FMA-rate kernel (qs_measure_fma_peak),
+# 2 flops per FMA; NVIDIA's published FP64 figure for GB300 (1.25 TFLOP/s) is context only.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def measure_fma_peaks(qs):
+    """Measured FMA rates (TFLOP/s) in float64 and float32, best of 3 launches."""
+    import torch
+
+    stream = int(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    for label, dt, iters in (("fp64", qs.QS_C128, 1 << 14), ("fp32", qs.QS_C64, 1 << 16)):
+        out[label] = round(max(qs.qs_measure_fma_peak(dt, iters, stream) for _ in range(3)) / 1e12, 3)
+    out["how"] = "8 independent FMA chains per thread on every SM, CUDA events, best of 3 (2 flops per FMA)"
+    return out
 
 
 class ClockSampler:
@@ -263,7 +275,7 @@ def _events_ms(fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def measure_adjoint(qs, W, reps=3):
+def measure_adjoint(qs, W, peak, reps=3):
     """Differentiation workload: n = 24, 20 layers, 960 parameters. grads/s = parameters /
     time of one full gradient (forward + energy + reverse sweep, host outputs)."""
     import numpy as np
@@ -277,9 +289,11 @@ def measure_adjoint(qs, W, reps=3):
     tuned = {"fwd": autotune.tune_fused(n, "c64", gates, th, adjoint=False, use_cache=False, reps=1),
              "adj": autotune.tune_fused(n, "c64", gates, th, adjoint=True, use_cache=False, reps=1)}
     out = {"tile_bits_c64": {"forward": tuned["fwd"]["tile_bits"], "adjoint": tuned["adj"]["tile_bits"]}}
+    out["compile_s_c64_compiled"] = _compile(qs, n, gates, th, "c64", adjoint=True)
     grads = {}
-    for label, dtype, flags in (("c64_fused", "c64", qs.QS_FLAG_FUSE), ("c64_unfused", "c64", 0),
-                                ("c128_plain", "c128", 0), ("c128_fused", "c128", qs.QS_FLAG_FUSE)):
+    F, J = qs.QS_FLAG_FUSE, qs.QS_FLAG_JIT
+    for label, dtype, flags in (("c64_fused_compiled", "c64", F | J), ("c64_fused", "c64", F), ("c64_unfused", "c64", 0),
+                                ("c128_plain", "c128", 0), ("c128_fused", "c128", F)):
         st = qs.State(n, dtype)
         try:
             st.adjoint_grad(gates, th, flags)  # warm-up (allocates lambda and scratch)
@@ -292,16 +306,35 @@ def measure_adjoint(qs, W, reps=3):
                 ts.append(time.perf_counter() - t0)
             grads[label] = g
             out[label] = {"s_per_gradient": round(min(ts), 5), "grads_per_s": round(th.size / min(ts), 1),
-                          "energy": e}
+                          "energy": e,
+                          **program_roofline(qs, n, gates, th, flags | qs.QS_FLAG_ADJOINT, dtype, min(ts) * 1e3, peak)}
         finally:
             st.close()
-    for label in ("c64_fused", "c64_unfused", "c128_fused"):
+    for label in ("c64_fused_compiled", "c64_fused", "c64_unfused", "c128_fused"):
         out[f"max_abs_grad_err_{label}_vs_c128"] = float(np.max(np.abs(grads[label] - grads["c128_plain"])))
     out["speedup_c64_fused_vs_c128_plain"] = round(out["c128_plain"]["s_per_gradient"] /
-                                                   out["c64_fused"]["s_per_gradient"], 2)
+                                                   out["c64_fused_compiled"]["s_per_gradient"], 2)
+    out["timing"] = "wall time of one synchronous qs_adjoint_grad call (host outputs), best of 3"
     _reset_tile_bits(qs)
     out["workload"] = "HEA n=24, 20 layers (RY,RZ per qubit + CNOT ladder), 960 params, observable sum Z_i"
     return out
+
+
+def program_roofline(qs, n, gates, theta, flags, dtype, ms, peak):
+    """Algorithmic bytes of the launches qs_apply_circuit (or, with QS_FLAG_ADJOINT,
+    qs_adjoint_grad) makes for these flags (per single gate its selected amplitudes, per tile
+    pass the tiles its gates select, per diagonal run the chunks it can change; read + write),
+    divided by the measured time: achieved GB/s and the fraction of the HBM peak."""
+    sch = qs.circuit_schedule(n, gates, theta, flags=flags & ~qs.QS_FLAG_GRAPH, dtype=dtype)
+    gbs = sch["algorithmic_bytes"] / (ms * 1e-3) / 1e9
+    return {"algorithmic_GB": round(sch["algorithmic_bytes"] / 1e9, 3), "achieved_GBps": round(gbs, 1),
+            "frac_hbm": round(gbs / peak, 3), "launches": sch["launches"], "tile_passes": sch["tile_passes"]}
+
+
+def _compile(qs, n, gates, theta, dtype, adjoint=False):
+    """Compile the shape-specialised pass kernels ahead of the timed runs; returns seconds."""
+    dt = qs.QS_C64 if dtype == "c64" else qs.QS_C128
+    return round(qs.qs_circuit_compile(n, dt, gates, theta, adjoint=adjoint)["compile_seconds"], 3)
 
 
 def _reset_tile_bits(qs):
@@ -312,41 +345,30 @@ def _reset_tile_bits(qs):
             qs.qs_set_tile_bits(dt, adj, 0)
 
 
-def measure_fused(qs, W):
-    """Fused tile passes: the 1000-gate scale circuit at n = 30 (complex64) and the ansatz at
-    n = 24, unfused vs fused (tile size from the autotuner), gates/s."""
+def measure_fused(qs, W, peak):
+    """Fused programs: the 1000-gate scale circuit at n = 30 (complex64) and the ansatz at
+    n = 24: one launch per gate, fused with interpreted tile passes, and fused with passes
+    compiled for their shape (QS_FLAG_JIT, compiled before timing); gates/s and the
+    algorithmic-byte roofline of each schedule. Tile size: library default (2^12 amplitudes)."""
     import torch
 
-    from paper_2411_18354_gb300 import autotune
-
     out = {}
-    n = 30
-    gates = W.scale_circuit(n, 1000, seed=1)
-    st = qs.State(n, "c64")
-    try:
-        t_unf = _events_ms(lambda: st.apply_circuit(gates, flags=qs.QS_FLAG_GRAPH), 1)
-        tb = autotune.tune_fused(n, "c64", gates, adjoint=False, candidates=(12, 13), use_cache=False, reps=1)
-        t_fus = _events_ms(lambda: st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_GRAPH), 1)
-    finally:
-        st.close()
-        torch.cuda.empty_cache()
-    out["scale_circuit_n30_c64"] = {"gates": 1000, "unfused_gates_per_s": round(1000 / (t_unf * 1e-3), 1),
-                                    "fused_gates_per_s": round(1000 / (t_fus * 1e-3), 1),
-                                    "tile_bits": tb["tile_bits"]}
-    _reset_tile_bits(qs)
-    n, layers = 24, 20
-    g = W.hea_circuit(n, layers)
-    th = W.hea_params(n, layers, seed=3)
-    st = qs.State(n, "c64")
-    try:
-        t_unf = _events_ms(lambda: st.apply_circuit(g, th), 3)
-        tb2 = autotune.tune_fused(n, "c64", g, th, adjoint=False, candidates=(12, 13), use_cache=False, reps=1)
-        t_fus = _events_ms(lambda: st.apply_circuit(g, th, qs.QS_FLAG_FUSE), 3)
-    finally:
-        st.close()
-        _reset_tile_bits(qs)
-    out["ansatz_n24_c64"] = {"gates": int(len(g)), "unfused_ms": round(t_unf, 3), "fused_ms": round(t_fus, 3),
-                             "fused_gates_per_s": round(len(g) / (t_fus * 1e-3), 1), "tile_bits": tb2["tile_bits"]}
+    F, G, J = qs.QS_FLAG_FUSE, qs.QS_FLAG_GRAPH, qs.QS_FLAG_JIT
+    for name, n, gates, th, reps in (("scale_circuit_n30_c64", 30, W.scale_circuit(30, 1000, seed=1), None, 1),
+                                     ("ansatz_n24_c64", 24, W.hea_circuit(24, 20), W.hea_params(24, 20, seed=3), 3)):
+        st = qs.State(n, "c64")
+        r = {"gates": int(len(gates))}
+        try:
+            r["compile_s"] = _compile(qs, n, gates, th, "c64")
+            for label, flags in (("unfused", G), ("fused_interpreted", F | G), ("fused_compiled", F | G | J)):
+                ms = _events_ms(lambda: st.apply_circuit(gates, th, flags), reps)
+                r[label] = {"ms": round(ms, 3), "gates_per_s": round(len(gates) / (ms * 1e-3), 1),
+                            **program_roofline(qs, n, gates, th, flags, "c64", ms, peak)}
+        finally:
+            st.close()
+            torch.cuda.empty_cache()
+        r["speedup_compiled_vs_unfused"] = round(r["unfused"]["ms"] / r["fused_compiled"]["ms"], 2)
+        out[name] = r
     return out
 
 
@@ -397,14 +419,12 @@ PAPER_TIMES_S = {
 }
 
 
-def measure_paper_circuits(qs, W, reps=3):
+def measure_paper_circuits(qs, W, peak, reps=3):
     """The paper's 29-qubit QFT (435 gates) and streaming circuit (29 X gates with 0..28
     controls) in complex64, each as one graph launch of the whole circuit through
     qs_apply_circuit: baseline schedule (QS_FLAG_MASKED), reduced iteration set, and fused
     tile passes. Device time per circuit (CUDA events, state 4.3 GB > L2)."""
     import torch
-
-    from paper_2411_18354_gb300 import autotune
 
     n = 29
     out = {}
@@ -414,14 +434,14 @@ def measure_paper_circuits(qs, W, reps=3):
             r = {"gates": int(len(gates)),
                  "algorithmic_GB": round(sum(2.0 * (1 << (n - bin(int(g["ctrl_mask"])).count("1"))) * 8
                                              for g in gates) / 1e9, 3)}
-            for label, flags in (("masked", qs.QS_FLAG_MASKED), ("reduced", 0), ("fused", qs.QS_FLAG_FUSE)):
-                if flags & qs.QS_FLAG_FUSE:
-                    r["fused_tile_bits"] = autotune.tune_fused(n, "c64", gates, adjoint=False, candidates=(12, 13),
-                                                               use_cache=False, reps=1)["tile_bits"]
+            r["compile_s"] = _compile(qs, n, gates, None, "c64")
+            for label, flags in (("masked", qs.QS_FLAG_MASKED), ("reduced", 0), ("fused", qs.QS_FLAG_FUSE),
+                                 ("fused_compiled", qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)):
                 st.set_basis(0)
                 ms = _events_ms(lambda: st.apply_circuit(gates, flags=flags | qs.QS_FLAG_GRAPH), reps)
                 r[f"{label}_ms"] = round(ms, 3)
-                _reset_tile_bits(qs)
+                rf = program_roofline(qs, n, gates, None, flags, "c64", ms, peak)
+                r[f"{label}_roofline"] = {k: rf[k] for k in ("algorithmic_GB", "achieved_GBps", "frac_hbm", "launches")}
             r["masked_over_reduced"] = round(r["masked_ms"] / r["reduced_ms"], 2)
             r["paper_s"] = PAPER_TIMES_S[name]
             out[name] = r
@@ -429,7 +449,8 @@ def measure_paper_circuits(qs, W, reps=3):
         st.close()
         torch.cuda.empty_cache()
     out["note"] = ("paper_s: Tables 2 and 4 (GTX Titan Black / Stratix V, one OpenCL compute unit), context only; "
-                   "algorithmic_GB counts 2*2^(n-c)*8 bytes per gate")
+                   "algorithmic_GB counts 2*2^(n-c)*8 bytes per gate; *_roofline: algorithmic bytes of that "
+                   "schedule's launches / its time; tile size: library default")
     return out
 
 
@@ -449,15 +470,17 @@ def measure_precision(qs, W):
     try:
         s128 = qs.State.wrap(b128, n)
         s64 = qs.State.wrap(b64, n)
-        for st, label, flags in ((s128, "c128", 0), (s64, "c64_fused", qs.QS_FLAG_FUSE)):
+        _compile(qs, n, gates, None, "c64")
+        for st, label, flags in ((s128, "c128", 0), (s64, "c64_fused", qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)):
             st.set_basis(0)
-            st.apply_circuit(prefix, flags=flags)
+            st.apply_circuit(prefix, flags=flags & ~qs.QS_FLAG_JIT)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st.apply_circuit(gates, flags=flags)
             torch.cuda.synchronize()
             out[label] = {"s": round(time.perf_counter() - t0, 3)}
         out["c64_fused"]["tile_bits"] = qs.qs_get_tile_bits(qs.QS_C64, 0)  # the library default
+        out["c64_fused"]["passes"] = "compiled for their shape (QS_FLAG_JIT), compiled before timing"
         z128, n128 = s128.expect_z()
         z64, n64 = s64.expect_z()
         err = 0.0
@@ -646,6 +669,10 @@ def run_ours(args, rank, world, local_rank):
     per_c = None if args.quick else measure_per_c(qs, st, n, esize, sched, peak)
     traffic = profiled_traffic(n, "c64")
 
+    roof_extra = {}
+    if per_c:
+        roof_extra = {"per_c_frac": [per_c[str(c)]["frac"] for c in range(CMAX + 1)],
+                      "per_c_frac_sector_adjusted": [per_c[str(c)]["frac_sector_adjusted"] for c in range(CMAX + 1)]}
     result = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -657,7 +684,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": peak_src,
                      "kernel": "k_gate (qs_apply_gate)",
-                     "frac_sector_adjusted": round(sect_bytes / (launch_ms * 1e-3) / 1e9 / peak, 4)},
+                     "frac_sector_adjusted": round(sect_bytes / (launch_ms * 1e-3) / 1e9 / peak, 4), **roof_extra},
         "per_c": per_c,
         "gpu_launches": len(per),
         "clocks": clocks,
@@ -741,18 +768,21 @@ def run_ours(args, rank, world, local_rank):
         ms2 = sum(x for _, _, x, _ in per2)
         pairs = sum(1 << (n - 1 - c) for c, _, _, _ in per2)
         flops = 28.0 * pairs  # general 2x2 complex update: 12 FMA + 4 MUL per pair, FMA = 2 flops
+        peaks = measure_fma_peaks(qs)
+        result["fma_peaks_tflops"] = peaks
         result["c128_sweep"] = {
             "GBps": round(b2 / (ms2 * 1e-3) / 1e9, 1), "frac_hbm": round(b2 / (ms2 * 1e-3) / 1e9 / peak, 3),
             "roofline": {"bound": "alu", "achieved": round(flops / (ms2 * 1e-3) / 1e12, 3),
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                         "frac": round(flops / (ms2 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 3)},
+                         "peak": peaks["fp64"], "unit": "TFLOP/s (FP64)", "peak_source": "measured (qs_measure_fma_peak)",
+                         "frac": round(flops / (ms2 * 1e-3) / 1e12 / peaks["fp64"], 3),
+                         "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS},
         }
-        result["adjoint"] = measure_adjoint(qs, W)
-        result["fused"] = measure_fused(qs, W)
+        result["adjoint"] = measure_adjoint(qs, W, peak)
+        result["fused"] = measure_fused(qs, W, peak)
         result["reduce_expect_z_n30"] = measure_reduce(qs, W, peak)
         result["masked_over_reduced_time_by_c"] = measure_masked(qs, n, sched)
         result["batch"] = measure_batch(qs, W)
-        result["paper_circuits"] = measure_paper_circuits(qs, W)
+        result["paper_circuits"] = measure_paper_circuits(qs, W, peak)
         result["precision_n32"] = measure_precision(qs, W)
         result["cpu_baseline"] = cpu_oracle_sample(n, sched)
 

@@ -64,8 +64,9 @@ enum {
     QS_FLAG_GRAPH = 2,       /* launch the whole sequence as one CUDA graph            */
     QS_FLAG_OUT_DEVICE = 4,  /* energy / grad / expectation outputs are device pointers */
     QS_FLAG_MASKED = 8,      /* qs_apply_circuit: baseline schedule (comparator only)   */
-    QS_FLAG_JIT = 16         /* with QS_FLAG_FUSE: tile passes as kernels compiled for
+    QS_FLAG_JIT = 16,        /* with QS_FLAG_FUSE: tile passes as kernels compiled for
                                 their exact shape (see qs_circuit_compile)             */
+    QS_FLAG_ADJOINT = 32     /* qs_circuit_schedule: the launches of qs_adjoint_grad   */
 };
 
 /* One gate (96 bytes, naturally aligned). Section III-A: target t, controls, matrix. */
@@ -171,7 +172,9 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count,
 
 /* The launch schedule qs_apply_circuit would use for `count` gates on an n-qubit state of
  * precision `dtype` with `flags`, computed on the host: no state, device or CUDA call is
- * needed. Gates and flags are validated as by qs_apply_circuit (QS_EINVAL, nothing filled).
+ * needed. With QS_FLAG_ADJOINT: the schedule of qs_adjoint_grad with the other flags (forward
+ * program, energy and lambda, reverse sweep over psi and lambda: a sweep launch moves both
+ * vectors, so it counts twice in algorithmic_bytes and model_cost). Gates and flags are validated as by qs_apply_circuit (QS_EINVAL, nothing filled).
  * With QS_FLAG_FUSE this is the fusion planner's result (gate fusion is the optimisation
  * the paper's conclusion proposes): the gates, after same-target merging, cut into single
  * launches, tile passes and diagonal runs of least modelled cost. model_cost is that cost
@@ -188,11 +191,22 @@ typedef struct {
     int32_t gates;         /* gates after same-target merging (identities included) */
     int32_t pass_gates;    /* gates applied inside tile passes */
     double model_cost;
+    double algorithmic_bytes; /* bytes the launches must read + write: per single gate its
+                                 selected amplitudes (2 * 2^(n-c) * s), per tile pass the
+                                 tiles one of its gates selects (2 * fraction * 2^n * s),
+                                 per diagonal run the chunks it can change */
 } qs_schedule;
 
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
                               const double *theta, size_t n_theta, int flags,
                               qs_schedule *out);
+
+/* Measured FMA rate of the current device in the arithmetic of `dtype` (QS_C64: float32,
+ * QS_C128: float64), in flop/s (2 per FMA): one launch of independent FMA chains on every SM
+ * for `iters` iterations (1 .. 2^24), timed with CUDA events on `stream`; synchronises the
+ * stream. It is the denominator of the arithmetic rooflines (the complex128 path runs on the
+ * FP64 pipe). Not part of the paper's method. */
+qs_status qs_measure_fma_peak(qs_dtype dtype, int iters, void *stream, double *flops_per_s);
 
 /* Compile the tile-pass kernels that qs_apply_circuit (adjoint = 0) or qs_adjoint_grad
  * (adjoint = 1: the forward and the reverse-sweep programs) would launch for these gates with

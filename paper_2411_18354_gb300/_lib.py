@@ -17,7 +17,7 @@ from .build import LIB_PATH
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
 QS_GATE_U, QS_GATE_X, QS_GATE_RY, QS_GATE_RZ = 0, 1, 2, 3
-QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED, QS_FLAG_JIT = 1, 2, 4, 8, 16
+QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED, QS_FLAG_JIT, QS_FLAG_ADJOINT = 1, 2, 4, 8, 16, 32
 
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EUNSUPPORTED"}
 
@@ -57,6 +57,7 @@ _SIGNATURES = [
                                            ctypes.c_int, _vp]),
     ("qs_circuit_compile", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]),
+    ("qs_measure_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _dp]),
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
     ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
@@ -227,7 +228,7 @@ class QsSchedule(ctypes.Structure):
 
     _fields_ = [("launches", ctypes.c_int32), ("single_gates", ctypes.c_int32), ("tile_passes", ctypes.c_int32),
                 ("diag_runs", ctypes.c_int32), ("gates", ctypes.c_int32), ("pass_gates", ctypes.c_int32),
-                ("model_cost", ctypes.c_double)]
+                ("model_cost", ctypes.c_double), ("algorithmic_bytes", ctypes.c_double)]
 
 
 def qs_circuit_schedule(n: int, dtype: int, gates, theta=None, flags: int = 0) -> dict:
@@ -250,6 +251,13 @@ def qs_circuit_compile(n: int, dtype: int, gates, theta=None, flags: int = QS_FL
     _check(lib().qs_circuit_compile(n, dtype, gp, g.size, tp, nt, flags, 1 if adjoint else 0, ctypes.byref(secs),
                                     ctypes.byref(passes)))
     return {"compile_seconds": secs.value, "passes": passes.value}
+
+
+def qs_measure_fma_peak(dtype: int, iters: int = 1 << 16, stream: int = 0) -> float:
+    """Measured FMA rate (flop/s) of the current device in the arithmetic of ``dtype``."""
+    out = ctypes.c_double(0.0)
+    _check(lib().qs_measure_fma_peak(dtype, iters, _vp(stream or None), ctypes.byref(out)))
+    return out.value
 
 
 def qs_expect_z(h: int, flags: int = 0, out=None, out_norm2=None):

@@ -122,6 +122,14 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
     return h;
 }
 
+// Bytes one single-gate launch must move: every selected amplitude read and written
+// (2 * 2^(n-c) * s); a one-sided diagonal gate touches only its changed side.
+static double gate_algorithmic_bytes(const GatePlan &p, int dtype) {
+    const double s = dtype == QS_C64 ? 8.0 : 16.0;
+    const double b = 2.0 * std::ldexp(s, p.n - __builtin_popcountll(p.ctrl_mask));
+    return p.op == OP_SIDE ? 0.5 * b : b;
+}
+
 static int tile_bits(int dtype, bool adjoint);
 
 // The bytes a recorded graph depends on: the gate records, the parameters, the flags, the
@@ -376,13 +384,16 @@ static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, 
     if (fuse) {
         std::vector<int> seq(fwd.size());
         for (size_t i = 0; i < fwd.size(); ++i) seq[i] = (int)i;
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &ap->pf);
+        const bool jit = (flags & QS_FLAG_JIT) != 0;
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &ap->pf, kPassMaxGates, true,
+                   0, jit);
         seq.resize(count);
         for (size_t i = 0; i < count; ++i) {
             seq[i] = (int)(count - 1 - i);
             if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
         }
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &ap->dusp, &slot_of, &ap->pa);
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &ap->dusp, &slot_of, &ap->pa, kPassMaxGates,
+                   true, 0, jit);
     }
     return true;
 }
@@ -407,19 +418,75 @@ qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits) {
 
 int qs_get_tile_bits(qs_dtype dtype, int adjoint) { return tile_bits(dtype, adjoint != 0); }
 
+// The launches of qs_adjoint_grad: the forward program, the energy reduction and lambda = O psi
+// (one read of psi; one read of psi and a write of lambda), the reverse sweep over psi and lambda
+// (a sweep step or pass reads and writes both vectors), the gradient sums.
+static qs_status adjoint_schedule(const qs_state *shape, const qs_gate *gates, size_t count, const double *theta,
+                                  size_t n_theta, int flags, qs_schedule *out) {
+    AdjPlan ap;
+    char err[256];
+    if (!plan_adjoint(shape, gates, count, theta, n_theta, flags, &ap, err, sizeof(err)))
+        return set_error(QS_EINVAL, err);
+    qs_schedule r;
+    std::memset(&r, 0, sizeof(r));
+    const int n = shape->n, dtype = shape->dtype;
+    const double state_bytes = std::ldexp(dtype == QS_C64 ? 8.0 : 16.0, n);
+    r.gates = (int32_t)(ap.fwd.size() + ap.adj.size());
+    auto add_program = [&](const FusedProgram &prog, const std::vector<GatePlan> &plans, double vectors) {
+        r.model_cost += prog.model_cost * vectors;
+        for (const TilePass &P : prog.passes) r.pass_gates += P.gate_count;
+        for (const FusedOp &op : prog.ops) {
+            if (op.drun >= 0) {
+                ++r.diag_runs;
+                r.algorithmic_bytes += vectors * state_bytes * std::ldexp(2.0, -prog.druns[op.drun].nc.nfix);
+            } else if (op.pass >= 0) {
+                ++r.tile_passes;
+                r.algorithmic_bytes += vectors * 2.0 * state_bytes * pass_touched_fraction(prog, op.pass);
+            } else {
+                ++r.single_gates;
+                r.algorithmic_bytes += vectors * gate_algorithmic_bytes(plans[op.gate], dtype);
+            }
+        }
+    };
+    if (flags & QS_FLAG_FUSE) {
+        add_program(ap.pf, ap.fwd, 1.0);
+        add_program(ap.pa, ap.adj, 2.0);
+    } else {
+        for (const auto *pl : {&ap.fwd, &ap.adj}) {
+            const double vectors = pl == &ap.adj ? 2.0 : 1.0;
+            for (const GatePlan &p : *pl) {
+                if (p.units == 0 && pl == &ap.fwd) continue;
+                ++r.single_gates;
+                // a sweep step of a parameterised gate reads both sides even when it is diagonal
+                const double b = p.op == OP_SIDE && pl == &ap.fwd ? 0.5 : 1.0;
+                r.algorithmic_bytes += vectors * b * 2.0 * std::ldexp(dtype == QS_C64 ? 8.0 : 16.0,
+                                                                      n - __builtin_popcountll(p.ctrl_mask));
+                r.model_cost += vectors * (single_launch_cost(p, dtype) + launch_latency_cost(n, dtype));
+            }
+        }
+    }
+    r.algorithmic_bytes += 3.0 * state_bytes;  // energy: read psi; lambda = O psi: read psi, write lambda
+    r.launches = r.single_gates + r.tile_passes + r.diag_runs + 4;  // + reductions, lambda, gradient sums
+    *out = r;
+    return QS_OK;
+}
+
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count, const double *theta,
                               size_t n_theta, int flags, qs_schedule *out) {
     if (!out) return set_error(QS_EINVAL, "qs_circuit_schedule: out is NULL");
     if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_circuit_schedule: bad dtype");
     if (n < 1 || n > kMaxQubits) return set_error(QS_EINVAL, "qs_circuit_schedule: n out of range");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_circuit_schedule: gates is NULL");
-    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED | QS_FLAG_JIT))
+    if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED | QS_FLAG_JIT | QS_FLAG_ADJOINT))
         return set_error(QS_EINVAL, "qs_circuit_schedule: unknown flags");
     if ((flags & QS_FLAG_FUSE) && (flags & QS_FLAG_MASKED))
         return set_error(QS_EINVAL, "qs_circuit_schedule: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
+    if ((flags & QS_FLAG_ADJOINT) && (flags & QS_FLAG_MASKED))
+        return set_error(QS_EINVAL, "qs_circuit_schedule: QS_FLAG_MASKED cannot be combined with QS_FLAG_ADJOINT");
     qs_state shape;  // planning reads only the state's size and precision
     shape.n = n;
     shape.dtype = dtype;
+    if (flags & QS_FLAG_ADJOINT) return adjoint_schedule(&shape, gates, count, theta, n_theta, flags, out);
     std::vector<GatePlan> plans(count);
     char err[256];
     for (size_t i = 0; i < count; ++i)
@@ -430,11 +497,13 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
     qs_schedule r;
     std::memset(&r, 0, sizeof(r));
     r.gates = (int32_t)plans.size();
+    const double state_bytes = std::ldexp(dtype == QS_C64 ? 8.0 : 16.0, n);
     if (flags & QS_FLAG_FUSE) {
         std::vector<int> seq(plans.size());
         for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
         FusedProgram prog;
-        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog);
+        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true, 0,
+                   (flags & QS_FLAG_JIT) != 0);
         for (const FusedOp &op : prog.ops) {
             if (op.drun >= 0)
                 ++r.diag_runs;
@@ -445,11 +514,20 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
         }
         for (const TilePass &P : prog.passes) r.pass_gates += P.gate_count;
         r.model_cost = prog.model_cost;
+        for (const FusedOp &op : prog.ops) {
+            if (op.drun >= 0)
+                r.algorithmic_bytes += state_bytes * std::ldexp(2.0, -prog.druns[op.drun].nc.nfix);
+            else if (op.pass >= 0)
+                r.algorithmic_bytes += 2.0 * state_bytes * pass_touched_fraction(prog, op.pass);
+            else
+                r.algorithmic_bytes += gate_algorithmic_bytes(plans[op.gate], dtype);
+        }
     } else {
         for (const GatePlan &p : plans) {
             if (p.units == 0) continue;
             ++r.single_gates;
             r.model_cost += (masked ? 1.0 : single_launch_cost(p, dtype)) + launch_latency_cost(n, dtype);
+            r.algorithmic_bytes += masked ? 2.0 * state_bytes : gate_algorithmic_bytes(p, dtype);
         }
     }
     r.launches = r.single_gates + r.tile_passes + r.diag_runs;
@@ -473,7 +551,7 @@ qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t
     std::vector<GatePlan> plans;
     FusedProgram prog;
     AdjPlan ap;
-    const int fl = flags | QS_FLAG_FUSE;
+    const int fl = flags | QS_FLAG_FUSE | QS_FLAG_JIT;
     if (!adjoint) {
         plans.resize(count);
         for (size_t i = 0; i < count; ++i)
@@ -482,7 +560,8 @@ qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t
         merge_runs(&shape, plans);
         std::vector<int> seq(plans.size());
         for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
-        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog);
+        plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true, 0,
+                   (fl & QS_FLAG_JIT) != 0);
         progs.push_back(&prog);
         adj_of.push_back(false);
     } else {
@@ -556,7 +635,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     if (fuse) {
         std::vector<int> seq(plans.size());  // after merging: fewer plans than records
         for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog);
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true,
+                   0, (flags & QS_FLAG_JIT) != 0);
     }
     std::vector<JitPass> jit;
     if (flags & QS_FLAG_JIT) {

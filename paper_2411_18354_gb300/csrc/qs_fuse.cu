@@ -285,8 +285,16 @@ static void make_pass(int n, uint64_t Lmask, TilePass *P) {
 // 0.15 fits the measured plans best. complex128 gates are FP64-bound alone and inside a pass
 // alike (a general 2x2 costs ~3 units either way), so only exchanges (no arithmetic, ~0.33)
 // gain from a pass.
-static double pass_gate_cost(int dtype, const GatePlan &p) {
-    if (dtype == QS_C64) return 0.15;
+static double pass_gate_cost(int dtype, const GatePlan &p, bool jit) {
+    if (dtype == QS_C64 && !jit) return 0.15;
+    if (dtype == QS_C64) {
+        // passes compiled for their shape (QS_FLAG_JIT), measured at n = 24 in units of one
+        // state read + write (45 us): general 2x2 5.8 us, real 2.8, exchange 1.8, diagonal and
+        // one-sided less; a gate computes only the pairs its controls select (in-row controls
+        // skip the arithmetic, row predicates most of it)
+        double c = p.op == OP_GEN ? 0.13 : p.op == OP_REAL ? 0.065 : p.op == OP_SWAP ? 0.04 : 0.035;
+        return c * std::max(std::ldexp(1.0, -popc(p.ctrl_mask)), 0.125);
+    }
     return p.op == OP_SWAP ? 0.33 : 3.0;
 }
 
@@ -296,7 +304,7 @@ static double diag_run_gate_cost(int dtype) { return dtype == QS_C64 ? 0.005 : 0
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates, bool allow_single, int group_bits) {
+                int max_gates, bool allow_single, int group_bits, bool jit) {
     prog->ops.clear();
     prog->passes.clear();
     prog->gates.clear();
@@ -330,7 +338,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
                 if (popc(L2) > k) break;
                 if (param && nparam >= kTileMaxParam) break;
                 frac = std::min(1.0, frac + std::ldexp(1.0, -popc(p.ctrl_mask & ~L2)));
-                compute += pass_gate_cost(dtype, p);
+                compute += pass_gate_cost(dtype, p, jit) * (param && jit ? 1.5 : 1.0);
                 L = L2;
                 nparam += param;
                 ++real;
@@ -516,6 +524,55 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
         }
     }
     return true;
+}
+
+// Fraction of the assignments of the non-local bits that satisfy at least one of the terms
+// (mask, vals): split on one bit at a time (Shannon expansion), dropping terms a shorter one
+// subsumes. Exact unless more than `budget` nodes are visited; then the union bound.
+static double union_fraction(std::vector<std::pair<uint64_t, uint64_t>> terms, long *budget) {
+    if (terms.empty()) return 0.0;
+    for (auto &t : terms)
+        if (t.first == 0) return 1.0;
+    if (--*budget < 0) {
+        double u = 0.0;
+        for (auto &t : terms) u += std::ldexp(1.0, -popc(t.first));
+        return std::min(1.0, u);
+    }
+    // drop duplicates and subsumed terms (t1's literals a subset of t2's: t2 adds nothing)
+    std::vector<std::pair<uint64_t, uint64_t>> keep;
+    for (size_t i = 0; i < terms.size(); ++i) {
+        bool drop = false;
+        for (size_t j = 0; j < terms.size() && !drop; ++j) {
+            if (i == j) continue;
+            const auto &a = terms[j], &b = terms[i];
+            const bool subset = (a.first & ~b.first) == 0 && (b.second & a.first) == a.second;
+            if (subset && (a.first != b.first || j < i)) drop = true;
+        }
+        if (!drop) keep.push_back(terms[i]);
+    }
+    const uint64_t bit = keep[0].first & (~keep[0].first + 1);
+    std::vector<std::pair<uint64_t, uint64_t>> t0, t1;
+    for (auto &t : keep) {
+        if (!(t.first & bit)) {
+            t0.push_back(t);
+            t1.push_back(t);
+        } else if (t.second & bit) {
+            t1.push_back({t.first & ~bit, t.second & ~bit});
+        } else {
+            t0.push_back({t.first & ~bit, t.second & ~bit});
+        }
+    }
+    return 0.5 * (union_fraction(std::move(t0), budget) + union_fraction(std::move(t1), budget));
+}
+
+double pass_touched_fraction(const FusedProgram &prog, int pass) {
+    const TilePass &P = prog.passes[pass];
+    if (!P.hctrl) return 1.0;
+    std::vector<std::pair<uint64_t, uint64_t>> terms;
+    for (int g = P.gate_begin; g < P.gate_begin + P.gate_count; ++g)
+        terms.push_back({prog.gates[g].hmask, prog.gates[g].hvals});
+    long budget = 200000;
+    return union_fraction(std::move(terms), &budget);
 }
 
 static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }

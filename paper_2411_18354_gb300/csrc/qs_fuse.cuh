@@ -35,6 +35,10 @@ struct FusedProgram {
 double single_launch_cost(const GatePlan &p, int dtype);
 double launch_latency_cost(int n, int dtype);
 
+// Fraction of the tiles pass `pass` reads and writes: those at least one of its gates selects
+// (all of them when exchanges are folded into its row copies).
+double pass_touched_fraction(const FusedProgram &prog, int pass);
+
 // Byte size and packing of a program's device table: groups, then gates, then the diagonal
 // runs' gates (each part 16-byte aligned).
 size_t program_table_bytes(const FusedProgram &p);
@@ -51,10 +55,12 @@ const DiagGate *table_dgates(const FusedProgram &p, const void *dev_base);
 // goes into a pass, also when the pass holds only that gate.
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates = kPassMaxGates, bool allow_single = true, int group_bits = 0);
+                int max_gates = kPassMaxGates, bool allow_single = true, int group_bits = 0, bool jit = false);
 // group_bits: register qubits per group; 0 = kGroupBits for forward programs and
 // kGroupBitsAdjoint when dus != nullptr. The kernel that runs the program must use the same.
 // Forward programs with allow_single (not the batched kernel) may also put consecutive
 // diagonal gates, optionally after one uncontrolled gate, into diagonal-run ops.
+// jit: the passes will run as kernels compiled for their shape (QS_FLAG_JIT), whose per-gate
+// cost is lower (and depends on the gate's operation), so passes may hold more gates.
 
 }  // namespace qs

@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -367,6 +368,46 @@ struct Module {
 std::mutex g_mu;
 std::vector<std::unique_ptr<Module>> g_modules;
 std::unordered_map<std::string, std::pair<int, int>> g_by_source;  // kernel source -> (module, kernel)
+std::unordered_map<std::string, std::pair<int, int>> g_by_shape;   // shape key -> (module, kernel)
+
+// Everything a pass's generated source depends on, as bytes (the matrices excluded): looking
+// this up costs far less than generating the source, so a repeated circuit finds its kernels
+// without writing them again.
+std::string shape_key(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups, const RegGate *gates) {
+    std::string k;
+    auto put = [&k](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
+    const int hdr[4] = {dtype, adjoint ? 1 : 0, P.gate_count, P.group_count};
+    put(hdr, sizeof(hdr));
+    put(&P.n, sizeof(P.n));
+    put(&P.k, sizeof(P.k));
+    put(&P.nruns, sizeof(P.nruns));
+    put(P.run_src, sizeof(P.run_src));
+    put(P.run_len, sizeof(P.run_len));
+    put(P.run_dst, sizeof(P.run_dst));
+    put(P.tmask, sizeof(P.tmask));
+    put(P.tshift, sizeof(P.tshift));
+    put(&P.tnseg, sizeof(P.tnseg));
+    put(&P.ntiles, sizeof(P.ntiles));
+    put(&P.hctrl, sizeof(P.hctrl));
+    put(&P.nparam, sizeof(P.nparam));
+    for (int i = 0; i < P.group_count; ++i) {
+        TileGroup g = groups[P.group_begin + i];
+        g.gate_begin -= P.gate_begin;
+        put(&g, sizeof(g));
+    }
+    for (int i = 0; i < P.gate_count; ++i) {
+        const RegGate &g = gates[P.gate_begin + i];
+        put(&g.p, 4);  // p, cqm, cqv, pad0
+        put(&g.crm, sizeof(g.crm));
+        put(&g.crv, sizeof(g.crv));
+        put(&g.op, sizeof(g.op));
+        put(&g.side, sizeof(g.side));
+        put(&g.slot, sizeof(g.slot));
+        put(&g.hmask, sizeof(g.hmask));
+        put(&g.hvals, sizeof(g.hvals));
+    }
+    return k;
+}
 
 bool compile_cubin(const std::string &src, std::vector<char> *cubin, std::string *err) {
     nvrtcProgram prog;
@@ -408,52 +449,100 @@ bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std:
     if (compile_seconds) *compile_seconds = 0.0;
     if (compiled_modules) *compiled_modules = 0;
     const size_t es = dtype == QS_C64 ? 8 : 16, rs = dtype == QS_C64 ? 4 : 8;
-    // one source per pass (kernel name fixed: the source text alone keys the cache)
-    std::vector<std::string> srcs(prog.passes.size());
-    for (size_t p = 0; p < prog.passes.size(); ++p)
-        srcs[p] = jit_pass_source(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data(), "qs_pass");
+    // one source per pass (kernel name fixed: the source text alone keys the cache); a pass
+    // whose shape was seen before takes its source from the shape cache
+    std::vector<std::string> srcs(prog.passes.size()), keys(prog.passes.size());
+    std::vector<char> known(prog.passes.size(), 0);
     std::lock_guard<std::mutex> lock(g_mu);
+    for (size_t p = 0; p < prog.passes.size(); ++p) {
+        keys[p] = shape_key(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data());
+        if (g_by_shape.count(keys[p])) {
+            known[p] = 1;
+            continue;
+        }
+        srcs[p] = jit_pass_source(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data(), "qs_pass");
+    }
     // passes whose source is not cached yet go into one new module (renamed kernels)
     std::vector<int> missing;
     std::unordered_map<std::string, int> first_of;
     for (size_t p = 0; p < srcs.size(); ++p) {
-        if (g_by_source.count(srcs[p])) continue;
+        if (known[p] || g_by_source.count(srcs[p])) continue;
         if (first_of.count(srcs[p])) continue;
         first_of[srcs[p]] = (int)p;
         missing.push_back((int)p);
     }
     if (!missing.empty()) {
         auto t0 = std::chrono::steady_clock::now();
-        auto m = std::make_unique<Module>();
-        // each pass source is self-contained; a module concatenates them inside namespaces
-        for (size_t i = 0; i < missing.size(); ++i) {
-            const std::string nm = "qs_pass_" + std::to_string(i);
-            std::string s = srcs[missing[i]];
-            const size_t at = s.find(" qs_pass(");
-            s.replace(at, 9, " " + nm + "(");
-            m->source += "namespace m" + std::to_string(i) + " {\n" + s + "}\n";
-            m->names.push_back(nm);
+        // split the new kernels into modules compiled concurrently (NVRTC is thread-safe):
+        // contiguous chunks of about equal source size, one per hardware thread at most
+        size_t total = 0;
+        for (int p : missing) total += srcs[p].size();
+        unsigned hw = std::thread::hardware_concurrency();
+        if (hw == 0) hw = 4;
+        const size_t nmod = std::max<size_t>(1, std::min<size_t>({(size_t)hw, missing.size(), 32}));
+        std::vector<std::unique_ptr<Module>> mods;
+        std::vector<std::vector<int>> members;
+        {
+            size_t acc = 0, cur = 0;
+            mods.push_back(std::make_unique<Module>());
+            members.emplace_back();
+            for (size_t i = 0; i < missing.size(); ++i) {
+                const std::string &src = srcs[missing[i]];
+                if (acc >= (cur + 1) * total / nmod && !members.back().empty() && cur + 1 < nmod) {
+                    ++cur;
+                    mods.push_back(std::make_unique<Module>());
+                    members.emplace_back();
+                }
+                Module &m = *mods.back();
+                const size_t idx = m.names.size();
+                const std::string nm = "qs_pass_" + std::to_string(idx);
+                std::string s2 = src;
+                const size_t at = s2.find(" qs_pass(");
+                s2.replace(at, 9, " " + nm + "(");
+                m.source += "namespace m" + std::to_string(idx) + " {\n" + s2 + "}\n";
+                m.names.push_back(nm);
+                members.back().push_back(missing[i]);
+                acc += src.size();
+            }
         }
         // QS_JIT_DUMP=<directory>: write each compiled module's source there (diagnostics)
         if (const char *dir = std::getenv("QS_JIT_DUMP")) {
             if (*dir) {
-                const std::string path = std::string(dir) + "/qs_jit_module_" + std::to_string(g_modules.size()) + ".cu";
-                if (FILE *f = std::fopen(path.c_str(), "w")) {
-                    std::fwrite(m->source.data(), 1, m->source.size(), f);
-                    std::fclose(f);
+                for (size_t i = 0; i < mods.size(); ++i) {
+                    const std::string path =
+                        std::string(dir) + "/qs_jit_module_" + std::to_string(g_modules.size() + i) + ".cu";
+                    if (FILE *f = std::fopen(path.c_str(), "w")) {
+                        std::fwrite(mods[i]->source.data(), 1, mods[i]->source.size(), f);
+                        std::fclose(f);
+                    }
                 }
             }
         }
-        if (!compile_cubin(m->source, &m->cubin, err)) return false;
-        const int mi = (int)g_modules.size();
-        for (size_t i = 0; i < missing.size(); ++i) g_by_source[srcs[missing[i]]] = {mi, (int)i};
-        g_modules.push_back(std::move(m));
+        std::vector<std::string> errs(mods.size());
+        std::vector<char> ok(mods.size(), 0);
+        {
+            std::vector<std::thread> th;
+            for (size_t i = 0; i < mods.size(); ++i)
+                th.emplace_back([&, i] { ok[i] = compile_cubin(mods[i]->source, &mods[i]->cubin, &errs[i]) ? 1 : 0; });
+            for (auto &t : th) t.join();
+        }
+        for (size_t i = 0; i < mods.size(); ++i)
+            if (!ok[i]) {
+                *err = errs[i];
+                return false;
+            }
+        for (size_t i = 0; i < mods.size(); ++i) {
+            const int mi = (int)g_modules.size();
+            for (size_t j = 0; j < members[i].size(); ++j) g_by_source[srcs[members[i][j]]] = {mi, (int)j};
+            g_modules.push_back(std::move(mods[i]));
+        }
         if (compile_seconds)
             *compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (compiled_modules) *compiled_modules = 1;
+        if (compiled_modules) *compiled_modules = (int)mods.size();
     }
     for (size_t p = 0; p < srcs.size(); ++p) {
-        const auto &mk = g_by_source.at(srcs[p]);
+        if (!known[p]) g_by_shape[keys[p]] = g_by_source.at(srcs[p]);
+        const auto &mk = g_by_shape.at(keys[p]);
         JitPass &j = (*out)[p];
         j.entry = mk.first;
         j.kernel = mk.second;
