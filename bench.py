@@ -57,6 +57,9 @@ def parse_args():
                     help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
     ap.add_argument("--ncu-qft", action="store_true",
                     help="profiling case: the fused QFT (29 qubits, or --n), twice (diagonal-run passes)")
+    ap.add_argument("--jit", action="store_true",
+                    help="profiling cases --ncu-fused / --ncu-qft: tile passes compiled for their shape (QS_FLAG_JIT), "
+                         "compiled before the profiled launches")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="small profiling case: one batch launch of 304 states (n=16, 2 layers of the ansatz)")
     return ap.parse_args()
@@ -340,9 +343,9 @@ def _compile(qs, n, gates, theta, dtype, adjoint=False):
 def _reset_tile_bits(qs):
     """Back to the library's default tile sizes, so that no measurement inherits the tile size
     another one tuned (the autotuner applies its choice process-wide)."""
-    for dt in (qs.QS_C64, qs.QS_C128):
-        for adj in (0, 1):
-            qs.qs_set_tile_bits(dt, adj, 0)
+    from paper_2411_18354_gb300 import autotune
+
+    autotune.restore_defaults()
 
 
 def measure_fused(qs, W, peak):
@@ -817,9 +820,12 @@ def run_ncu_fused(args):
     n, layers = 24, 2
     g = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
+    flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if args.jit else 0)
+    if args.jit:
+        _compile(qs, n, g, th, args.dtype, adjoint=True)
     with qs.State(n, args.dtype) as st:
-        st.apply_circuit(g, th, qs.QS_FLAG_FUSE)
-        st.adjoint_grad(g, th, qs.QS_FLAG_FUSE)
+        st.apply_circuit(g, th, flags)
+        st.adjoint_grad(g, th, flags)
         torch.cuda.synchronize()
     print("ncu fused case done")
 
@@ -919,9 +925,12 @@ def run_ncu_qft(args):
     qs.build()
     n = args.n if args.n != 30 else 29
     g = W.qft_circuit(n)
+    flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if args.jit else 0)
+    if args.jit:
+        _compile(qs, n, g, None, "c64")
     with qs.State(n, "c64") as st:
         for _ in range(2):
-            st.apply_circuit(g, flags=qs.QS_FLAG_FUSE)
+            st.apply_circuit(g, flags=flags)
         torch.cuda.synchronize()
     print("ncu qft case done")
 

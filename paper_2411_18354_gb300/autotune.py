@@ -83,38 +83,95 @@ def _time(fn, reps: int) -> float:
     return best
 
 
+def _dt(dtype) -> int:
+    return _lib.QS_C64 if dtype in ("c64", "complex64", _lib.QS_C64) else _lib.QS_C128
+
+
+def _set_bits(dt: int, adjoint: int, bits: int) -> None:
+    """qs_set_tile_bits, falling back to the library default for a value it rejects (one that
+    came from the QS_TILE_BITS override, which allows smaller tiles)."""
+    try:
+        _lib.qs_set_tile_bits(dt, adjoint, bits)
+    except _lib.QsError:
+        _lib.qs_set_tile_bits(dt, adjoint, 0)
+
+
+def restore_defaults() -> None:
+    """Back to the library's default tile sizes for both precisions and directions (undoes
+    every tile size the tuner applied in this process)."""
+    for dt in (_lib.QS_C64, _lib.QS_C128):
+        for adj in (0, 1):
+            _lib.qs_set_tile_bits(dt, adj, 0)
+
+
 def tune_fused(n: int, dtype: str, gates, theta=None, adjoint: bool = False, candidates=FUSED_CANDIDATES,
-               reps: int = 2, use_cache: bool = True) -> dict:
-    """Pick the tile size of the fused passes for this circuit; applies it process-wide."""
-    from . import GATE_DTYPE, QS_FLAG_FUSE, State, as_gate_array
+               reps: int = 2, use_cache: bool = True, flags: int = 0, apply: bool = True) -> dict:
+    """Pick the tile size of the fused passes for this circuit by timing each candidate with
+    QS_FLAG_FUSE (| flags, e.g. QS_FLAG_JIT). With apply=True the choice is applied
+    process-wide (qs_set_tile_bits); with apply=False the setting in force before the call is
+    put back. Candidates the library rejects for the precision and direction are skipped."""
+    from . import QS_FLAG_FUSE, State, as_gate_array
 
     g = as_gate_array(gates)
-    dt = _lib.QS_C64 if dtype in ("c64", "complex64") else _lib.QS_C128
-    key = f"{_device_key()}|fused|{dtype}|{int(adjoint)}|n{n}|{_sig(g['target'], g['ctrl_mask'], g['kind'])}"
+    dt = _dt(dtype)
+    fl = QS_FLAG_FUSE | flags
+    key = f"{_device_key()}|fused|{dtype}|{int(adjoint)}|f{fl}|n{n}|{_sig(g['target'], g['ctrl_mask'], g['kind'])}"
+    prev = _lib.qs_get_tile_bits(dt, int(adjoint))
     cache = _load() if use_cache else {}
     if key in cache:
-        _lib.qs_set_tile_bits(dt, int(adjoint), int(cache[key]["tile_bits"]))
+        if apply:
+            _lib.qs_set_tile_bits(dt, int(adjoint), int(cache[key]["tile_bits"]))
         return dict(cache[key], cached=True)
     results = {}
-    with State(n, dtype) as st:
-        for k in candidates:
-            try:
-                _lib.qs_set_tile_bits(dt, int(adjoint), k)
-            except _lib.QsError:  # a tile whose block does not fit this precision / direction
-                continue
-            if adjoint:
-                fn = lambda: (st.set_basis(0), st.adjoint_grad(g, theta, QS_FLAG_FUSE))  # noqa: E731
-            else:
-                fn = lambda: st.apply_circuit(g, theta, QS_FLAG_FUSE)  # noqa: E731
-            results[k] = _time(fn, reps)
+    try:
+        with State(n, dtype) as st:
+            for k in candidates:
+                try:
+                    _lib.qs_set_tile_bits(dt, int(adjoint), k)
+                except _lib.QsError:  # a tile whose block does not fit this precision / direction
+                    continue
+                if adjoint:
+                    fn = lambda: (st.set_basis(0), st.adjoint_grad(g, theta, fl))  # noqa: E731
+                else:
+                    fn = lambda: st.apply_circuit(g, theta, fl)  # noqa: E731
+                results[k] = _time(fn, reps)
+    finally:
+        _set_bits(dt, int(adjoint), prev)
+    if not results:
+        raise RuntimeError("tune_fused: no candidate tile size is valid for this precision and direction")
     best = min(results, key=results.get)
-    _lib.qs_set_tile_bits(dt, int(adjoint), best)
+    if apply:
+        _lib.qs_set_tile_bits(dt, int(adjoint), best)
     entry = {"tile_bits": best, "seconds": results[best], "tried": {str(k): v for k, v in results.items()}}
     if use_cache:
         cache = _load()
         cache[key] = entry
         _save(cache)
     return dict(entry, cached=False)
+
+
+class tuned_tile_bits:
+    """Context manager: tune (or take from the cache) and apply the tile size of the fused
+    passes for this circuit; on exit the tile size in force before is restored.
+
+        with autotune.tuned_tile_bits(n, "c64", gates, theta) as choice:
+            state.apply_circuit(gates, theta, QS_FLAG_FUSE)
+    """
+
+    def __init__(self, n, dtype, gates, theta=None, adjoint=False, **kw):
+        self.args = (n, dtype, gates, theta, adjoint)
+        self.kw = kw
+        self.dt = _dt(dtype)
+        self.adjoint = int(adjoint)
+
+    def __enter__(self):
+        self.prev = _lib.qs_get_tile_bits(self.dt, self.adjoint)
+        n, dtype, gates, theta, adjoint = self.args
+        return tune_fused(n, dtype, gates, theta, adjoint, apply=True, **self.kw)
+
+    def __exit__(self, *exc):
+        _set_bits(self.dt, self.adjoint, self.prev)
+        return False
 
 
 def tune_batch(n_qubits, circuits, n_params, thetas, dtype: str = "c64", candidates=BATCH_CANDIDATES,

@@ -183,3 +183,27 @@ def test_device_outputs_and_autograd(qs):
     E.backward()
     assert abs(E.item() - e_host) <= 1e-12
     assert np.max(np.abs(theta.grad.cpu().numpy() - g_host)) <= 1e-12
+
+
+def test_autograd_reuses_its_state_across_steps(qs):
+    """Several optimisation steps through AdjointEnergy (compiled passes): each step's energy
+    and gradient match the oracle's parameter shift, the working state is created once, and a
+    step after an update starts again from |0...0> (no drift from the previous step)."""
+    import torch
+
+    from paper_2411_18354_gb300 import autograd as ag
+
+    n, layers = 7, 2
+    gates = W.hea_circuit(n, layers)
+    theta = torch.tensor(W.hea_params(n, layers, seed=9), dtype=torch.float64, device="cuda", requires_grad=True)
+    before = len(ag._STATES)
+    for step in range(3):
+        theta.grad = None
+        E = ag.AdjointEnergy.apply(theta, n, gates, "c64", qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)
+        E.backward()
+        th = theta.detach().cpu().numpy()
+        assert abs(E.item() - oracle.energy(n, gates, th)) <= 1e-5, step
+        assert np.max(np.abs(theta.grad.cpu().numpy() - oracle.param_shift_grad(n, gates, th))) <= 1e-4, step
+        with torch.no_grad():
+            theta -= 0.1 * theta.grad
+    assert len(ag._STATES) <= before + 1
