@@ -90,8 +90,9 @@ void preamble(Out &o, bool dbl) {
     o.f("__device__ __forceinline__ void cp16(void *s, const void *g) {\n"
         "  asm volatile(\"cp.async.cg.shared.global [%%0], [%%1], 16;\\n\" :: \"r\"((u32)__cvta_generic_to_shared(s)), "
         "\"l\"(g) : \"memory\");\n}\n");
-    o.f("__device__ __forceinline__ void cpwait() {\n"
-        "  asm volatile(\"cp.async.commit_group;\\ncp.async.wait_group 0;\\n\" ::: \"memory\");\n}\n");
+    o.f("__device__ __forceinline__ void cpcommit() { asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\"); }\n");
+    o.f("__device__ __forceinline__ void cpwait0() { asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\"); }\n");
+    o.f("__device__ __forceinline__ void cpwait1() { asm volatile(\"cp.async.wait_group 1;\\n\" ::: \"memory\"); }\n");
 }
 
 // Expression of the tile swizzle of `a` (the same bijection as tile_swizzle, k_tile.cuh).
@@ -103,8 +104,8 @@ std::string swz_expr(const char *a, int sw) {
 }
 
 // Tile predicate of a set of gates: "" if some gate has no non-local control (every tile
-// is selected), else the condition that one of them selects the tile at `base`.
-std::string any_selects(const RegGate *g, int count) {
+// is selected), else the condition that one of them selects the tile at `bv` (a variable).
+std::string any_selects(const RegGate *g, int count, const char *bv = "base") {
     std::vector<std::pair<uint64_t, uint64_t>> seen;
     std::string c;
     for (int i = 0; i < count; ++i) {
@@ -114,7 +115,7 @@ std::string any_selects(const RegGate *g, int count) {
         if (dup) continue;
         seen.push_back({g[i].hmask, g[i].hvals});
         char b[96];
-        std::snprintf(b, sizeof(b), "%s((base & 0x%llxull) == 0x%llxull)", c.empty() ? "" : " || ",
+        std::snprintf(b, sizeof(b), "%s((%s & 0x%llxull) == 0x%llxull)", c.empty() ? "" : " || ", bv,
                       (unsigned long long)g[i].hmask, (unsigned long long)g[i].hvals);
         c += b;
     }
@@ -152,7 +153,82 @@ void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, int 
     }
 }
 
+// A run of consecutive diagonal gates (diag(a, d) or one side only) in a register group: they
+// commute, so their product is applied at once. The gates are sorted into classes by the
+// element bits their factor depends on (target place, in-row controls); per row, each class
+// multiplies its gates' factors (a for target bit 0, d for bit 1) where the gate's tile and row
+// predicates hold, and each element is then multiplied by the factors of the classes that
+// select it: one complex product per gate and row plus one per selected element and class,
+// instead of one per selected element and gate.
+void emit_diag_run(Out &o, const RegGate *gs, int gi0, int count, int E, bool adjoint) {
+    struct Cls {
+        int p, cqm, cqv;
+        bool has_a = false, has_d = false;
+    };
+    std::vector<Cls> cls;
+    std::vector<int> cls_of(count);
+    for (int i = 0; i < count; ++i) {
+        const RegGate &R = gs[i];
+        int c = -1;
+        for (size_t j = 0; j < cls.size(); ++j)
+            if (cls[j].p == R.p && cls[j].cqm == R.cqm && cls[j].cqv == R.cqv) c = (int)j;
+        if (c < 0) {
+            cls.push_back(Cls{R.p, R.cqm, R.cqv});
+            c = (int)cls.size() - 1;
+        }
+        cls_of[i] = c;
+        const bool a = R.op == OP_DIAG || (R.op == OP_SIDE && R.side == 0);
+        const bool d = R.op == OP_DIAG || (R.op == OP_SIDE && R.side == 1);
+        cls[c].has_a |= a;
+        cls[c].has_d |= d;
+    }
+    o.f("      { // %d diagonal gates in %zu classes\n", count, cls.size());
+    for (size_t c = 0; c < cls.size(); ++c) {
+        if (cls[c].has_a) o.f("        T2 fa%zu; fa%zu.x = 1; fa%zu.y = 0;\n", c, c, c);
+        if (cls[c].has_d) o.f("        T2 fd%zu; fd%zu.x = 1; fd%zu.y = 0;\n", c, c, c);
+    }
+    for (int i = 0; i < count; ++i) {
+        const RegGate &R = gs[i];
+        const int gi = gi0 + i, c = cls_of[i];
+        std::string cond;
+        char t[128];
+        if (R.hmask) {
+            std::snprintf(t, sizeof(t), "((base & 0x%llxull) == 0x%llxull)", (unsigned long long)R.hmask,
+                          (unsigned long long)R.hvals);
+            cond = t;
+        }
+        if (R.crm) {
+            std::snprintf(t, sizeof(t), "%s((ra & 0x%xu) == 0x%xu)", cond.empty() ? "" : " && ", R.crm, R.crv);
+            cond += t;
+        }
+        o.f("        if (%s) {", cond.empty() ? "true" : cond.c_str());
+        if (R.op == OP_DIAG)
+            o.f(" u_mul(fa%d, a.m[%d][0], a.m[%d][1]); u_mul(fd%d, a.m[%d][6], a.m[%d][7]);", c, gi, gi, c, gi, gi);
+        else
+            o.f(" u_mul(f%c%d, a.m[%d][0], a.m[%d][1]);", R.side ? 'd' : 'a', c, gi, gi);
+        o.f(" }\n");
+    }
+    for (int e = 0; e < E; ++e) {
+        for (size_t c = 0; c < cls.size(); ++c) {
+            if ((e & cls[c].cqm) != cls[c].cqv) continue;
+            const bool hi = (e >> cls[c].p) & 1;
+            if (hi ? !cls[c].has_d : !cls[c].has_a) continue;
+            const char f = hi ? 'd' : 'a';
+            o.f("        u_mul(v[%d], f%c%zu.x, f%c%zu.y);\n", e, f, c, f, c);
+            if (adjoint) o.f("        u_mul(w[%d], f%c%zu.x, f%c%zu.y);\n", e, f, c, f, c);
+        }
+    }
+    o.f("      }\n");
+}
+
 }  // namespace
+
+// Two tile buffers per block (the next tile's copies in flight while the current one is
+// computed) where both still leave room for two blocks per SM.
+bool jit_double_buffer(int dtype, bool adjoint, int k) {
+    const size_t tile = (size_t(1) << k) * (dtype == QS_C64 ? 8 : 16) * (adjoint ? 2 : 1);
+    return 2 * tile <= 100 * 1024;
+}
 
 std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups,
                             const RegGate *gates, const char *kname) {
@@ -181,11 +257,13 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     else
         o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, const __grid_constant__ A a) {\n",
             T, minb, kname);
+    const bool db = jit_double_buffer(dtype, adjoint, k);
+    const uint32_t TILE = 1u << k;
+    const uint32_t BUF = (adjoint ? 2 : 1) * TILE;  // one buffer: psi tile (and lambda tile)
     o.f("  extern __shared__ __align__(16) unsigned char sm_[];\n");
-    o.f("  T2 *tp = reinterpret_cast<T2 *>(sm_);\n");
+    o.f("  T2 *const sm0 = reinterpret_cast<T2 *>(sm_);\n");
     if (adjoint) {
-        o.f("  T2 *tl = tp + %u;\n", 1u << k);
-        o.f("  R *acc_s = reinterpret_cast<R *>(tl + %u);\n", 1u << k);
+        o.f("  R *acc_s = reinterpret_cast<R *>(sm0 + %u);\n", (db ? 2 : 1) * BUF);
         o.f("  R *acc_c = acc_s + %d;\n", (NP > 0 ? NP : 1) * (T / 32));
         o.f("  for (int i = threadIdx.x; i < %d; i += %d) { acc_s[i] = 0; acc_c[i] = 0; }\n", (NP > 0 ? NP : 1) * (T / 32), T);
         o.f("  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n");
@@ -206,47 +284,73 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     o.f("  const u32 s_t = swz(o_t);\n");
     const bool cp_guard = nvec < (uint32_t)T;
     o.f("  const u64 ntiles = %lluull;\n", (unsigned long long)P.ntiles);
-    o.f("  for (u64 tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n");
     {
         std::string b = "0ull";
         for (int s = 0; s < P.tnseg; ++s) {
             char t[96];
-            std::snprintf(t, sizeof(t), " | ((tau << %d) & 0x%llxull)", P.tshift[s], (unsigned long long)P.tmask[s]);
+            std::snprintf(t, sizeof(t), " | ((t_ << %d) & 0x%llxull)", P.tshift[s], (unsigned long long)P.tmask[s]);
             b += t;
         }
-        o.f("    const u64 base = %s;\n", b.c_str());
+        o.f("  auto tile_base = [](u64 t_) -> u64 { return %s; };\n", b.c_str());
     }
-    if (P.hctrl) {
-        const std::string c = any_selects(gates + P.gate_begin, G);
-        if (!c.empty()) o.f("    if (!(%s)) continue;\n", c.c_str());
-    }
-    // tile load (asynchronous copies into swizzled shared-memory positions)
+    std::string sel;
+    if (P.hctrl) sel = any_selects(gates + P.gate_begin, G, "b_");
+    if (!sel.empty()) o.f("  auto selected = [](u64 b_) -> bool { return %s; };\n", sel.c_str());
+    // tile copies (asynchronous loads into swizzled shared-memory positions; stores from registers)
     const uint32_t s1 = tile_swizzle(1u, SW);
-    auto copies = [&](bool load, const char *gname, const char *tname) {
+    auto copies = [&](bool load, const char *gname, const char *tname, const char *bname) {
         if (cp_guard) o.f("    if (tid < %uu) {\n", nvec);
         for (uint32_t j = 0; j < steps; ++j) {
             const uint32_t oj = j * T * VEC;
             const unsigned long long gj = (unsigned long long)scatter_host(P, oj);
             const uint32_t sj = tile_swizzle(oj, SW);
             if (load && !dbl)
-                o.f("    { const T2 *g = %s + (base | g_t | 0x%llxull); const u32 s = s_t ^ %uu; "
+                o.f("    { const T2 *g = %s + (%s | g_t | 0x%llxull); const u32 s = s_t ^ %uu; "
                     "cp8(%s + s, g); cp8(%s + (s ^ %uu), g + 1); }\n",
-                    gname, gj, sj, tname, tname, s1);
+                    gname, bname, gj, sj, tname, tname, s1);
             else if (load)
-                o.f("    cp16(%s + (s_t ^ %uu), %s + (base | g_t | 0x%llxull));\n", tname, sj, gname, gj);
+                o.f("    cp16(%s + (s_t ^ %uu), %s + (%s | g_t | 0x%llxull));\n", tname, sj, gname, bname, gj);
             else if (!dbl)
                 o.f("    { const u32 s = s_t ^ %uu; const T2 x0 = %s[s], x1 = %s[s ^ %uu]; T4 q; q.x = x0.x; "
-                    "q.y = x0.y; q.z = x1.x; q.w = x1.y; *reinterpret_cast<T4 *>(%s + (base | g_t | 0x%llxull)) = q; }\n",
-                    sj, tname, tname, s1, gname, gj);
+                    "q.y = x0.y; q.z = x1.x; q.w = x1.y; *reinterpret_cast<T4 *>(%s + (%s | g_t | 0x%llxull)) = q; }\n",
+                    sj, tname, tname, s1, gname, bname, gj);
             else
-                o.f("    %s[base | g_t | 0x%llxull] = %s[s_t ^ %uu];\n", gname, gj, tname, sj);
+                o.f("    %s[%s | g_t | 0x%llxull] = %s[s_t ^ %uu];\n", gname, bname, gj, tname, sj);
         }
         if (cp_guard) o.f("    }\n");
     };
-    auto emit_copies = [&](bool load, const char *gname, const char *tname) { copies(load, gname, tname); };
-    emit_copies(true, "psi", "tp");
-    if (adjoint) emit_copies(true, "lam", "tl");
-    o.f("    cpwait();\n    __syncthreads();\n");
+    auto loads = [&](const char *tname, const char *bname) {
+        o.f("    {\n    T2 *tq = %s;\n", tname);
+        copies(true, "psi", "tq", bname);
+        if (adjoint) {
+            o.f("    T2 *tr = tq + %u;\n", TILE);
+            copies(true, "lam", "tr", bname);
+        }
+        o.f("    }\n    cpcommit();\n");
+    };
+    const char *skip_next = sel.empty() ? "" : "    while (nxt < ntiles && !selected(tile_base(nxt))) nxt += gridDim.x;\n";
+    o.f("  u64 tau = blockIdx.x;\n");
+    if (!sel.empty()) o.f("  while (tau < ntiles && !selected(tile_base(tau))) tau += gridDim.x;\n");
+    o.f("  int cur = 0;\n");
+    if (db) {
+        o.f("  if (tau < ntiles) {\n    const u64 b0 = tile_base(tau);\n");
+        loads("sm0", "b0");
+        o.f("  }\n");
+    }
+    o.f("  while (tau < ntiles) {\n");
+    o.f("    const u64 base = tile_base(tau);\n");
+    o.f("    u64 nxt = tau + gridDim.x;\n%s", skip_next);
+    o.f("    T2 *tp = sm0 + cur * %u;\n", BUF);
+    if (adjoint) o.f("    T2 *tl = tp + %u;\n", TILE);
+    if (db) {
+        o.f("    if (nxt < ntiles) {\n      const u64 nb = tile_base(nxt);\n      T2 *tn = sm0 + (cur ^ 1) * %u;\n", BUF);
+        loads("tn", "nb");
+        o.f("      cpwait1();\n    } else {\n      cpwait0();\n    }\n");
+    } else {
+        loads("tp", "base");
+        o.f("    cpwait0();\n");
+    }
+    o.f("    __syncthreads();\n");
 
     const RegGate *pg = gates + P.gate_begin;
     for (int gi_ = 0; gi_ < P.group_count; ++gi_) {
@@ -295,7 +399,18 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                 if (adjoint) o.f("        w[%d].x = 0; w[%d].y = 0;\n", e, e);
             }
             o.f("      }\n");
+            auto mergeable = [&](int g) {
+                const RegGate &R = pg[gb + g];
+                return (R.op == OP_DIAG || R.op == OP_SIDE) && !(adjoint && R.slot >= 0);
+            };
             for (int g = 0; g < Gr.gate_count; ++g) {
+                if (g + 1 < Gr.gate_count && mergeable(g) && mergeable(g + 1)) {
+                    int h = g;
+                    while (h < Gr.gate_count && mergeable(h)) ++h;
+                    emit_diag_run(o, pg + gb + g, gb + g, h - g, E, adjoint);
+                    g = h - 1;
+                    continue;
+                }
                 const RegGate &R = pg[gb + g];
                 const int gi = gb + g;  // index into a.m
                 const int slot = adjoint ? R.slot : -1;
@@ -334,9 +449,9 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
         }
         o.f("    }\n    __syncthreads();\n");
     }
-    emit_copies(false, "psi", "tp");
-    if (adjoint) emit_copies(false, "lam", "tl");
-    o.f("    __syncthreads();\n  }\n");
+    copies(false, "psi", "tp", "base");
+    if (adjoint) copies(false, "lam", "tl", "base");
+    o.f("    __syncthreads();\n    tau = nxt;\n    cur ^= 1;\n  }\n");
     if (adjoint && NP > 0) {
         o.f("  __syncthreads();\n");
         o.f("  for (int p = threadIdx.x; p < %d; p += %d) {\n", NP, T);
@@ -548,7 +663,7 @@ bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std:
         j.kernel = mk.second;
         const TilePass &P = prog.passes[p];
         const size_t T = size_t(1) << P.k;
-        j.smem = (adjoint ? 2 : 1) * T * es +
+        j.smem = (jit_double_buffer(dtype, adjoint, P.k) ? 2 : 1) * (adjoint ? 2 : 1) * T * es +
                  (adjoint ? 2 * (size_t)(P.nparam > 0 ? P.nparam : 1) * (kTileThreads / 32) * rs : 0);
         const size_t G = P.gate_count > 0 ? P.gate_count : 1;
         size_t bytes = G * 8 * rs;

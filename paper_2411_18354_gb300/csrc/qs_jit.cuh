@@ -42,6 +42,9 @@ bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std:
 cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
                             double *part, size_t part_stride, cudaStream_t st);
 
+// Whether the kernel of a pass with 2^k-amplitude tiles double-buffers them.
+bool jit_double_buffer(int dtype, bool adjoint, int k);
+
 // The generated source of one pass (exposed for tests of the generator).
 std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups,
                             const RegGate *gates, const char *kname);
