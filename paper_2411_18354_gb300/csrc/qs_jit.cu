@@ -331,7 +331,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     const char *skip_next = sel.empty() ? "" : "    while (nxt < ntiles && !selected(tile_base(nxt))) nxt += gridDim.x;\n";
     o.f("  u64 tau = blockIdx.x;\n");
     if (!sel.empty()) o.f("  while (tau < ntiles && !selected(tile_base(tau))) tau += gridDim.x;\n");
-    o.f("  int cur = 0;\n");
+    if (db) o.f("  int cur = 0;\n");
     if (db) {
         o.f("  if (tau < ntiles) {\n    const u64 b0 = tile_base(tau);\n");
         loads("sm0", "b0");
@@ -340,7 +340,10 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     o.f("  while (tau < ntiles) {\n");
     o.f("    const u64 base = tile_base(tau);\n");
     o.f("    u64 nxt = tau + gridDim.x;\n%s", skip_next);
-    o.f("    T2 *tp = sm0 + cur * %u;\n", BUF);
+    if (db)
+        o.f("    T2 *tp = sm0 + cur * %u;\n", BUF);
+    else
+        o.f("    T2 *tp = sm0;  // one buffer\n");
     if (adjoint) o.f("    T2 *tl = tp + %u;\n", TILE);
     if (db) {
         o.f("    if (nxt < ntiles) {\n      const u64 nb = tile_base(nxt);\n      T2 *tn = sm0 + (cur ^ 1) * %u;\n", BUF);
@@ -451,7 +454,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     }
     copies(false, "psi", "tp", "base");
     if (adjoint) copies(false, "lam", "tl", "base");
-    o.f("    __syncthreads();\n    tau = nxt;\n    cur ^= 1;\n  }\n");
+    o.f("    __syncthreads();\n    tau = nxt;\n%s  }\n", db ? "    cur ^= 1;\n" : "");
     if (adjoint && NP > 0) {
         o.f("  __syncthreads();\n");
         o.f("  for (int p = threadIdx.x; p < %d; p += %d) {\n", NP, T);

@@ -170,3 +170,49 @@ def test_jit_adjoint_controlled_rotations(qs, dtype, tol, tile_bits, monkeypatch
     assert np.max(np.abs(g - fd)) <= tol
     assert g[12] == 0.0 and g[13] == 0.0
     assert abs(e - oracle.energy(n, gates, th, psi0.astype(np.complex128))) <= tol
+
+
+@pytest.mark.parametrize("dtype,tile_bits", [("c64", 13), ("c128", 12), ("c64", 11)])
+def test_jit_many_tiles_per_block(qs, dtype, tile_bits, monkeypatch):
+    """n = 22 with tiles large enough that a block holds one tile buffer only (complex64 2^13,
+    complex128 2^12 amplitudes) and small enough that every block processes several tiles;
+    2^11 complex64 tiles are double-buffered with the same property. Random circuit with
+    non-local controls (tiles skipped) against the oracle."""
+    monkeypatch.setenv("QS_TILE_BITS", str(tile_bits))
+    n = 22
+    rng = np.random.default_rng(220 + tile_bits)
+    gates = _random_gates(rng, n, 150, cmax=2)
+    psi0 = random_state(n, dtype, 22)
+    ref = c128_of(psi0).copy()
+    oracle.run_circuit(ref, n, gates)
+    with qs.State(n, dtype) as st:
+        st.from_numpy(psi0)
+        st.apply_circuit(gates, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)
+        got = c128_of(st.to_numpy())
+    assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype]
+
+
+@pytest.mark.parametrize("dtype,tile_bits", [("c64", 12), ("c128", 10)])
+def test_jit_adjoint_many_tiles_per_block(qs, dtype, tile_bits, monkeypatch):
+    """Sweep passes with several tiles per block, n = 21: psi and lambda tiles of 2^12
+    complex64 amplitudes (one buffer per block) and of 2^10 complex128 amplitudes (two
+    buffers): energy against the oracle, gradient against the interpreted passes and against
+    central finite differences of the oracle energy for a few parameters."""
+    monkeypatch.setenv("QS_TILE_BITS", str(tile_bits))
+    n, layers = 21, 2
+    gates = W.hea_circuit(n, layers)
+    th = W.hea_params(n, layers, seed=21)
+    with qs.State(n, dtype) as st:
+        e, g = st.adjoint_grad(gates, th, qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)
+        st.set_basis(0)
+        e2, g2 = st.adjoint_grad(gates, th, qs.QS_FLAG_FUSE)
+    tol = 1e-4 if dtype == "c64" else 1e-9
+    assert abs(e - oracle.energy(n, gates, th)) <= tol
+    assert np.max(np.abs(g - g2)) <= tol
+    h = 1e-4
+    for p in (0, 17, 2 * n * layers - 1):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (oracle.energy(n, gates, tp) - oracle.energy(n, gates, tm)) / (2 * h)
+        assert abs(g[p] - fd) <= (1e-4 if dtype == "c64" else 1e-6), p
