@@ -292,14 +292,18 @@ def measure_adjoint(qs, W, peak, reps=3):
     n, layers = 24, 20
     gates = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
-    tuned = {"fwd": autotune.tune_fused(n, "c64", gates, th, adjoint=False, use_cache=False, reps=1),
-             "adj": autotune.tune_fused(n, "c64", gates, th, adjoint=True, use_cache=False, reps=1)}
-    out = {"tile_bits_c64": {"forward": tuned["fwd"]["tile_bits"], "adjoint": tuned["adj"]["tile_bits"]}}
-    out["compile_s_c64_compiled"] = _compile(qs, n, gates, th, "c64", adjoint=True)
+    out = {"tile_bits_c64": {}}
     grads = {}
     F, J = qs.QS_FLAG_FUSE, qs.QS_FLAG_JIT
     for label, dtype, flags in (("c64_fused_compiled", "c64", F | J), ("c64_fused", "c64", F), ("c64_unfused", "c64", 0),
                                 ("c128_plain", "c128", 0), ("c128_fused", "c128", F)):
+        _reset_tile_bits(qs)
+        if dtype == "c64" and flags & F:  # tile sizes tuned for this kind of pass (compiled or interpreted)
+            tb = [autotune.tune_fused(n, "c64", gates, th, adjoint=adj, use_cache=False, reps=1, flags=flags & J,
+                                      candidates=(11, 12, 13))["tile_bits"] for adj in (False, True)]
+            out["tile_bits_c64"][label] = {"forward": tb[0], "adjoint": tb[1]}
+            if flags & J:
+                out["compile_s_c64_compiled"] = _compile(qs, n, gates, th, "c64", adjoint=True)
         st = qs.State(n, dtype)
         try:
             st.adjoint_grad(gates, th, flags)  # warm-up (allocates lambda and scratch)
