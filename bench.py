@@ -538,10 +538,32 @@ def measure_batch(qs, W):
         info = b.info()
     finally:
         b.close()
-    return {"states": len(ns), "ms_per_launch": round(ms, 2), "states_per_s": round(len(ns) / (ms * 1e-3), 1),
-            "gradient_entries_per_s": round(sum(nparams) / (ms * 1e-3), 1), "config": cfg,
-            "grid": info["grid"], "smem_bytes": info["smem_bytes"],
-            "workload": "4096 states, n~U{10..20} (seed 4), HEA 8 layers, energies + adjoint gradients, complex64"}
+    out = {"states": len(ns), "ms_per_launch": round(ms, 2), "states_per_s": round(len(ns) / (ms * 1e-3), 1),
+           "gradient_entries_per_s": round(sum(nparams) / (ms * 1e-3), 1), "config": cfg,
+           "grid": info["grid"], "smem_bytes": info["smem_bytes"],
+           "workload": "4096 states, n~U{10..20} (seed 4), HEA 8 layers, energies + adjoint gradients, complex64"}
+    # pass-major path: states above small_bits side by side, every pass compiled for its shape and
+    # run over all states of one size per launch (first run compiles: untimed)
+    best = None
+    for jcfg in ({"small_bits": 12, "tile_bits": 12, "max_pass_gates": 64},
+                 {"small_bits": 12, "tile_bits": 11, "max_pass_gates": 64}):
+        b = qs.Batch(ns, circuits, nparams, "c64", **jcfg)
+        try:
+            t0 = time.perf_counter()
+            b.run(th, en, gr, qs.QS_FLAG_GRAPH | qs.QS_FLAG_JIT)
+            torch.cuda.synchronize()
+            first_s = time.perf_counter() - t0
+            msj = _events_ms(lambda: b.run(th, en, gr, qs.QS_FLAG_GRAPH | qs.QS_FLAG_JIT), 3)
+        finally:
+            b.close()
+        if best is None or msj < best[0]:
+            best = (msj, jcfg, first_s)
+    msj, jcfg, first_s = best
+    out["pass_major_compiled"] = {"ms_per_run": round(msj, 2), "states_per_s": round(len(ns) / (msj * 1e-3), 1),
+                                  "gradient_entries_per_s": round(sum(nparams) / (msj * 1e-3), 1), "config": jcfg,
+                                  "first_run_s_with_compile": round(first_s, 2),
+                                  "speedup_vs_persistent": round(ms / msj, 2)}
+    return out
 
 
 def cpu_oracle_sample(n_target: int, sched, max_gates=None):

@@ -18,8 +18,10 @@
 #include <vector>
 
 #include "k_batch.cuh"
+#include "k_batch_major.cuh"
 #include "qs_fuse.cuh"
 #include "qs_internal.cuh"
+#include "qs_jit.cuh"
 #include "qs_state.cuh"
 
 namespace qs {
@@ -33,6 +35,21 @@ constexpr uint32_t kBatchMagic = 0x51534254u;  // "QSBT"
 constexpr int kBatchMaxQubits = 30;
 constexpr int kBatchMaxParams = 4096;
 }  // namespace
+
+// A program of the pass-major path (QS_FLAG_JIT): its states side by side in one buffer, every
+// pass run over all of them by a kernel compiled for the pass.
+struct BatchJitProg {
+    int n = 0, nparam = 0;
+    std::vector<int> states;        // global state indices
+    qs::FusedProgram pf, pa;        // forward and sweep programs (rotation kinds / indices filled in)
+    std::vector<qs::JitPass> jf, ja;
+    void *psi = nullptr, *lam = nullptr, *cs = nullptr;
+    double *part = nullptr, *obs = nullptr;  // sweep gradient partials, energy partials
+    int *d_states = nullptr, *d_csr = nullptr;
+    uint64_t *d_items = nullptr;
+    std::vector<size_t> pass_off;   // per sweep pass: offset (doubles) of its partials in part
+    uint32_t tiles = 1;             // tiles per state
+};
 
 struct qs_batch {
     uint32_t magic = kBatchMagic;
@@ -53,7 +70,16 @@ struct qs_batch {
     cudaGraphExec_t exec = nullptr;
     const double *g_theta = nullptr;
     double *g_energy = nullptr, *g_grad = nullptr;
+    int g_flags = 0;
     cudaStream_t capture_stream = nullptr;
+    // pass-major path (QS_FLAG_JIT): programs of the states above small_bits, prepared on first use
+    std::vector<BatchJitProg> jprogs;
+    std::vector<int32_t> small_order;  // the states at or below small_bits, largest first
+    int *d_small_order = nullptr;
+    uint64_t *d_param_off = nullptr;
+    std::vector<uint64_t> param_off_host;
+    bool jit_ready = false;
+    double jit_compile_s = 0.0;
 };
 
 namespace {
@@ -61,6 +87,12 @@ namespace {
 void free_batch(qs_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (BatchJitProg &jp : b->jprogs)
+        for (void *p : {jp.psi, jp.lam, jp.cs, (void *)jp.part, (void *)jp.obs, (void *)jp.d_states, (void *)jp.d_csr,
+                        (void *)jp.d_items})
+            if (p) cudaFree(p);
+    if (b->d_small_order) cudaFree(b->d_small_order);
+    if (b->d_param_off) cudaFree(b->d_param_off);
     for (void *p : {b->d_states, b->d_order, b->d_progs, b->d_passes, b->d_gates, b->d_groups, b->workspace,
                     (void *)b->queue})
         if (p) cudaFree(p);
@@ -122,6 +154,109 @@ bool plan_pair(int n, int dtype, const qs_gate &g, int nparam, GatePlan *fwd, Ga
     return true;
 }
 
+// Compile the pass-major path's kernels and allocate its buffers (first QS_FLAG_JIT run).
+qs_status ensure_jit(qs_batch *b) {
+    if (b->jit_ready) return QS_OK;
+    const size_t es = elem_bytes(b->dtype), rs = es / 2;
+    std::vector<JitRequest> reqs;
+    for (BatchJitProg &jp : b->jprogs) {
+        reqs.push_back({&jp.pf, false, true, &jp.jf});
+        reqs.push_back({&jp.pa, true, true, &jp.ja});
+    }
+    std::string err;
+    if (!reqs.empty() && !jit_prepare_programs(b->dtype, reqs, &err, &b->jit_compile_s))
+        return set_error(QS_ECUDA, ("qs_batch_run: " + err).c_str());
+    auto dev_alloc = [](void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        return true;
+    };
+    for (BatchJitProg &jp : b->jprogs) {
+        const int S = (int)jp.states.size();
+        const size_t N = size_t(1) << jp.n;
+        jp.tiles = jp.pa.passes.empty() ? (jp.pf.passes.empty() ? 1u : (uint32_t)jp.pf.passes[0].ntiles)
+                                        : (uint32_t)jp.pa.passes[0].ntiles;
+        // sweep partials: per pass, [J][state][tile]; per parameter, the blocks of its gates
+        jp.pass_off.clear();
+        size_t total = 0;
+        std::vector<std::vector<uint64_t>> items(jp.nparam);
+        for (size_t i = 0; i < jp.pa.passes.size(); ++i) {
+            const TilePass &P = jp.pa.passes[i];
+            jp.pass_off.push_back(total);
+            int J = 0;
+            for (int g = P.gate_begin; g < P.gate_begin + P.gate_count; ++g) {
+                const RegGate &G = jp.pa.gates[g];
+                if (G.pkind == 0) continue;
+                if (G.slot >= 0 && G.slot < jp.nparam)
+                    items[G.slot].push_back(total + (uint64_t)J * S * (uint64_t)P.ntiles);
+                ++J;
+            }
+            total += (size_t)J * S * (size_t)P.ntiles;
+            if (P.ntiles != jp.tiles) return set_error(QS_EUNSUPPORTED, "qs_batch_run: passes of unequal tile counts");
+        }
+        std::vector<int> csr(jp.nparam + 1, 0);
+        std::vector<uint64_t> flat;
+        for (int q = 0; q < jp.nparam; ++q) {
+            csr[q] = (int)flat.size();
+            flat.insert(flat.end(), items[q].begin(), items[q].end());
+        }
+        csr[jp.nparam] = (int)flat.size();
+        if (!dev_alloc(&jp.psi, (size_t)S * N * es) || !dev_alloc(&jp.lam, (size_t)S * N * es) ||
+            !dev_alloc(&jp.cs, (size_t)S * std::max(1, jp.nparam) * 2 * rs) ||
+            !dev_alloc((void **)&jp.part, total * sizeof(double)) ||
+            !dev_alloc((void **)&jp.obs, bm_obs_partials(jp.n, S) * sizeof(double)))
+            return set_error(QS_ENOMEM, "qs_batch_run: cannot allocate the pass-major state buffers");
+        qs_status st;
+        if ((st = upload(jp.states, (void **)&jp.d_states)) != QS_OK || (st = upload(csr, (void **)&jp.d_csr)) != QS_OK ||
+            (st = upload(flat, (void **)&jp.d_items)) != QS_OK)
+            return st;
+        jp.pass_off.push_back(total);  // end marker: total partials
+    }
+    qs_status st;
+    if ((st = upload(b->small_order, (void **)&b->d_small_order)) != QS_OK) return st;
+    if ((st = upload(b->param_off_host, (void **)&b->d_param_off)) != QS_OK) return st;
+    b->jit_ready = true;
+    return QS_OK;
+}
+
+// Enqueue one pass-major run on `st`: the small states in the persistent kernel, then every
+// larger program's passes over all its states.
+cudaError_t enqueue_jit(qs_batch *b, const BatchArgs &a0, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (!b->small_order.empty()) {
+        BatchArgs a = a0;
+        a.order = b->d_small_order;
+        a.num_states = (int)b->small_order.size();
+        e = cudaMemsetAsync(b->queue, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_batch(b->dtype, a, b->grid, b->smem, st);
+        if (e != cudaSuccess) return e;
+    }
+    for (BatchJitProg &jp : b->jprogs) {
+        const int S = (int)jp.states.size();
+        const uint64_t N = 1ull << jp.n;
+        e = launch_bm_init(b->dtype, jp.psi, jp.n, S, jp.cs, jp.nparam, a0.theta, b->d_param_off, jp.d_states, st);
+        for (size_t i = 0; e == cudaSuccess && i < jp.pf.passes.size(); ++i)
+            e = launch_jit_pass_batched(b->dtype, jp.jf[i], jp.pf, (int)i, jp.psi, nullptr, nullptr, N, S, jp.cs,
+                                        2u * (uint32_t)jp.nparam, st);
+        if (e == cudaSuccess)
+            e = launch_bm_obs(b->dtype, jp.psi, jp.lam, jp.n, S, jp.obs, a0.energy, jp.d_states, st);
+        if (e == cudaSuccess && jp.pass_off.back() > 0)
+            e = cudaMemsetAsync(jp.part, 0, jp.pass_off.back() * sizeof(double), st);
+        for (size_t i = 0; e == cudaSuccess && i < jp.pa.passes.size(); ++i)
+            e = launch_jit_pass_batched(b->dtype, jp.ja[i], jp.pa, (int)i, jp.psi, jp.lam, jp.part + jp.pass_off[i], N,
+                                        S, jp.cs, 2u * (uint32_t)jp.nparam, st);
+        if (e == cudaSuccess)
+            e = launch_bm_grad(jp.part, jp.d_csr, jp.d_items, jp.nparam, S, jp.tiles, a0.grad, b->d_param_off,
+                               jp.d_states, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -149,6 +284,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     std::vector<RegGate> tgates;
     std::vector<TileGroup> tgroups;
     std::map<std::string, int> prog_of;
+    std::vector<std::pair<FusedProgram, FusedProgram>> host_progs;  // per program: forward, sweep
     int max_params = 1, max_large_n = 0, max_small_n = 0, smem_bits = 5;
     char err[256], e2[512];
     for (int s = 0; s < num_states; ++s) {
@@ -237,7 +373,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
                     tgroups.push_back(Gr);
                 }
                 for (size_t gi = 0; gi < fp.gates.size(); ++gi) {
-                    RegGate G = fp.gates[gi];
+                    RegGate &G = fp.gates[gi];  // rotation fields filled in place (the pass-major path keeps fp)
                     const int first = dir ? fp.gate_src[gi] : srcm[fp.gate_src[gi]].first;
                     const int second = dir ? -1 : srcm[fp.gate_src[gi]].second;
                     const qs_gate &src = gs[first];
@@ -253,6 +389,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
                         }
                     } else {
                         G.slot = -1;
+                        G.pkind = 0;
                     }
                     tgates.push_back(G);
                 }
@@ -269,6 +406,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
             pid = (int)progs.size();
             progs.push_back(bp);
             prog_of.emplace(key, pid);
+            host_progs.push_back({std::move(pf), std::move(pa)});
         }
         states[s].n = n;
         states[s].prog = pid;
@@ -324,6 +462,29 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
         free_batch(b);
         return set_error(QS_ENOMEM, "qs_batch_create: cannot allocate the work queue");
     }
+    // the pass-major path's programs (states above small_bits), compiled on first use
+    {
+        std::vector<int> jp_of(progs.size(), -1);
+        for (int o = 0; o < num_states; ++o) {
+            const int s = order[o];
+            if (states[s].n <= small_bits) {
+                b->small_order.push_back(s);
+                continue;
+            }
+            const int pid = states[s].prog;
+            if (jp_of[pid] < 0) {
+                jp_of[pid] = (int)b->jprogs.size();
+                b->jprogs.emplace_back();
+                BatchJitProg &jp = b->jprogs.back();
+                jp.n = states[s].n;
+                jp.nparam = states[s].nparam;
+                jp.pf = host_progs[pid].first;
+                jp.pa = host_progs[pid].second;
+            }
+            b->jprogs[jp_of[pid]].states.push_back(s);
+        }
+        b->param_off_host.assign(param_offsets, param_offsets + num_states + 1);
+    }
     BatchArgs &a = b->args;
     a.states = static_cast<const BatchState *>(b->d_states);
     a.order = static_cast<const int32_t *>(b->d_order);
@@ -345,18 +506,27 @@ qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double 
     if (!b || b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_run: batch is NULL or not valid");
     if (!theta || !energy || (b->num_params > 0 && !grad))
         return set_error(QS_EINVAL, "qs_batch_run: theta, energy and grad must be device pointers");
-    if (flags & ~QS_FLAG_GRAPH) return set_error(QS_EINVAL, "qs_batch_run: unknown flags");
+    if (flags & ~(QS_FLAG_GRAPH | QS_FLAG_JIT)) return set_error(QS_EINVAL, "qs_batch_run: unknown flags");
     BatchArgs a = b->args;
     a.theta = theta;
     a.energy = energy;
     a.grad = grad;
+    const bool jit = (flags & QS_FLAG_JIT) != 0;
+    if (jit) {
+        qs_status st = ensure_jit(b);
+        if (st != QS_OK) return st;
+    }
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+        if (jit) return enqueue_jit(b, a, st);
+        cudaError_t e1 = cudaMemsetAsync(b->queue, 0, sizeof(int), st);
+        return e1 == cudaSuccess ? launch_batch(b->dtype, a, b->grid, b->smem, st) : e1;
+    };
     cudaError_t e;
     if (!(flags & QS_FLAG_GRAPH)) {
-        e = cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream);
-        if (e == cudaSuccess) e = launch_batch(b->dtype, a, b->grid, b->smem, b->stream);
+        e = enqueue(b->stream);
         return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_batch_run launch");
     }
-    if (!b->exec || b->g_theta != theta || b->g_energy != energy || b->g_grad != grad) {
+    if (!b->exec || b->g_theta != theta || b->g_energy != energy || b->g_grad != grad || b->g_flags != flags) {
         if (b->exec) {
             cudaStreamSynchronize(b->stream);
             cudaGraphExecDestroy(b->exec);
@@ -368,8 +538,7 @@ qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double 
         }
         e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "qs_batch_run: begin capture");
-        cudaError_t e1 = cudaMemsetAsync(b->queue, 0, sizeof(int), b->capture_stream);
-        cudaError_t e2 = e1 == cudaSuccess ? launch_batch(b->dtype, a, b->grid, b->smem, b->capture_stream) : e1;
+        cudaError_t e2 = enqueue(b->capture_stream);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(b->capture_stream, &graph);
         if (e2 != cudaSuccess || e != cudaSuccess) {
@@ -385,6 +554,7 @@ qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double 
         b->g_theta = theta;
         b->g_energy = energy;
         b->g_grad = grad;
+        b->g_flags = flags;
     }
     e = cudaGraphLaunch(b->exec, b->stream);
     return e == cudaSuccess ? QS_OK : cuda_fail(e, "qs_batch_run: graph launch");

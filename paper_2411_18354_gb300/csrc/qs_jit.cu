@@ -84,6 +84,23 @@ void preamble(Out &o, bool dbl) {
         "  T2 a; a.x = F(ar, x.x, -ai * x.y); a.y = F(ar, x.y, ai * x.x); x = a;\n}\n");
     o.f("__device__ __forceinline__ void u_diag(T2 &x, T2 &y, const R *m) { u_mul(x, m[0], m[1]); u_mul(y, m[6], m[7]); }\n");
     o.f("__device__ __forceinline__ void u_swap(T2 &x, T2 &y) { T2 t = x; x = y; y = t; }\n");
+    // a parameterised gate from (c, s) = (cos, sin) of theta / 2: kind 2 = RY = [[c, -s], [s, c]],
+    // kind 3 = RZ = diag(c - i s, c + i s); adj: the dagger; d: dU/dtheta of the gate itself
+    o.f("__device__ __forceinline__ void pmat(int kind, R c, R s, int adj, R *u, R *d) {\n"
+        "  for (int i = 0; i < 8; ++i) { u[i] = 0; d[i] = 0; }\n"
+        "  const R h = (R)0.5;\n"
+        "  u[0] = c; u[6] = c;\n"
+        "  if (kind == 2) { u[2] = adj ? s : -s; u[4] = adj ? -s : s; d[0] = -h * s; d[2] = -h * c; d[4] = h * c; "
+        "d[6] = -h * s; }\n"
+        "  else { u[1] = adj ? s : -s; u[7] = adj ? -s : s; d[0] = -h * s; d[1] = -h * c; d[6] = -h * s; d[7] = h * c; }\n"
+        "}\n");
+    // w = a b for row-major complex 2x2 matrices (interleaved re, im)
+    o.f("__device__ __forceinline__ void mat2(const R *a, const R *b, R *w) {\n"
+        "  for (int i = 0; i < 2; ++i) for (int j = 0; j < 2; ++j) {\n"
+        "    const R *x = a + 4 * i, *y0 = b + 2 * j, *y1 = b + 4 + 2 * j;\n"
+        "    w[4 * i + 2 * j] = x[0] * y0[0] - x[1] * y0[1] + x[2] * y1[0] - x[3] * y1[1];\n"
+        "    w[4 * i + 2 * j + 1] = x[0] * y0[1] + x[1] * y0[0] + x[2] * y1[1] + x[3] * y1[0];\n"
+        "  }\n}\n");
     o.f("__device__ __forceinline__ void cp8(void *s, const void *g) {\n"
         "  asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\\n\" :: \"r\"((u32)__cvta_generic_to_shared(s)), "
         "\"l\"(g) : \"memory\");\n}\n");
@@ -122,8 +139,17 @@ std::string any_selects(const RegGate *g, int count, const char *bv = "base") {
     return c;
 }
 
-// The pair updates of one gate on row registers v (and, adjoint, w with the derivative dot).
-void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, int slot, const char *v, const char *w) {
+// Expressions of the gates' matrices (m), derivatives (d) and gradient accumulator indices.
+struct Refs {
+    std::vector<std::string> m, d;
+    std::vector<int> acc;
+};
+
+// The pair updates of one gate on row registers v (and, adjoint, w with the derivative dot
+// when the gate has a parameter).
+void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, bool param, const char *v, const char *w,
+                     const Refs &refs) {
+    const char *M = refs.m[gi].c_str();
     const int p = G.p;
     int dop = G.op == OP_DIAG ? OP_DIAG : (G.op == OP_REAL ? OP_REAL : OP_GEN);
     for (int e = 0; e < E; ++e) {
@@ -132,19 +158,20 @@ void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, int 
         const int e2 = e | (1 << p);
         auto op = [&](const char *a) {
             switch (G.op) {
-            case OP_GEN: o.f("u_gen(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
-            case OP_REAL: o.f("u_real(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
-            case OP_DIAG: o.f("u_diag(%s[%d], %s[%d], a.m[%d]);\n", a, e, a, e2, gi); break;
+            case OP_GEN: o.f("u_gen(%s[%d], %s[%d], %s);\n", a, e, a, e2, M); break;
+            case OP_REAL: o.f("u_real(%s[%d], %s[%d], %s);\n", a, e, a, e2, M); break;
+            case OP_DIAG: o.f("u_diag(%s[%d], %s[%d], %s);\n", a, e, a, e2, M); break;
             case OP_SWAP: o.f("u_swap(%s[%d], %s[%d]);\n", a, e, a, e2); break;
-            case OP_SIDE: o.f("u_mul(%s[%d], a.m[%d][0], a.m[%d][1]);\n", a, G.side ? e2 : e, gi, gi); break;
+            case OP_SIDE: o.f("u_mul(%s[%d], %s[0], %s[1]);\n", a, G.side ? e2 : e, M, M); break;
             default: break;
             }
         };
         op(v);
         if (adjoint) {
-            if (slot >= 0) {
+            if (param) {
                 o.f("{ T2 mx = %s[%d], my = %s[%d]; ", v, e, v, e2);
-                o.f("%s(mx, my, a.d[%d]); ", dop == OP_DIAG ? "u_diag" : (dop == OP_REAL ? "u_real" : "u_gen"), slot);
+                o.f("%s(mx, my, %s); ", dop == OP_DIAG ? "u_diag" : (dop == OP_REAL ? "u_real" : "u_gen"),
+                    refs.d[gi].c_str());
                 o.f("dot += %s[%d].x * mx.x + %s[%d].y * mx.y + %s[%d].x * my.x + %s[%d].y * my.y; }\n", w, e, w, e, w,
                     e2, w, e2);
             }
@@ -160,7 +187,7 @@ void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, int 
 // predicates hold, and each element is then multiplied by the factors of the classes that
 // select it: one complex product per gate and row plus one per selected element and class,
 // instead of one per selected element and gate.
-void emit_diag_run(Out &o, const RegGate *gs, int gi0, int count, int E, bool adjoint) {
+void emit_diag_run(Out &o, const RegGate *gs, int gi0, int count, int E, bool adjoint, const Refs &refs) {
     struct Cls {
         int p, cqm, cqv;
         bool has_a = false, has_d = false;
@@ -202,10 +229,11 @@ void emit_diag_run(Out &o, const RegGate *gs, int gi0, int count, int E, bool ad
             cond += t;
         }
         o.f("        if (%s) {", cond.empty() ? "true" : cond.c_str());
+        const char *M = refs.m[gi].c_str();
         if (R.op == OP_DIAG)
-            o.f(" u_mul(fa%d, a.m[%d][0], a.m[%d][1]); u_mul(fd%d, a.m[%d][6], a.m[%d][7]);", c, gi, gi, c, gi, gi);
+            o.f(" u_mul(fa%d, %s[0], %s[1]); u_mul(fd%d, %s[6], %s[7]);", c, M, M, c, M, M);
         else
-            o.f(" u_mul(f%c%d, a.m[%d][0], a.m[%d][1]);", R.side ? 'd' : 'a', c, gi, gi);
+            o.f(" u_mul(f%c%d, %s[0], %s[1]);", R.side ? 'd' : 'a', c, M, M);
         o.f(" }\n");
     }
     for (int e = 0; e < E; ++e) {
@@ -231,7 +259,7 @@ bool jit_double_buffer(int dtype, bool adjoint, int k) {
 }
 
 std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups,
-                            const RegGate *gates, const char *kname) {
+                            const RegGate *gates, const char *kname, bool batched) {
     const bool dbl = dtype == QS_C128;
     const int SW = dbl ? 3 : 4;
     const int VEC = dbl ? 1 : 2;
@@ -240,17 +268,46 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     const uint32_t nvec = (1u << k) / VEC;
     const uint32_t steps = (nvec + T - 1) / T;
     const int G = P.gate_count;
-    const int NP = adjoint ? P.nparam : 0;
+    const RegGate *pg = gates + P.gate_begin;
+    // Matrix (and derivative) of each gate as an expression: parameters of the kernel (single
+    // state), or, in a batch, shared-memory rows formed per tile from the tile's state's angles
+    // for the parameterised gates (pm_, pd_; J = index among them).
+    std::vector<int> pj(G, -1);
+    int NPG = 0;
+    if (batched)
+        for (int i = 0; i < G; ++i)
+            if (pg[i].pkind != 0) pj[i] = NPG++;
+    const int NP = adjoint ? (batched ? NPG : P.nparam) : 0;  // gradient accumulators
+    Refs refs;
+    refs.m.resize(G);
+    refs.d.resize(G);
+    for (int i = 0; i < G; ++i) {
+        char b[48];
+        if (pj[i] >= 0) std::snprintf(b, sizeof(b), "(pm_ + %d)", 8 * pj[i]);
+        else std::snprintf(b, sizeof(b), "a.m[%d]", i);
+        refs.m[i] = b;
+        if (pj[i] >= 0) std::snprintf(b, sizeof(b), "(pd_ + %d)", 8 * pj[i]);
+        else std::snprintf(b, sizeof(b), "a.d[%d]", pg[i].slot);
+        refs.d[i] = b;
+        refs.acc.push_back(batched ? pj[i] : pg[i].slot);
+    }
     Out o;
     preamble(o, dbl);
-    // parameter block: the matrices of the pass's gates (U, or U^dagger in the adjoint sweep),
-    // the derivatives of its parameterised gates, their global gradient slots, the partials
+    // parameter block: the fixed matrices of the pass's gates (U, or U^dagger in the adjoint
+    // sweep); single state: the derivatives of its parameterised gates and their global
+    // gradient slots; batch: the parameter indices of the parameterised gates
     o.f("struct alignas(16) A {\n  R m[%d][8];\n", G > 0 ? G : 1);
-    if (adjoint) o.f("  R d[%d][8];\n  int gs[%d];\n", NP > 0 ? NP : 1, NP > 0 ? NP : 1);
+    if (adjoint && !batched) o.f("  R d[%d][8];\n  int gs[%d];\n", NP > 0 ? NP : 1, NP > 0 ? NP : 1);
+    if (batched) o.f("  int pix[%d][2];\n", G > 0 ? G : 1);
     o.f("};\n");
     o.f("__device__ __forceinline__ u32 swz(u32 a) { return %s; }\n", swz_expr("a", SW).c_str());
     const int minb = (adjoint && dbl) ? 1 : 2;
-    if (adjoint)
+    if (batched)
+        o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, T2 *__restrict__ lam, "
+            "double *__restrict__ part, u64 stride, u64 nstates, const R *__restrict__ cs, u32 cs_stride, "
+            "const __grid_constant__ A a) {\n",
+            T, minb, kname);
+    else if (adjoint)
         o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, T2 *__restrict__ lam, "
             "double *__restrict__ part, u64 part_stride, const __grid_constant__ A a) {\n",
             T, minb, kname);
@@ -262,8 +319,14 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     const uint32_t BUF = (adjoint ? 2 : 1) * TILE;  // one buffer: psi tile (and lambda tile)
     o.f("  extern __shared__ __align__(16) unsigned char sm_[];\n");
     o.f("  T2 *const sm0 = reinterpret_cast<T2 *>(sm_);\n");
+    o.f("  R *const sr_ = reinterpret_cast<R *>(sm0 + %u);\n", (db ? 2 : 1) * BUF);
+    if (batched) {
+        o.f("  R *const pm_ = sr_;\n");
+        if (adjoint) o.f("  R *const pd_ = pm_ + %d;\n", 8 * (NPG > 0 ? NPG : 1));
+    }
+    const int pm_words = batched ? (adjoint ? 2 : 1) * 8 * (NPG > 0 ? NPG : 1) : 0;
     if (adjoint) {
-        o.f("  R *acc_s = reinterpret_cast<R *>(sm0 + %u);\n", (db ? 2 : 1) * BUF);
+        o.f("  R *acc_s = sr_ + %d;\n", pm_words);
         o.f("  R *acc_c = acc_s + %d;\n", (NP > 0 ? NP : 1) * (T / 32));
         o.f("  for (int i = threadIdx.x; i < %d; i += %d) { acc_s[i] = 0; acc_c[i] = 0; }\n", (NP > 0 ? NP : 1) * (T / 32), T);
         o.f("  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;\n");
@@ -283,7 +346,12 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     }
     o.f("  const u32 s_t = swz(o_t);\n");
     const bool cp_guard = nvec < (uint32_t)T;
-    o.f("  const u64 ntiles = %lluull;\n", (unsigned long long)P.ntiles);
+    int logt = 0;
+    while ((1ull << logt) < P.ntiles) ++logt;
+    if (batched)
+        o.f("  const u64 ntiles = nstates << %d;  // %llu tiles per state\n", logt, (unsigned long long)P.ntiles);
+    else
+        o.f("  const u64 ntiles = %lluull;\n", (unsigned long long)P.ntiles);
     {
         std::string b = "0ull";
         for (int s = 0; s < P.tnseg; ++s) {
@@ -291,10 +359,19 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
             std::snprintf(t, sizeof(t), " | ((t_ << %d) & 0x%llxull)", P.tshift[s], (unsigned long long)P.tmask[s]);
             b += t;
         }
-        o.f("  auto tile_base = [](u64 t_) -> u64 { return %s; };\n", b.c_str());
+        if (batched)  // the tile index within its state: the low bits of the batch-wide index
+            o.f("  auto tile_base = [](u64 t_) -> u64 { t_ &= %lluull; return %s; };\n",
+                (unsigned long long)(P.ntiles - 1), b.c_str());
+        else
+            o.f("  auto tile_base = [](u64 t_) -> u64 { return %s; };\n", b.c_str());
+    }
+    if (batched) {
+        o.f("  auto gvec = [&](T2 *v_, u64 t_) -> T2 * { return v_ + (t_ >> %d) * stride; };\n", logt);
+    } else {
+        o.f("  auto gvec = [](T2 *v_, u64) -> T2 * { return v_; };\n");
     }
     std::string sel;
-    if (P.hctrl) sel = any_selects(gates + P.gate_begin, G, "b_");
+    if (P.hctrl) sel = any_selects(pg, G, "b_");
     if (!sel.empty()) o.f("  auto selected = [](u64 b_) -> bool { return %s; };\n", sel.c_str());
     // tile copies (asynchronous loads into swizzled shared-memory positions; stores from registers)
     const uint32_t s1 = tile_swizzle(1u, SW);
@@ -319,14 +396,35 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
         }
         if (cp_guard) o.f("    }\n");
     };
-    auto loads = [&](const char *tname, const char *bname) {
-        o.f("    {\n    T2 *tq = %s;\n", tname);
-        copies(true, "psi", "tq", bname);
+    auto loads = [&](const char *tname, const char *bname, const char *tau_name) {
+        o.f("    {\n    T2 *tq = %s;\n    const T2 *gp_ = gvec(psi, %s);\n", tname, tau_name);
+        copies(true, "gp_", "tq", bname);
         if (adjoint) {
-            o.f("    T2 *tr = tq + %u;\n", TILE);
-            copies(true, "lam", "tr", bname);
+            o.f("    T2 *tr = tq + %u;\n    const T2 *gl_ = gvec(lam, %s);\n", TILE, tau_name);
+            copies(true, "gl_", "tr", bname);
         }
         o.f("    }\n    cpcommit();\n");
+    };
+    // batch: the matrices of the parameterised gates for the state of tile tau_ (one thread
+    // per gate), from that state's (cos, sin) of theta / 2
+    auto stage_params = [&](const char *tau_name) {
+        if (!batched || NPG == 0) return;
+        o.f("    {\n      const R *cq = cs + (%s >> %d) * (u64)cs_stride;\n", tau_name, logt);
+        for (int i = 0; i < G; ++i) {
+            if (pj[i] < 0) continue;
+            const RegGate &R = pg[i];
+            o.f("      if (tid == %d) { R u1[8], d1[8]; pmat(%d, cq[2 * a.pix[%d][0]], cq[2 * a.pix[%d][0] + 1], %d, u1, d1);",
+                pj[i] % T, R.pkind, i, i, adjoint ? 1 : 0);
+            if (!adjoint && R.pkind2 != 0)
+                o.f(" R u2[8], d2[8]; pmat(%d, cq[2 * a.pix[%d][1]], cq[2 * a.pix[%d][1] + 1], 0, u2, d2);"
+                    " mat2(u2, u1, pm_ + %d);",
+                    R.pkind2, i, i, 8 * pj[i]);
+            else
+                o.f(" for (int q_ = 0; q_ < 8; ++q_) pm_[%d + q_] = u1[q_];", 8 * pj[i]);
+            if (adjoint) o.f(" for (int q_ = 0; q_ < 8; ++q_) pd_[%d + q_] = d1[q_];", 8 * pj[i]);
+            o.f(" }\n");
+        }
+        o.f("    }\n");
     };
     const char *skip_next = sel.empty() ? "" : "    while (nxt < ntiles && !selected(tile_base(nxt))) nxt += gridDim.x;\n";
     o.f("  u64 tau = blockIdx.x;\n");
@@ -334,7 +432,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     if (db) o.f("  int cur = 0;\n");
     if (db) {
         o.f("  if (tau < ntiles) {\n    const u64 b0 = tile_base(tau);\n");
-        loads("sm0", "b0");
+        loads("sm0", "b0", "tau");
         o.f("  }\n");
     }
     o.f("  while (tau < ntiles) {\n");
@@ -345,17 +443,17 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
     else
         o.f("    T2 *tp = sm0;  // one buffer\n");
     if (adjoint) o.f("    T2 *tl = tp + %u;\n", TILE);
+    stage_params("tau");
     if (db) {
         o.f("    if (nxt < ntiles) {\n      const u64 nb = tile_base(nxt);\n      T2 *tn = sm0 + (cur ^ 1) * %u;\n", BUF);
-        loads("tn", "nb");
+        loads("tn", "nb", "nxt");
         o.f("      cpwait1();\n    } else {\n      cpwait0();\n    }\n");
     } else {
-        loads("tp", "base");
+        loads("tp", "base", "tau");
         o.f("    cpwait0();\n");
     }
     o.f("    __syncthreads();\n");
 
-    const RegGate *pg = gates + P.gate_begin;
     for (int gi_ = 0; gi_ < P.group_count; ++gi_) {
         const TileGroup &Gr = groups[P.group_begin + gi_];
         const int r = Gr.r;
@@ -389,7 +487,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
             }
             o.f("      const u32 ra = %s;\n      const u32 rs = swz(ra);\n", ra.c_str());
             o.f("      const bool act = %s;\n", guard ? (std::string("rho < ") + std::to_string(rows) + "u").c_str() : "true");
-            o.f("      T2 v[%d]%s;\n", E, adjoint ? "" : "");
+            o.f("      T2 v[%d];\n", E);
             if (adjoint) o.f("      T2 w[%d];\n", E);
             o.f("      if (act) {\n");
             for (int e = 0; e < E; ++e) {
@@ -410,13 +508,13 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                 if (g + 1 < Gr.gate_count && mergeable(g) && mergeable(g + 1)) {
                     int h = g;
                     while (h < Gr.gate_count && mergeable(h)) ++h;
-                    emit_diag_run(o, pg + gb + g, gb + g, h - g, E, adjoint);
+                    emit_diag_run(o, pg + gb + g, gb + g, h - g, E, adjoint, refs);
                     g = h - 1;
                     continue;
                 }
                 const RegGate &R = pg[gb + g];
-                const int gi = gb + g;  // index into a.m
-                const int slot = adjoint ? R.slot : -1;
+                const int gi = gb + g;  // pass-relative gate index
+                const int slot = adjoint && R.slot >= 0 ? refs.acc[gi] : -1;
                 o.f("      // gate %d: op %d, place %d, cq %x/%x, rows %x/%x\n", gi, R.op, R.p, R.cqm, R.cqv, R.crm, R.crv);
                 const bool tile_guard = R.hmask != 0;
                 if (tile_guard)
@@ -433,7 +531,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                 }
                 const bool need_rc = guard || R.crm;
                 if (need_rc) o.f("        if (%s) {\n", rc.c_str());
-                emit_gate_pairs(o, R, gi, E, adjoint, slot, "v", "w");
+                emit_gate_pairs(o, R, gi, E, adjoint, slot >= 0, "v", "w", refs);
                 if (need_rc) o.f("        }\n");
                 if (slot >= 0) {
                     o.f("        for (int of = 16; of > 0; of >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, of);\n");
@@ -452,10 +550,26 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
         }
         o.f("    }\n    __syncthreads();\n");
     }
-    copies(false, "psi", "tp", "base");
-    if (adjoint) copies(false, "lam", "tl", "base");
-    o.f("    __syncthreads();\n    tau = nxt;\n%s  }\n", db ? "    cur ^= 1;\n" : "");
-    if (adjoint && NP > 0) {
+    o.f("    {\n    T2 *gp_ = gvec(psi, tau);\n");
+    copies(false, "gp_", "tp", "base");
+    if (adjoint) {
+        o.f("    T2 *gl_ = gvec(lam, tau);\n");
+        copies(false, "gl_", "tl", "base");
+    }
+    o.f("    }\n    __syncthreads();\n");
+    if (adjoint && batched && NP > 0) {
+        // this tile's gradient partials (sum over the block's warps), then fresh accumulators;
+        // the loop's next block barrier orders them before the next tile adds to them
+        o.f("    for (int p = threadIdx.x; p < %d; p += %d) {\n", NP, T);
+        o.f("      double s = 0.0;\n");
+        o.f("      for (int w_ = 0; w_ < %d; ++w_) { s += (double)acc_s[p * %d + w_] - (double)acc_c[p * %d + w_]; "
+            "acc_s[p * %d + w_] = 0; acc_c[p * %d + w_] = 0; }\n",
+            T / 32, T / 32, T / 32, T / 32, T / 32);
+        o.f("      part[((u64)p * nstates + (tau >> %d)) * %lluull + (tau & %lluull)] = s;\n    }\n", logt,
+            (unsigned long long)P.ntiles, (unsigned long long)(P.ntiles - 1));
+    }
+    o.f("    tau = nxt;\n%s  }\n", db ? "    cur ^= 1;\n" : "");
+    if (adjoint && !batched && NP > 0) {
         o.f("  __syncthreads();\n");
         o.f("  for (int p = threadIdx.x; p < %d; p += %d) {\n", NP, T);
         o.f("    double s = 0.0;\n");
@@ -491,10 +605,11 @@ std::unordered_map<std::string, std::pair<int, int>> g_by_shape;   // shape key 
 // Everything a pass's generated source depends on, as bytes (the matrices excluded): looking
 // this up costs far less than generating the source, so a repeated circuit finds its kernels
 // without writing them again.
-std::string shape_key(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups, const RegGate *gates) {
+std::string shape_key(int dtype, bool adjoint, bool batched, const TilePass &P, const TileGroup *groups,
+                      const RegGate *gates) {
     std::string k;
     auto put = [&k](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
-    const int hdr[4] = {dtype, adjoint ? 1 : 0, P.gate_count, P.group_count};
+    const int hdr[5] = {dtype, adjoint ? 1 : 0, batched ? 1 : 0, P.gate_count, P.group_count};
     put(hdr, sizeof(hdr));
     put(&P.n, sizeof(P.n));
     put(&P.k, sizeof(P.k));
@@ -523,6 +638,10 @@ std::string shape_key(int dtype, bool adjoint, const TilePass &P, const TileGrou
         put(&g.slot, sizeof(g.slot));
         put(&g.hmask, sizeof(g.hmask));
         put(&g.hvals, sizeof(g.hvals));
+        if (batched) {  // the kinds of the rotations whose matrices the kernel forms
+            const int kinds[2] = {g.pkind, g.pkind2};
+            put(kinds, sizeof(kinds));
+        }
     }
     return k;
 }
@@ -561,26 +680,41 @@ bool compile_cubin(const std::string &src, std::vector<char> *cubin, std::string
 
 }  // namespace
 
-bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std::vector<JitPass> *out,
-                         std::string *err, double *compile_seconds, int *compiled_modules) {
-    out->assign(prog.passes.size(), JitPass{});
+bool jit_prepare_programs(int dtype, const std::vector<JitRequest> &reqs, std::string *err, double *compile_seconds,
+                          int *compiled_modules) {
     if (compile_seconds) *compile_seconds = 0.0;
     if (compiled_modules) *compiled_modules = 0;
     const size_t es = dtype == QS_C64 ? 8 : 16, rs = dtype == QS_C64 ? 4 : 8;
+    // every pass of every request, in order
+    struct Item {
+        const FusedProgram *prog;
+        int pass;
+        bool adjoint, batched;
+        size_t req;
+    };
+    std::vector<Item> items;
+    for (size_t ri = 0; ri < reqs.size(); ++ri) {
+        const JitRequest &r = reqs[ri];
+        r.out->assign(r.prog->passes.size(), JitPass{});
+        for (size_t p = 0; p < r.prog->passes.size(); ++p) items.push_back({r.prog, (int)p, r.adjoint, r.batched, ri});
+    }
     // one source per pass (kernel name fixed: the source text alone keys the cache); a pass
-    // whose shape was seen before takes its source from the shape cache
-    std::vector<std::string> srcs(prog.passes.size()), keys(prog.passes.size());
-    std::vector<char> known(prog.passes.size(), 0);
+    // whose shape was seen before needs no source
+    std::vector<std::string> srcs(items.size()), keys(items.size());
+    std::vector<char> known(items.size(), 0);
     std::lock_guard<std::mutex> lock(g_mu);
-    for (size_t p = 0; p < prog.passes.size(); ++p) {
-        keys[p] = shape_key(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data());
-        if (g_by_shape.count(keys[p])) {
-            known[p] = 1;
+    for (size_t i = 0; i < items.size(); ++i) {
+        const Item &it = items[i];
+        const FusedProgram &prog = *it.prog;
+        keys[i] = shape_key(dtype, it.adjoint, it.batched, prog.passes[it.pass], prog.groups.data(), prog.gates.data());
+        if (g_by_shape.count(keys[i])) {
+            known[i] = 1;
             continue;
         }
-        srcs[p] = jit_pass_source(dtype, adjoint, prog.passes[p], prog.groups.data(), prog.gates.data(), "qs_pass");
+        srcs[i] = jit_pass_source(dtype, it.adjoint, prog.passes[it.pass], prog.groups.data(), prog.gates.data(),
+                                  "qs_pass", it.batched);
     }
-    // passes whose source is not cached yet go into one new module (renamed kernels)
+    // passes whose source is not cached yet go into new modules (renamed kernels)
     std::vector<int> missing;
     std::unordered_map<std::string, int> first_of;
     for (size_t p = 0; p < srcs.size(); ++p) {
@@ -658,74 +792,109 @@ bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std:
             *compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (compiled_modules) *compiled_modules = (int)mods.size();
     }
-    for (size_t p = 0; p < srcs.size(); ++p) {
-        if (!known[p]) g_by_shape[keys[p]] = g_by_source.at(srcs[p]);
-        const auto &mk = g_by_shape.at(keys[p]);
-        JitPass &j = (*out)[p];
+    for (size_t i = 0; i < items.size(); ++i) {
+        if (!known[i]) g_by_shape[keys[i]] = g_by_source.at(srcs[i]);
+        const auto &mk = g_by_shape.at(keys[i]);
+        const Item &it = items[i];
+        const FusedProgram &prog = *it.prog;
+        JitPass &j = (*reqs[it.req].out)[it.pass];
         j.entry = mk.first;
         j.kernel = mk.second;
-        const TilePass &P = prog.passes[p];
+        const TilePass &P = prog.passes[it.pass];
         const size_t T = size_t(1) << P.k;
-        j.smem = (jit_double_buffer(dtype, adjoint, P.k) ? 2 : 1) * (adjoint ? 2 : 1) * T * es +
-                 (adjoint ? 2 * (size_t)(P.nparam > 0 ? P.nparam : 1) * (kTileThreads / 32) * rs : 0);
+        int npg = 0;  // batch: parameterised gates of the pass
+        if (it.batched)
+            for (int g = P.gate_begin; g < P.gate_begin + P.gate_count; ++g) npg += prog.gates[g].pkind != 0;
+        const size_t NP = it.adjoint ? (size_t)std::max(1, it.batched ? npg : P.nparam) : 0;
+        const size_t pm = it.batched ? (it.adjoint ? 2 : 1) * 8 * (size_t)std::max(1, npg) : 0;
+        j.smem = (jit_double_buffer(dtype, it.adjoint, P.k) ? 2 : 1) * (it.adjoint ? 2 : 1) * T * es +
+                 (pm + 2 * NP * (kTileThreads / 32)) * rs;
+        j.nparam_gates = npg;
         const size_t G = P.gate_count > 0 ? P.gate_count : 1;
         size_t bytes = G * 8 * rs;
-        if (adjoint) {
-            const size_t NP = P.nparam > 0 ? P.nparam : 1;
+        if (it.adjoint && !it.batched) {
             bytes += NP * 8 * rs;
             bytes += NP * sizeof(int);
         }
+        if (it.batched) bytes = ((bytes + 3) & ~size_t(3)) + G * 2 * sizeof(int);
         j.arg_bytes = (bytes + 15) & ~size_t(15);
+        j.batched = it.batched;
     }
     return true;
 }
 
-cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
-                            double *part, size_t part_stride, cudaStream_t st) {
-    Module *m;
-    cudaKernel_t kern;
-    int occ = 1;
+bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std::vector<JitPass> *out,
+                         std::string *err, double *compile_seconds, int *compiled_modules) {
+    return jit_prepare_programs(dtype, {JitRequest{&prog, adjoint, false, out}}, err, compile_seconds, compiled_modules);
+}
+
+namespace {
+
+// The kernel of a compiled pass on the current device: loaded on first use, its dynamic shared
+// memory allowed, its resident blocks per SM looked up once.
+cudaError_t jit_kernel(const JitPass &jp, cudaKernel_t *kern, int *occ) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (jp.entry < 0 || jp.entry >= (int)g_modules.size()) return cudaErrorInvalidValue;
-        m = g_modules[jp.entry].get();
-        if (!m->lib) {
-            cudaError_t e = cudaLibraryLoadData(&m->lib, m->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (jp.entry < 0 || jp.entry >= (int)g_modules.size()) return cudaErrorInvalidValue;
+    Module *m = g_modules[jp.entry].get();
+    if (!m->lib) {
+        cudaError_t e = cudaLibraryLoadData(&m->lib, m->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e != cudaSuccess) return e;
+        m->kernels.resize(m->names.size());
+        for (size_t i = 0; i < m->names.size(); ++i) {
+            e = cudaLibraryGetKernel(&m->kernels[i], m->lib, m->names[i].c_str());
             if (e != cudaSuccess) return e;
-            m->kernels.resize(m->names.size());
-            for (size_t i = 0; i < m->names.size(); ++i) {
-                e = cudaLibraryGetKernel(&m->kernels[i], m->lib, m->names[i].c_str());
-                if (e != cudaSuccess) return e;
-            }
         }
-        kern = m->kernels[jp.kernel];
-        auto &ss = m->smem_set[dev];
-        auto &oc = m->occ[dev];
-        if (ss.size() < m->kernels.size()) {
-            ss.resize(m->kernels.size(), 0);
-            oc.resize(m->kernels.size(), 0);
-        }
-        if (jp.smem > 48 * 1024 && ss[jp.kernel] < jp.smem) {
-            cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(kern),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jp.smem);
-            if (e != cudaSuccess) return e;
-            ss[jp.kernel] = jp.smem;
-            oc[jp.kernel] = 0;
-        }
-        if (oc[jp.kernel] == 0) {
-            int v = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, reinterpret_cast<const void *>(kern), kTileThreads,
-                                                              jp.smem) != cudaSuccess ||
-                v < 1) {
-                cudaGetLastError();
-                v = 1;
-            }
-            oc[jp.kernel] = v;
-        }
-        occ = oc[jp.kernel];
     }
+    *kern = m->kernels[jp.kernel];
+    auto &ss = m->smem_set[dev];
+    auto &oc = m->occ[dev];
+    if (ss.size() < m->kernels.size()) {
+        ss.resize(m->kernels.size(), 0);
+        oc.resize(m->kernels.size(), 0);
+    }
+    if (jp.smem > 48 * 1024 && ss[jp.kernel] < jp.smem) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(*kern),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jp.smem);
+        if (e != cudaSuccess) return e;
+        ss[jp.kernel] = jp.smem;
+        oc[jp.kernel] = 0;
+    }
+    if (oc[jp.kernel] == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, reinterpret_cast<const void *>(*kern), kTileThreads,
+                                                          jp.smem) != cudaSuccess ||
+            v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        oc[jp.kernel] = v;
+    }
+    *occ = oc[jp.kernel];
+    return cudaSuccess;
+}
+
+// The fixed matrices of a pass's gates (state precision), row-major 8 reals each.
+void put_matrices(int dtype, const FusedProgram &prog, const TilePass &P, unsigned char *dst) {
+    const size_t rs = dtype == QS_C64 ? 4 : 8;
+    const RegGate *g = prog.gates.data() + P.gate_begin;
+    for (int i = 0; i < P.gate_count; ++i) {
+        if (dtype == QS_C64)
+            std::memcpy(dst + (size_t)i * 8 * rs, g[i].Uf, 8 * rs);
+        else
+            std::memcpy(dst + (size_t)i * 8 * rs, g[i].U, 8 * rs);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
+                            double *part, size_t part_stride, cudaStream_t st) {
+    cudaKernel_t kern;
+    int occ = 1;
+    cudaError_t e = jit_kernel(jp, &kern, &occ);
+    if (e != cudaSuccess) return e;
     const TilePass &P = prog.passes[p];
     const bool adjoint = lam != nullptr;
     // parameter block: matrices (state precision), derivatives, gradient slots
@@ -734,12 +903,7 @@ cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &pr
     const RegGate *g = prog.gates.data() + P.gate_begin;
     const size_t rs = dtype == QS_C64 ? 4 : 8;
     const size_t G1 = G > 0 ? G : 1;
-    for (int i = 0; i < G; ++i) {
-        if (dtype == QS_C64)
-            std::memcpy(&blk[(size_t)i * 8 * rs], g[i].Uf, 8 * rs);
-        else
-            std::memcpy(&blk[(size_t)i * 8 * rs], g[i].U, 8 * rs);
-    }
+    put_matrices(dtype, prog, P, blk.data());
     if (adjoint) {
         const size_t NP1 = P.nparam > 0 ? P.nparam : 1;
         unsigned char *d = &blk[G1 * 8 * rs];
@@ -761,6 +925,35 @@ cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &pr
     void *args_adj[] = {&psi, &lam, &part, &stride, blk.data()};
     return cudaLaunchKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kTileThreads),
                             adjoint ? args_adj : args_fwd, jp.smem, st);
+}
+
+cudaError_t launch_jit_pass_batched(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi,
+                                    void *lam, double *part, uint64_t stride, uint64_t nstates, const void *cs,
+                                    uint32_t cs_stride, cudaStream_t st) {
+    if (!jp.batched) return cudaErrorInvalidValue;
+    cudaKernel_t kern;
+    int occ = 1;
+    cudaError_t e = jit_kernel(jp, &kern, &occ);
+    if (e != cudaSuccess) return e;
+    const TilePass &P = prog.passes[p];
+    std::vector<unsigned char> blk(jp.arg_bytes, 0);
+    const int G = P.gate_count;
+    const size_t rs = dtype == QS_C64 ? 4 : 8;
+    const size_t G1 = G > 0 ? G : 1;
+    put_matrices(dtype, prog, P, blk.data());
+    int *pix = reinterpret_cast<int *>(blk.data() + ((G1 * 8 * rs + 3) & ~size_t(3)));
+    const RegGate *g = prog.gates.data() + P.gate_begin;
+    for (int i = 0; i < G; ++i) {
+        pix[2 * i] = g[i].pidx;
+        pix[2 * i + 1] = g[i].pidx2;
+    }
+    const uint64_t total = nstates * P.ntiles;
+    const uint64_t cap = (uint64_t)device_sm_count() * occ;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(total, cap));
+    unsigned long long stride_ = stride, nst = nstates;
+    unsigned cs_st = cs_stride;
+    void *args[] = {&psi, &lam, &part, &stride_, &nst, const_cast<void **>(&cs), &cs_st, blk.data()};
+    return cudaLaunchKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kTileThreads), args, jp.smem, st);
 }
 
 }  // namespace qs

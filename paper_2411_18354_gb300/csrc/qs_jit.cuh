@@ -29,7 +29,21 @@ struct JitPass {
     int kernel = -1;          // kernel index inside the module
     size_t smem = 0;          // dynamic shared memory of one block
     size_t arg_bytes = 0;     // size of the parameter block (matrices)
+    bool batched = false;     // runs over the states of a batch program
+    int nparam_gates = 0;     // batch: parameterised gates of the pass
 };
+
+// One program to compile: its passes, forward or reverse sweep, single state or batch.
+struct JitRequest {
+    const FusedProgram *prog;
+    bool adjoint;
+    bool batched;
+    std::vector<JitPass> *out;
+};
+
+// Compile the passes of several programs at once (new kernels compiled concurrently).
+bool jit_prepare_programs(int dtype, const std::vector<JitRequest> &reqs, std::string *err,
+                          double *compile_seconds = nullptr, int *compiled_modules = nullptr);
 
 // Generate (and compile, on a cache miss) the kernels of every tile pass of `prog`. Forward
 // programs: lam_mode = false; adjoint sweep: true. Fills `out` with one JitPass per pass.
@@ -42,11 +56,24 @@ bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std:
 cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
                             double *part, size_t part_stride, cudaStream_t st);
 
+// Launch batched pass `p` over `nstates` states whose vectors start `stride` amplitudes apart at
+// psi (and lam, sweep), with their (cos, sin) of theta/2 at cs (cs_stride reals per state);
+// sweep: part receives per tile and parameterised gate J the partial of Re <lambda| dU psi> at
+// [(J * nstates + state) * tiles_per_state + tile].
+cudaError_t launch_jit_pass_batched(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi,
+                                    void *lam, double *part, uint64_t stride, uint64_t nstates, const void *cs,
+                                    uint32_t cs_stride, cudaStream_t st);
+
 // Whether the kernel of a pass with 2^k-amplitude tiles double-buffers them.
 bool jit_double_buffer(int dtype, bool adjoint, int k);
 
 // The generated source of one pass (exposed for tests of the generator).
+// batched: the kernel runs the pass over `nstates` states of one batch program at once (tile
+// index = state * tiles per state + tile), each state's vectors `stride` amplitudes apart,
+// the parameterised gates' matrices formed per tile from that state's (cos, sin) of theta/2
+// (RegGate pkind / pkind2 / pidx / pidx2), and in the sweep the gradient partial of every
+// parameterised gate written per tile.
 std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const TileGroup *groups,
-                            const RegGate *gates, const char *kname);
+                            const RegGate *gates, const char *kname, bool batched = false);
 
 }  // namespace qs

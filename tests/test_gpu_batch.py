@@ -38,18 +38,23 @@ def _run_batch(qs, ns, circuits, nparams, thetas, dtype, flags=None, **tune):
     return e, [g[offs[s]:offs[s + 1]] for s in range(len(ns))], info
 
 
+@pytest.mark.parametrize("jit", [False, True])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("tune", [{}, {"small_bits": 5, "tile_bits": 5, "max_pass_gates": 3}])
-def test_batch_ansatz_against_parameter_shift(qs, dtype, tune):
+@pytest.mark.parametrize("tune", [{}, {"small_bits": 5, "tile_bits": 5, "max_pass_gates": 3},
+                                  {"small_bits": 5, "tile_bits": 7, "max_pass_gates": 64}])
+def test_batch_ansatz_against_parameter_shift(qs, dtype, tune, jit):
     """States of 2..9 qubits running the ansatz (2 layers) with their own parameters: energies
-    and gradients against the oracle's parameter-shift rule. The second tuning forces the
-    large-state path (tile passes through global memory) for n > 5."""
+    and gradients against the oracle's parameter-shift rule. The second and third tunings
+    force the large-state path for n > 5 (tile passes through global memory; with
+    QS_FLAG_JIT the pass-major path: every pass compiled for its shape and run over all
+    states of one size at once)."""
     rng = np.random.default_rng(44)
     ns = [int(v) for v in rng.integers(2, 10, size=14)]
     circuits = [W.hea_circuit(n, 2) for n in ns]
     nparams = [4 * n for n in ns]
     thetas = [rng.uniform(0, 2 * np.pi, size=p) for p in nparams]
-    e, g, _ = _run_batch(qs, ns, circuits, nparams, thetas, dtype, **tune)
+    flags = qs.QS_FLAG_GRAPH | (qs.QS_FLAG_JIT if jit else 0)
+    e, g, _ = _run_batch(qs, ns, circuits, nparams, thetas, dtype, flags=flags, **tune)
     for s, n in enumerate(ns):
         assert abs(e[s] - oracle.energy(n, circuits[s], thetas[s])) <= TOL[dtype], s
         ps = oracle.param_shift_grad(n, circuits[s], thetas[s])
@@ -78,17 +83,21 @@ def _random_param_circuit(rng, n, nparam, count):
     return W.gate_list(gl)
 
 
+@pytest.mark.parametrize("jit", [False, True])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("tune", [{}, {"small_bits": 4, "tile_bits": 5, "max_pass_gates": 5}])
-def test_batch_random_circuits_against_finite_differences(qs, dtype, tune):
+def test_batch_random_circuits_against_finite_differences(qs, dtype, tune, jit):
     """Random controlled (also negatively controlled) RY/RZ with shared parameters, fixed
-    Haar / phase / X gates, per-state gate lists: against oracle central differences."""
+    Haar / phase / X gates, per-state gate lists: against oracle central differences (also
+    with two states sharing one gate list, which the pass-major path runs together)."""
     rng = np.random.default_rng(7)
-    ns = [3, 6, 8, 9, 7, 5]
-    nparams = [5, 6, 3, 7, 4, 2]
-    circuits = [_random_param_circuit(rng, n, p, 40) for n, p in zip(ns, nparams)]
+    ns = [3, 6, 8, 9, 7, 5, 8]
+    nparams = [5, 6, 3, 7, 4, 2, 3]
+    circuits = [_random_param_circuit(rng, n, p, 40) for n, p in zip(ns[:-1], nparams[:-1])]
+    circuits.append(circuits[2])
     thetas = [rng.uniform(0, 2 * np.pi, size=p) for p in nparams]
-    e, g, _ = _run_batch(qs, ns, circuits, nparams, thetas, dtype, **tune)
+    flags = qs.QS_FLAG_GRAPH | (qs.QS_FLAG_JIT if jit else 0)
+    e, g, _ = _run_batch(qs, ns, circuits, nparams, thetas, dtype, flags=flags, **tune)
     tol = 1e-4 if dtype == "c64" else 1e-6
     for s, n in enumerate(ns):
         assert abs(e[s] - oracle.energy(n, circuits[s], thetas[s])) <= tol
@@ -109,16 +118,19 @@ def test_batch_graph_and_direct_launch_agree(qs):
         assert np.array_equal(a, b)
 
 
-def test_batch_full_workload_sampled(qs):
+@pytest.mark.parametrize("jit", [False, True])
+def test_batch_full_workload_sampled(qs, jit):
     """The batching workload at full size: 4096 states, n uniform in 10..20, 8 layers of the
-    ansatz, complex64. Sampled states are checked against the oracle: parameter shift for
-    two n = 10 states, central differences on two parameters of one n = 20 state."""
+    ansatz, complex64, interpreted and pass-major (QS_FLAG_JIT). Sampled states are checked
+    against the oracle: parameter shift for two n = 10 states, central differences on two
+    parameters of one n = 20 state."""
     ns, thetas = W.batch_workload(4096, 10, 20, 8, seed=4)
     ns = [int(v) for v in ns]
     circ = {n: W.hea_circuit(n, 8) for n in set(ns)}
     circuits = [circ[n] for n in ns]
     nparams = [16 * n for n in ns]
-    e, g, info = _run_batch(qs, ns, circuits, nparams, thetas, "c64")
+    e, g, info = _run_batch(qs, ns, circuits, nparams, thetas, "c64",
+                            flags=qs.QS_FLAG_GRAPH | (qs.QS_FLAG_JIT if jit else 0))
     assert np.all(np.isfinite(e))
     small = [s for s, n in enumerate(ns) if n == 10][:2]
     for s in small:
@@ -141,3 +153,20 @@ def test_batch_rejects_bad_input(qs):
         qs.Batch([5], [W.hea_circuit(5, 1)], [3], "c64")  # parameter index beyond the state's parameters
     with pytest.raises(qs.QsError):
         qs.Batch([5], [W.hea_circuit(5, 1)], [10], "c64", tile_bits=4)
+
+
+def test_batch_jit_matches_interpreted(qs):
+    """The pass-major path and the persistent kernel agree on a 40-state batch of 4..14
+    qubits (3 layers), directly launched and as a graph."""
+    rng = np.random.default_rng(3)
+    ns = [int(v) for v in rng.integers(4, 15, size=40)]
+    circuits = [W.hea_circuit(n, 3) for n in ns]
+    nparams = [6 * n for n in ns]
+    thetas = [rng.uniform(0, 2 * np.pi, size=p) for p in nparams]
+    tune = {"small_bits": 8, "tile_bits": 8}
+    e1, g1, _ = _run_batch(qs, ns, circuits, nparams, thetas, "c64", flags=qs.QS_FLAG_GRAPH, **tune)
+    for flags in (qs.QS_FLAG_JIT, qs.QS_FLAG_JIT | qs.QS_FLAG_GRAPH):
+        e2, g2, _ = _run_batch(qs, ns, circuits, nparams, thetas, "c64", flags=flags, **tune)
+        assert np.max(np.abs(e1 - e2)) <= 1e-5
+        for a, b in zip(g1, g2):
+            assert np.max(np.abs(a - b)) <= 1e-4
