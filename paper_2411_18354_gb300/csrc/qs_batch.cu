@@ -166,6 +166,11 @@ qs_status ensure_jit(qs_batch *b) {
     std::string err;
     if (!reqs.empty() && !jit_prepare_programs(b->dtype, reqs, &err, &b->jit_compile_s))
         return set_error(QS_ECUDA, ("qs_batch_run: " + err).c_str());
+    for (BatchJitProg &jp : b->jprogs) {  // loaded before any stream capture records them
+        cudaError_t e = jit_load(jp.jf);
+        if (e == cudaSuccess) e = jit_load(jp.ja);
+        if (e != cudaSuccess) return cuda_fail(e, "qs_batch_run: loading compiled passes");
+    }
     auto dev_alloc = [](void **p, size_t bytes) {
         cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
         if (e != cudaSuccess) {

@@ -643,6 +643,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         std::string jerr;
         if (!jit_prepare_program(s->dtype, false, prog, &jit, &jerr))
             return set_error(QS_ECUDA, ("qs_apply_circuit: " + jerr).c_str());
+        cudaError_t e = jit_load(jit);  // before any stream capture below
+        if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit: loading compiled passes");
     }
     const std::vector<JitPass> *jp = (flags & QS_FLAG_JIT) ? &jit : nullptr;
     const size_t table_bytes = fuse ? program_table_bytes(prog) : 0;

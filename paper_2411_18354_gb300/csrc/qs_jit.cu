@@ -889,6 +889,16 @@ void put_matrices(int dtype, const FusedProgram &prog, const TilePass &P, unsign
 
 }  // namespace
 
+cudaError_t jit_load(const std::vector<JitPass> &passes) {
+    for (const JitPass &jp : passes) {
+        cudaKernel_t kern;
+        int occ = 0;
+        cudaError_t e = jit_kernel(jp, &kern, &occ);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
                             double *part, size_t part_stride, cudaStream_t st) {
     cudaKernel_t kern;

@@ -51,6 +51,10 @@ bool jit_prepare_programs(int dtype, const std::vector<JitRequest> &reqs, std::s
 bool jit_prepare_program(int dtype, bool adjoint, const FusedProgram &prog, std::vector<JitPass> *out,
                          std::string *err, double *compile_seconds = nullptr, int *compiled_modules = nullptr);
 
+// Load the compiled kernels of these passes on the current device and set their launch
+// attributes (done before a stream capture records launches of them).
+cudaError_t jit_load(const std::vector<JitPass> &passes);
+
 // Launch pass `p` of `prog` with its compiled kernel. Adjoint: lam, part (gradient partials
 // [slot][part_stride]) as for launch_tile_pass.
 cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &prog, int p, void *psi, void *lam,
