@@ -896,10 +896,10 @@ def run_ncu_batch(args):
     ns = [16] * 304
     circ = W.hea_circuit(16, 2)
     th = torch.tensor(np.random.default_rng(1).uniform(0, 6.28, size=304 * 64), dtype=torch.float64, device="cuda")
-    b = qs.Batch(ns, [circ] * 304, [64] * 304, "c64")
+    b = qs.Batch(ns, [circ] * 304, [64] * 304, "c64", small_bits=12, tile_bits=12)
     en = torch.zeros(304, dtype=torch.float64, device="cuda")
     gr = torch.zeros(304 * 64, dtype=torch.float64, device="cuda")
-    b.run(th, en, gr, 0)
+    b.run(th, en, gr, qs.QS_FLAG_JIT if args.jit else 0)
     torch.cuda.synchronize()
     b.close()
     print("ncu batch case done")
