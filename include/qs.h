@@ -208,6 +208,18 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
  * FP64 pipe). Not part of the paper's method. */
 qs_status qs_measure_fma_peak(qs_dtype dtype, int iters, void *stream, double *flops_per_s);
 
+/* Debug build (the library compiled with QS_DEBUG_CHECKS, libqs_debug.so): the gate,
+ * sweep, tile-pass, diagonal-run and compiled single-state pass kernels check every global
+ * access against a state of n_amps amplitudes (0: no check) and, when `counts` (device,
+ * count_n uint32 entries) is given, count the writes of each amplitude with atomics. An access
+ * outside the state is not made; the status word records it (bit 0) with one failing index.
+ * qs_debug_configure synchronises the device, sets the checks and clears the status;
+ * qs_debug_status synchronises and reads it. In the release build both return
+ * QS_EUNSUPPORTED and qs_debug_build() returns 0. Not part of the paper's method. */
+int qs_debug_build(void);
+qs_status qs_debug_configure(uint64_t n_amps, unsigned int *counts, uint64_t count_n);
+qs_status qs_debug_status(unsigned int *status, uint64_t *first_bad);
+
 /* Compile the tile-pass kernels that qs_apply_circuit (adjoint = 0) or qs_adjoint_grad
  * (adjoint = 1: the forward and the reverse-sweep programs) would launch for these gates with
  * QS_FLAG_FUSE | QS_FLAG_JIT, without running anything; needs no device or state.

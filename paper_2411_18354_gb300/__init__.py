@@ -17,7 +17,7 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     QS_C64, QS_C128, QS_FLAG_ADJOINT, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_JIT, QS_FLAG_MASKED, QS_FLAG_OUT_DEVICE, QS_GATE_U,
     QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_compile, qs_circuit_schedule,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
-    qs_measure_fma_peak,
+    qs_measure_fma_peak, qs_debug_build, qs_debug_configure, qs_debug_status,
     qs_state_alloc, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
     qs_set_l2_fetch_bytes, qs_set_tile_bits,
     qs_state_copy_from_host, qs_state_copy_from_host_async, qs_state_copy_to_host, qs_state_copy_to_host_async,
@@ -165,7 +165,7 @@ class Batch:
             pass
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, debug: bool = False) -> str:
     from .build import build as _b
 
-    return _b(force=force)
+    return _b(force=force, debug=debug)

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-from .build import LIB_PATH
+from .build import DEBUG_LIB_PATH, LIB_PATH
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_C64, QS_C128 = 0, 1
@@ -58,6 +58,9 @@ _SIGNATURES = [
     ("qs_circuit_compile", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]),
     ("qs_measure_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _dp]),
+    ("qs_debug_build", ctypes.c_int, []),
+    ("qs_debug_configure", ctypes.c_int, [_u64, _vp, _u64]),
+    ("qs_debug_status", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(_u64)]),
     ("qs_expect_z", ctypes.c_int, [_c_state_p, _dp, _dp, ctypes.c_int]),
     ("qs_expect_z_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _dp, _dp]),
     ("qs_adjoint_grad", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _dp, _dp, ctypes.c_int]),
@@ -77,13 +80,20 @@ _SIGNATURES = [
 _lib = None
 
 
+def lib_path() -> str:
+    """libqs.so, or its debug build when QS_LIB_VARIANT=debug."""
+    return DEBUG_LIB_PATH if os.environ.get("QS_LIB_VARIANT") == "debug" else LIB_PATH
+
+
 def lib():
     """Load libqs.so (built in-tree by ``paper_2411_18354_gb300.build``)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libqs.so not found at {LIB_PATH}: build it with paper_2411_18354_gb300.build.build()")
-        L = ctypes.CDLL(LIB_PATH)
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(f"{os.path.basename(path)} not found at {path}: build it with "
+                              f"paper_2411_18354_gb300.build.build()")
+        L = ctypes.CDLL(path)
         for name, res, args in _SIGNATURES:
             fn = getattr(L, name)
             fn.restype = res
@@ -251,6 +261,24 @@ def qs_circuit_compile(n: int, dtype: int, gates, theta=None, flags: int = QS_FL
     _check(lib().qs_circuit_compile(n, dtype, gp, g.size, tp, nt, flags, 1 if adjoint else 0, ctypes.byref(secs),
                                     ctypes.byref(passes)))
     return {"compile_seconds": secs.value, "passes": passes.value}
+
+
+def qs_debug_build() -> bool:
+    return bool(lib().qs_debug_build())
+
+
+def qs_debug_configure(n_amps: int, counts_dev: int = 0, count_n: int = 0) -> None:
+    """Debug build: check accesses against n_amps amplitudes (0: off) and count writes per
+    amplitude into the device array counts_dev (uint32, count_n entries; 0: off)."""
+    _check(lib().qs_debug_configure(n_amps, _vp(counts_dev or None), count_n))
+
+
+def qs_debug_status():
+    """Debug build: (status word, an index that failed the bounds check)."""
+    st = ctypes.c_uint(0)
+    bad = _u64(0)
+    _check(lib().qs_debug_status(ctypes.byref(st), ctypes.byref(bad)))
+    return st.value, bad.value
 
 
 def qs_measure_fma_peak(dtype: int, iters: int = 1 << 16, stream: int = 0) -> float:

@@ -19,6 +19,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libqs.so")
+# The debug build (QS_DEBUG_CHECKS): every global access of the gate, tile-pass, diagonal-run and
+# sweep kernels checked against the state under test, writes counted on request (see
+# csrc/qs_debug.cuh); loaded instead of libqs.so when QS_LIB_VARIANT=debug.
+DEBUG_BUILD_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB_PATH = os.path.join(DEBUG_BUILD_DIR, "libqs_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,10 +42,10 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB_PATH):
+def _stale(lib_path: str = LIB_PATH) -> bool:
+    if not os.path.exists(lib_path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(lib_path)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
@@ -48,14 +53,19 @@ def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    if not force and not _stale():
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    lib_path = DEBUG_LIB_PATH if debug else LIB_PATH
+    build_dir = DEBUG_BUILD_DIR if debug else BUILD_DIR
+    if not force and not _stale(lib_path):
+        return lib_path
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    flags = _flags() + list(extra_flags or [])
+    os.makedirs(build_dir, exist_ok=True)
+    # the debug build's status word is one __device__ variable shared by every translation
+    # unit: relocatable device code, linked into the shared library
+    dbg_flags = ["-DQS_DEBUG_CHECKS=1", "-rdc=true"] if debug else []
+    flags = _flags() + dbg_flags + list(extra_flags or [])
     srcs = _sources()
-    objs = [os.path.join(BUILD_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(src_obj):
         src, obj = src_obj
@@ -70,15 +80,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     workers = max(1, min(len(srcs), os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(workers) as ex:
         list(ex.map(compile_one, zip(srcs, objs)))
-    tmp = LIB_PATH + ".tmp"
+    tmp = lib_path + ".tmp"
     # NVRTC compiles the shape-specialised tile passes at run time (QS_FLAG_JIT)
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker", f"-rpath,{cuda_lib}"]
+    cmd = [nvcc, *ARCH, *(["-rdc=true"] if debug else []), "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker",
+           f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

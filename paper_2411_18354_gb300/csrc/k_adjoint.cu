@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "k_gate.cuh"
+#include "qs_debug.cuh"
 
 namespace qs {
 
@@ -34,6 +35,7 @@ k_adj_step(typename CxT<Real>::T *__restrict__ psi, typename CxT<Real>::T *__res
     const Idx step = (Idx)gridDim.x * kGateThreads;
     for (Idx u = (Idx)blockIdx.x * kGateThreads + threadIdx.x; u < units; u += step) {
         const Idx lo = deposit<Idx, NS>(u << r, g);
+        if (LAY == LAY_ADJ ? !QS_DBG_OK(lo, A) : (!QS_DBG_OK(lo, R) || !QS_DBG_OK(lo | g.tbit, R))) continue;
         T2 px[A], py[(LAY == LAY_SPLIT) ? R : 1], lx[A], ly[(LAY == LAY_SPLIT) ? R : 1];
         if (LAY == LAY_ADJ) {
             Vec<Real, A>::ld(psi + lo, px);
@@ -61,7 +63,10 @@ k_adj_step(typename CxT<Real>::T *__restrict__ psi, typename CxT<Real>::T *__res
         if (LAY == LAY_ADJ) {
             Vec<Real, A>::st(psi + lo, px);
             Vec<Real, A>::st(lam + lo, lx);
+            QS_DBG_WRITE(lo, A);
         } else {
+            QS_DBG_WRITE(lo, R);
+            QS_DBG_WRITE(lo | g.tbit, R);
             Vec<Real, R>::st(psi + lo, px);
             Vec<Real, R>::st(psi + (lo | g.tbit), py);
             Vec<Real, R>::st(lam + lo, lx);

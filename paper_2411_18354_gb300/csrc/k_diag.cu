@@ -3,6 +3,7 @@
 #include <cstring>
 
 #include "k_diag.cuh"
+#include "qs_debug.cuh"
 #include "k_gate.cuh"
 
 namespace qs {
@@ -353,6 +354,7 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
             const uint64_t c0 = ((cc >> p) << (p + 1)) | (cc & ((1ull << p) - 1ull));
             const uint64_t b0 = c0 << kDiagChunkBits, b1 = b0 | (1ull << nc.lead_t);
             T2 x[E], y[E], f[E];
+            if (!QS_DBG_OK(b0, E) || !QS_DBG_OK(b1, E)) continue;
             ld8(psi + b0, x);
             ld8(psi + b1, y);
 #pragma unroll
@@ -367,6 +369,8 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
             }
             st8(psi + b0, x);
             st8(psi + b1, y);
+            QS_DBG_WRITE(b0, E);
+            QS_DBG_WRITE(b1, E);
         } else {
             uint64_t c = cc;  // insert the fixed bits, lowest position first
             for (int i = 0; i < nc.nfix; ++i) {
@@ -377,6 +381,7 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
             // the chunk's loads are issued before its factors are formed, so that their latency
             // overlaps that work (the compact counter leaves few chunks whose factors are all 1)
             T2 x[E], f[E];
+            if (!QS_DBG_OK(base, E)) continue;
             ld8(psi + base, x);
             const bool touched = chunk_factors<Real>(base, sg, count, nc, lane, f);
             if (LEAD == 0 && !touched) continue;  // every factor of this chunk is 1: no store
@@ -390,6 +395,7 @@ __global__ void __launch_bounds__(256) k_diag_run(typename CxT<Real>::T *__restr
                 for (int e = 0; e < E; ++e) x[e] = cmul<T2, Real>(f[e].x, f[e].y, x[e]);
             }
             st8(psi + base, x);
+            QS_DBG_WRITE(base, E);
         }
     }
 }

@@ -16,6 +16,7 @@
 // (diagonal) or scale one side only (diagonal with a 1 on the other side).
 #pragma once
 
+#include "qs_debug.cuh"
 #include "qs_internal.cuh"
 
 namespace qs {
@@ -177,6 +178,13 @@ k_gate(typename CxT<Real>::T *__restrict__ psi, const DevGate<Real, Idx> g, Idx 
             on[k] = u < units;
             lo[k] = deposit<Idx, NS>(u << r, g);
             if (MASKED) on[k] = on[k] && ((lo[k] & g.cmask) == g.cvals);
+#ifdef QS_DEBUG_CHECKS
+            if (on[k]) {
+                if (LAY == LAY_ADJ) on[k] = QS_DBG_OK(lo[k], A);
+                else if (OP == OP_SIDE) on[k] = QS_DBG_OK(lo[k] | (side ? g.tbit : (Idx)0), R);
+                else on[k] = QS_DBG_OK(lo[k], R) && QS_DBG_OK(lo[k] | g.tbit, R);
+            }
+#endif
             if (on[k]) {
                 if (LAY == LAY_ADJ) {
                     Vec<Real, A>::ld(psi + lo[k], x[k]);
@@ -195,15 +203,19 @@ k_gate(typename CxT<Real>::T *__restrict__ psi, const DevGate<Real, Idx> g, Idx 
 #pragma unroll
                 for (int i = 0; i < R; ++i) pair_update<OP, T2, Real>(x[k][2 * i], x[k][2 * i + 1], g.m);
                 Vec<Real, A>::st(psi + lo[k], x[k]);
+                QS_DBG_WRITE(lo[k], A);
             } else if (OP == OP_SIDE) {
 #pragma unroll
                 for (int i = 0; i < R; ++i) x[k][i] = cmul<T2, Real>(g.m[0], g.m[1], x[k][i]);
                 Vec<Real, R>::st(psi + (lo[k] | (side ? g.tbit : (Idx)0)), x[k]);
+                QS_DBG_WRITE(lo[k] | (side ? g.tbit : (Idx)0), R);
             } else {
 #pragma unroll
                 for (int i = 0; i < R; ++i) pair_update<OP, T2, Real>(x[k][i], y[k][i], g.m);
                 Vec<Real, R>::st(psi + lo[k], x[k]);
                 Vec<Real, R>::st(psi + (lo[k] | g.tbit), y[k]);
+                QS_DBG_WRITE(lo[k], R);
+                QS_DBG_WRITE(lo[k] | g.tbit, R);
             }
         }
     }

@@ -446,6 +446,7 @@ __device__ __forceinline__ void load_tile(const TileAddr &ta, const uint64_t *g_
                                           const typename TileT<Real>::T2 *src, typename TileT<Real>::T2 *dst) {
     const uint64_t g0 = base | ta.g_t;
     for (uint32_t j = 0; j < ta.steps; ++j) {
+        if (!QS_DBG_OK(g0 | g_j[j], TileT<Real>::VEC)) continue;
         const typename TileT<Real>::T2 *g = src + (g0 | g_j[j]);
         const uint32_t s = ta.s_t ^ s_j[j];
         if (sizeof(Real) == 4) {
@@ -466,6 +467,8 @@ __device__ __forceinline__ void store_tile(const TileAddr &ta, const uint64_t *g
     constexpr int VEC = TileT<Real>::VEC;
     const uint64_t g0 = base | ta.g_t;
     for (uint32_t j = 0; j < ta.steps; ++j) {
+        if (!QS_DBG_OK(g0 | g_j[j], VEC)) continue;
+        QS_DBG_WRITE(g0 | g_j[j], VEC);
         const uint32_t s = ta.s_t ^ s_j[j];
         V x;
         T2 *xs = reinterpret_cast<T2 *>(&x);

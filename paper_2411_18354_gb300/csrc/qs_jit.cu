@@ -26,6 +26,13 @@
 namespace qs {
 
 int device_sm_count();
+void *debug_state_address();
+
+#ifdef QS_DEBUG_CHECKS
+constexpr bool kDebugBuild = true;
+#else
+constexpr bool kDebugBuild = false;
+#endif
 
 namespace {
 
@@ -291,8 +298,19 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
         refs.d[i] = b;
         refs.acc.push_back(batched ? pj[i] : pg[i].slot);
     }
+    // debug build: every global access checked against the state's size (2^n), writes counted
+    const bool dbg = kDebugBuild && !batched;
     Out o;
     preamble(o, dbl);
+    if (dbg) {
+        o.f("struct DebugState { unsigned status, pad; u64 n_amps; unsigned *counts; u64 count_n; u64 first_bad; };\n");
+        o.f("__device__ __forceinline__ bool dok(DebugState *d, u64 i, int span) {\n"
+            "  if (d->n_amps == 0 || i + span <= d->n_amps) return true;\n"
+            "  d->first_bad = i; atomicOr(&d->status, 1u); return false;\n}\n");
+        o.f("__device__ __forceinline__ void dcount(DebugState *d, u64 i, int span) {\n"
+            "  if (!d->counts) return;\n"
+            "  for (int j = 0; j < span; ++j) if (i + j < d->count_n) atomicAdd(d->counts + i + j, 1u);\n}\n");
+    }
     // parameter block: the fixed matrices of the pass's gates (U, or U^dagger in the adjoint
     // sweep); single state: the derivatives of its parameterised gates and their global
     // gradient slots; batch: the parameter indices of the parameterised gates
@@ -309,11 +327,11 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
             T, minb, kname);
     else if (adjoint)
         o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, T2 *__restrict__ lam, "
-            "double *__restrict__ part, u64 part_stride, const __grid_constant__ A a) {\n",
-            T, minb, kname);
+            "double *__restrict__ part, u64 part_stride, const __grid_constant__ A a%s) {\n",
+            T, minb, kname, dbg ? ", DebugState *dbg" : "");
     else
-        o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, const __grid_constant__ A a) {\n",
-            T, minb, kname);
+        o.f("extern \"C\" __global__ void __launch_bounds__(%d, %d) %s(T2 *__restrict__ psi, const __grid_constant__ A a%s) {\n",
+            T, minb, kname, dbg ? ", DebugState *dbg" : "");
     const bool db = jit_double_buffer(dtype, adjoint, k);
     const uint32_t TILE = 1u << k;
     const uint32_t BUF = (adjoint ? 2 : 1) * TILE;  // one buffer: psi tile (and lambda tile)
@@ -381,6 +399,10 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
             const uint32_t oj = j * T * VEC;
             const unsigned long long gj = (unsigned long long)scatter_host(P, oj);
             const uint32_t sj = tile_swizzle(oj, SW);
+            if (dbg) {
+                o.f("    if (dok(dbg, %s | g_t | 0x%llxull, %d)) ", bname, gj, VEC);
+                if (!load) o.f("{ dcount(dbg, %s | g_t | 0x%llxull, %d); ", bname, gj, VEC);
+            }
             if (load && !dbl)
                 o.f("    { const T2 *g = %s + (%s | g_t | 0x%llxull); const u32 s = s_t ^ %uu; "
                     "cp8(%s + s, g); cp8(%s + (s ^ %uu), g + 1); }\n",
@@ -393,6 +415,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                     sj, tname, tname, s1, gname, bname, gj);
             else
                 o.f("    %s[%s | g_t | 0x%llxull] = %s[s_t ^ %uu];\n", gname, bname, gj, tname, sj);
+            if (dbg && !load) o.f("    }\n");
         }
         if (cp_guard) o.f("    }\n");
     };
@@ -931,8 +954,9 @@ cudaError_t launch_jit_pass(int dtype, const JitPass &jp, const FusedProgram &pr
     if (adjoint) cap = std::min<uint64_t>(cap, part_stride);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(P.ntiles, cap));
     unsigned long long stride = part_stride;
-    void *args_fwd[] = {&psi, blk.data()};
-    void *args_adj[] = {&psi, &lam, &part, &stride, blk.data()};
+    void *dbg = debug_state_address();  // debug build only: the generated kernels take it last
+    void *args_fwd[] = {&psi, blk.data(), &dbg};
+    void *args_adj[] = {&psi, &lam, &part, &stride, blk.data(), &dbg};
     return cudaLaunchKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(kTileThreads),
                             adjoint ? args_adj : args_fwd, jp.smem, st);
 }
