@@ -804,6 +804,7 @@ def run_ours(args, rank, world, local_rank):
         ms2 = sum(x for _, _, x, _ in per2)
         pairs = sum(1 << (n - 1 - c) for c, _, _, _ in per2)
         flops = 28.0 * pairs  # general 2x2 complex update: 12 FMA + 4 MUL per pair, FMA = 2 flops
+        fp64_instr = 16.0 * pairs  # the FP64 instructions of that update (FMA and MUL issue alike)
         peaks = measure_fma_peaks(qs)
         result["fma_peaks_tflops"] = peaks
         result["c128_sweep"] = {
@@ -811,7 +812,11 @@ def run_ours(args, rank, world, local_rank):
             "roofline": {"bound": "alu", "achieved": round(flops / (ms2 * 1e-3) / 1e12, 3),
                          "peak": peaks["fp64"], "unit": "TFLOP/s (FP64)", "peak_source": "measured (qs_measure_fma_peak)",
                          "frac": round(flops / (ms2 * 1e-3) / 1e12 / peaks["fp64"], 3),
-                         "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS},
+                         "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS,
+                         # the pipe issues MUL and FMA at one rate: against the measured FMA
+                         # instruction rate (peak / 2 flops) the update's 16 instructions per pair
+                         "fp64_instr_per_s": round(fp64_instr / (ms2 * 1e-3) / 1e12, 3),
+                         "frac_of_fp64_instr_rate": round(fp64_instr / (ms2 * 1e-3) / 1e12 / (peaks["fp64"] / 2), 3)},
         }
     if rank == 0:
         if want("adjoint"):
