@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--quick", action="store_true", help="headline sweep only (for profiler runs)")
     ap.add_argument("--only", default="",
                     help="comma list: run only these extra measurements after the headline sweep "
-                         "(e2e,c128,adjoint,fused,reduce,masked,batch,paper,precision,cpu)")
+                         "(e2e,c128,q30,adjoint,fused,reduce,masked,batch,paper,precision,cpu)")
     ap.add_argument("--ncu-case", type=int, default=None, metavar="C",
                     help="small profiling case: the 3 sweep gates with C controls (set 0) at --n, run twice "
                          "(profile with -s 3 -c 3 to skip the first round)")
@@ -818,6 +818,19 @@ def run_ours(args, rank, world, local_rank):
                          "fp64_instr_per_s": round(fp64_instr / (ms2 * 1e-3) / 1e12, 3),
                          "frac_of_fp64_instr_rate": round(fp64_instr / (ms2 * 1e-3) / 1e12 / (peaks["fp64"] / 2), 3)},
         }
+    if want("q30") and rank == 0:
+        # fixed-point (Q1.30) states: the same sweep, one step, algorithmic bytes at 8 per amplitude
+        st3 = qs.State(n, "q30")
+        for q in range(n):
+            st3.apply_gate(q, W.H_MATRIX)
+        sm3, per3 = run_sweep(qs, st3, n, 8, sched, 1, 1)
+        st3.close()
+        torch.cuda.empty_cache()
+        b3 = sum(alg_bytes(n, c, 8) for c, _, _, _ in per3)
+        ms3 = sum(x for _, _, x, _ in per3)
+        result["q30_sweep"] = {"GBps": round(b3 / (ms3 * 1e-3) / 1e9, 1),
+                               "frac_hbm": round(b3 / (ms3 * 1e-3) / 1e9 / peak, 3),
+                               "format": "Q1.30 int32 (re, im), exact 64-bit products, one rounding per output"}
     if rank == 0:
         if want("adjoint"):
             result["adjoint"] = measure_adjoint(qs, W, peak)

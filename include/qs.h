@@ -45,7 +45,19 @@ typedef enum qs_status {
     QS_EUNSUPPORTED = 5   /* valid request this build does not handle               */
 } qs_status;
 
-typedef enum qs_dtype { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+/* Amplitude formats. QS_C64: complex float32 (8 bytes); QS_C128: complex float64 (16 bytes);
+ * QS_Q30: fixed point, each real and imaginary part a signed 32-bit integer v meaning
+ * v / 2^30 (Q1.30, 8 bytes per amplitude, interleaved (re, im)). For QS_Q30 the gate matrix is
+ * rounded once to Q1.30 (nearest, halves away from zero, clamped to int32) and each output
+ * component of a selected pair is the exact 64-bit sum of its four products rounded to the
+ * nearest Q1.30 value with halves toward +infinity (floor((S + 2^29) / 2^30)), clamped to
+ * int32: results are exact integer arithmetic and reproducible bit for bit. Valid for
+ * components and matrix entries of magnitude <= 1 (normalised states, unitary gates), where
+ * no 64-bit sum can overflow. QS_Q30 supports single gates, the masked comparator, unfused
+ * circuits (also as graphs), <Z_i> and host copies; fused passes, gradients and batches
+ * return QS_EUNSUPPORTED. (The paper's conclusion names fixed-point amplitudes as future work
+ * without a format; this one is the library's choice.) */
+typedef enum qs_dtype { QS_C64 = 0, QS_C128 = 1, QS_Q30 = 2 } qs_dtype;
 
 /* Gate kinds of qs_gate.kind. */
 enum {

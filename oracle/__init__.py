@@ -16,6 +16,10 @@ Pieces and the passages they follow:
 - ``energy`` / ``param_shift_grad`` / ``fd_grad``: E = <psi|sum_i Z_i|psi>; its gradient by
   the two-term parameter-shift rule (exact for RY/RZ, Mitarai et al. 2018; Schuld et al.
   2019) and by central finite differences.
+- ``quantize_q30`` / ``apply_gate_q30`` / ``run_circuit_q30`` / ``gate_output_q30`` /
+  ``expect_z_q30``: fixed-point amplitudes (the paper's conclusion names them as future work;
+  the format is this library's choice): Q1.30 integers, Eq. 2 in exact 64-bit integer
+  products, one rounding per output component (nearest, halves toward +infinity), clamped.
 
 Parity: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py``.
@@ -59,6 +63,15 @@ def lib():
         L.oracle_inner_re.argtypes = [_dp, _dp, ctypes.c_int]
         L.oracle_num_threads.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
+        _ip = ctypes.POINTER(ctypes.c_int32)
+        L.oracle_quantize_q30.restype = ctypes.c_int32
+        L.oracle_quantize_q30.argtypes = [ctypes.c_double]
+        L.oracle_apply_gate_q30.restype = None
+        L.oracle_apply_gate_q30.argtypes = [_ip, ctypes.c_int, ctypes.c_int, _u64, _u64, _ip]
+        L.oracle_gate_output_q30.restype = None
+        L.oracle_gate_output_q30.argtypes = [_u64, ctypes.c_int, _u64, _u64, _ip, _ip, _ip, _ip]
+        L.oracle_expect_z_q30.restype = None
+        L.oracle_expect_z_q30.argtypes = [_ip, ctypes.c_int, _dp]
         _lib = L
     return _lib
 
@@ -223,3 +236,72 @@ def fd_grad(n: int, gates, theta, h: float = 1e-4, psi0=None) -> np.ndarray:
         tm[p] -= h
         g[p] = (energy(n, gates, tp, psi0) - energy(n, gates, tm, psi0)) / (2.0 * h)
     return g
+
+
+# ---------------------------------------------------------------------------------------
+# Fixed-point amplitudes (Q1.30): int32 (re, im) pairs, value = integer / 2^30
+# ---------------------------------------------------------------------------------------
+
+Q30_ONE = 1 << 30
+
+
+def quantize_q30(v: float) -> int:
+    """Q1.30 integer of a real number: nearest, halves away from zero, clamped to int32."""
+    return int(lib().oracle_quantize_q30(float(v)))
+
+
+def q30_matrix(U) -> np.ndarray:
+    """A 2x2 complex matrix (or 8 interleaved doubles) as 8 Q1.30 integers."""
+    u = _u8(U)
+    return np.array([quantize_q30(x) for x in u], dtype=np.int32)
+
+
+def _check_q30(psi: np.ndarray, n: int):
+    if psi.dtype != np.int32 or not psi.flags.c_contiguous or psi.shape != (1 << n, 2):
+        raise ValueError("Q1.30 oracle state must be a contiguous int32 array of shape (2^n, 2)")
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def apply_gate_q30(psi: np.ndarray, n: int, t: int, ctrl_mask: int, ctrl_vals: int, U) -> None:
+    """In place: Eq. 2 in Q1.30 on the selected pairs (U quantised with quantize_q30)."""
+    _check_q30(psi, n)
+    _check_gate(n, t, ctrl_mask, ctrl_vals)
+    uq = q30_matrix(U)
+    lib().oracle_apply_gate_q30(_iptr(psi), n, t, ctrl_mask, ctrl_vals, _iptr(uq))
+
+
+def run_circuit_q30(psi: np.ndarray, n: int, gates, theta=None) -> np.ndarray:
+    """Apply the gate records in order to a Q1.30 state (X gates as their exact matrix)."""
+    for g in gates:
+        apply_gate_q30(psi, n, int(g["target"]), int(g["ctrl_mask"]), int(g["ctrl_vals"]), gate_matrix(g, theta))
+    return psi
+
+
+def gate_output_q30(k: int, t: int, ctrl_mask: int, ctrl_vals: int, U, in_k, in_partner) -> tuple:
+    uq = q30_matrix(U)
+    a = np.ascontiguousarray(in_k, dtype=np.int32)
+    b = np.ascontiguousarray(in_partner, dtype=np.int32)
+    o = np.empty(2, dtype=np.int32)
+    lib().oracle_gate_output_q30(k, t, ctrl_mask, ctrl_vals, _iptr(uq), _iptr(a), _iptr(b), _iptr(o))
+    return int(o[0]), int(o[1])
+
+
+def expect_z_q30(psi: np.ndarray, n: int) -> np.ndarray:
+    _check_q30(psi, n)
+    out = np.empty(n)
+    lib().oracle_expect_z_q30(_iptr(psi), n, _ptr(out))
+    return out
+
+
+def to_q30(psi: np.ndarray) -> np.ndarray:
+    """A complex vector as Q1.30 integers (each part quantised)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    out = np.empty((psi.size, 2), dtype=np.int32)
+    lib_q = lib().oracle_quantize_q30
+    for k, z in enumerate(psi):
+        out[k, 0] = lib_q(float(z.real))
+        out[k, 1] = lib_q(float(z.imag))
+    return out

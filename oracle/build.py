@@ -26,9 +26,9 @@ def build(force: bool = False) -> str:
     os.close(fd)
     try:
         try:
-            subprocess.run(base + ["-fopenmp", SRC, "-o", tmp], check=True, capture_output=True)
+            subprocess.run(base + ["-fopenmp", SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
         except subprocess.CalledProcessError:
-            subprocess.run(base + [SRC, "-o", tmp], check=True, capture_output=True)
+            subprocess.run(base + [SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
         os.replace(tmp, LIB_PATH)
     finally:
         if os.path.exists(tmp):

@@ -21,6 +21,7 @@
  * the iterations of one gate can run in parallel). Reductions are sequential so that
  * their rounding order is fixed.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -182,4 +183,94 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Fixed-point amplitudes (Q1.30), the paper's conclusion's future-work format          */
+/* ---------------------------------------------------------------------------------- */
+
+/* The paper names fixed-point amplitudes as future work without a format; the format taken
+ * here (written down with the library): each real and imaginary part is a signed 32-bit
+ * integer v meaning v / 2^30. */
+
+/* A real number in Q1.30: v * 2^30 rounded to the nearest integer, halves away from zero,
+ * then clamped to [-2^31, 2^31 - 1]. */
+int32_t oracle_quantize_q30(double v)
+{
+    double s = v * 1073741824.0;
+    double r = (s >= 0.0) ? floor(s + 0.5) : -floor(-s + 0.5);
+    if (r > 2147483647.0) r = 2147483647.0;
+    if (r < -2147483648.0) r = -2147483648.0;
+    return (int32_t)r;
+}
+
+/* One output component from its exact 64-bit sum S (a sum of products of Q1.30 values, i.e.
+ * of value * 2^60): floor((S + 2^29) / 2^30), the nearest integer with halves rounded toward
+ * +infinity, clamped to the int32 range. */
+static int32_t q30_round(long long S)
+{
+    long long r = S + (1ll << 29);
+    /* floor division by 2^30 (an arithmetic right shift, written out for negative values) */
+    long long q = (r >= 0) ? (r / 1073741824ll) : -((-r + 1073741823ll) / 1073741824ll);
+    if (q > 2147483647ll) q = 2147483647ll;
+    if (q < -2147483648ll) q = -2147483648ll;
+    return (int32_t)q;
+}
+
+/* Eq. 2 in Q1.30 for every selected pair (the same loop and control test as
+ * oracle_apply_gate): C'_k = a C_k + b C_{k+2^t}, C'_{k+2^t} = c C_k + d C_{k+2^t}, each
+ * component's four products summed exactly in 64 bits and rounded once by q30_round.
+ * psi[2k], psi[2k+1] = Re, Im of C_k; U[0..7] = a, b, c, d as (re, im), in Q1.30. */
+void oracle_apply_gate_q30(int32_t *psi, int n, int t, uint64_t ctrl_mask, uint64_t ctrl_vals, const int32_t *U)
+{
+    const int64_t N = (int64_t)1 << n;
+    const uint64_t stride = 1ull << t;
+    const long long ar = U[0], ai = U[1], br = U[2], bi = U[3];
+    const long long cr = U[4], ci = U[5], dr = U[6], di = U[7];
+#pragma omp parallel for schedule(static)
+    for (int64_t kk = 0; kk < N; ++kk) {
+        uint64_t k = (uint64_t)kk;
+        if (k & stride) continue;
+        if ((k & ctrl_mask) != ctrl_vals) continue;
+        uint64_t k2 = k + stride;
+        long long xr = psi[2 * k], xi = psi[2 * k + 1];
+        long long yr = psi[2 * k2], yi = psi[2 * k2 + 1];
+        psi[2 * k]      = q30_round(ar * xr - ai * xi + br * yr - bi * yi);
+        psi[2 * k + 1]  = q30_round(ar * xi + ai * xr + br * yi + bi * yr);
+        psi[2 * k2]     = q30_round(cr * xr - ci * xi + dr * yr - di * yi);
+        psi[2 * k2 + 1] = q30_round(cr * xi + ci * xr + dr * yi + di * yr);
+    }
+}
+
+/* Output amplitude k of one Q1.30 gate from its pair's inputs (sampled checks). */
+void oracle_gate_output_q30(uint64_t k, int t, uint64_t ctrl_mask, uint64_t ctrl_vals, const int32_t *U,
+                            const int32_t *in_k, const int32_t *in_partner, int32_t *out)
+{
+    const uint64_t stride = 1ull << t;
+    uint64_t k0 = k & ~stride;
+    if ((k0 & ctrl_mask) != ctrl_vals) {
+        out[0] = in_k[0];
+        out[1] = in_k[1];
+        return;
+    }
+    const int32_t *x = (k & stride) ? in_partner : in_k;
+    const int32_t *y = (k & stride) ? in_k : in_partner;
+    const int32_t *r = (k & stride) ? U + 4 : U;
+    out[0] = q30_round((long long)r[0] * x[0] - (long long)r[1] * x[1] + (long long)r[2] * y[0] - (long long)r[3] * y[1]);
+    out[1] = q30_round((long long)r[0] * x[1] + (long long)r[1] * x[0] + (long long)r[2] * y[1] + (long long)r[3] * y[0]);
+}
+
+/* <Z_i> of a Q1.30 state: |C_k|^2 = (re^2 + im^2) / 2^60, summed sequentially in double. */
+void oracle_expect_z_q30(const int32_t *psi, int n, double *out)
+{
+    const uint64_t N = 1ull << n;
+    for (int i = 0; i < n; ++i) out[i] = 0.0;
+    for (uint64_t k = 0; k < N; ++k) {
+        long long re = psi[2 * k], im = psi[2 * k + 1];
+        double p = (double)(re * re + im * im) * 8.673617379884035e-19; /* 2^-60 */
+        for (int i = 0; i < n; ++i) {
+            if ((k >> i) & 1ull) out[i] -= p;
+            else out[i] += p;
+        }
+    }
 }

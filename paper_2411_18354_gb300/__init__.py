@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported C-ABI names)
-    QS_C64, QS_C128, QS_FLAG_ADJOINT, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_JIT, QS_FLAG_MASKED, QS_FLAG_OUT_DEVICE, QS_GATE_U,
+    QS_C64, QS_C128, QS_Q30, QS_FLAG_ADJOINT, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_JIT, QS_FLAG_MASKED, QS_FLAG_OUT_DEVICE, QS_GATE_U,
     QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_compile, qs_circuit_schedule,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
     qs_measure_fma_peak, qs_debug_build, qs_debug_configure, qs_debug_status,
@@ -25,8 +25,8 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
 )
 from .gates import GATE_DTYPE, as_gate_array  # noqa: F401
 
-_DT = {"c64": QS_C64, "complex64": QS_C64, "c128": QS_C128, "complex128": QS_C128}
-_NP = {QS_C64: np.complex64, QS_C128: np.complex128}
+_DT = {"c64": QS_C64, "complex64": QS_C64, "c128": QS_C128, "complex128": QS_C128, "q30": QS_Q30}
+_NP = {QS_C64: np.complex64, QS_C128: np.complex128}  # QS_Q30: int32 array of shape (2^n, 2)
 
 
 def circuit_schedule(n: int, gates, theta=None, flags: int = QS_FLAG_FUSE, dtype="c64") -> dict:
@@ -64,6 +64,20 @@ class State:
                           _current_stream() if stream is None else stream)
         st = cls(n, dt, _handle=h)
         st._tensor = tensor  # keep the memory alive
+        return st
+
+    @classmethod
+    def wrap_q30(cls, tensor, n: int, stream: int | None = None) -> "State":
+        """Use a contiguous torch int32 CUDA tensor of shape (2^n, 2) as a QS_Q30 state."""
+        import torch
+
+        if tensor.dtype != torch.int32 or not tensor.is_cuda or not tensor.is_contiguous() or \
+                tuple(tensor.shape) != (1 << n, 2):
+            raise ValueError("need a contiguous int32 CUDA tensor of shape (2^n, 2)")
+        h = qs_state_wrap(tensor.data_ptr(), tensor.numel() * tensor.element_size(), n, QS_Q30,
+                          _current_stream() if stream is None else stream)
+        st = cls(n, QS_Q30, _handle=h)
+        st._tensor = tensor
         return st
 
     def close(self):
@@ -112,14 +126,24 @@ class State:
         return qs_adjoint_grad(self.h, gates, theta, flags)
 
     def to_numpy(self) -> np.ndarray:
-        out = np.empty(1 << self.n, dtype=_NP[self.dtype])
+        """The amplitudes: complex64 / complex128, or for QS_Q30 the Q1.30 integers as an int32
+        array of shape (2^n, 2) (real, imaginary)."""
+        if self.dtype == QS_Q30:
+            out = np.empty((1 << self.n, 2), dtype=np.int32)
+        else:
+            out = np.empty(1 << self.n, dtype=_NP[self.dtype])
         qs_state_copy_to_host(self.h, out)
         return out
 
     def from_numpy(self, a: np.ndarray):
-        a = np.ascontiguousarray(a, dtype=_NP[self.dtype])
-        if a.size != (1 << self.n):
-            raise ValueError("wrong number of amplitudes")
+        if self.dtype == QS_Q30:
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            if a.shape != (1 << self.n, 2):
+                raise ValueError("a QS_Q30 state takes an int32 array of shape (2^n, 2)")
+        else:
+            a = np.ascontiguousarray(a, dtype=_NP[self.dtype])
+            if a.size != (1 << self.n):
+                raise ValueError("wrong number of amplitudes")
         qs_state_copy_from_host(self.h, a)
 
 

@@ -15,7 +15,7 @@ import numpy as np
 from .build import DEBUG_LIB_PATH, LIB_PATH
 
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
-QS_C64, QS_C128 = 0, 1
+QS_C64, QS_C128, QS_Q30 = 0, 1, 2
 QS_GATE_U, QS_GATE_X, QS_GATE_RY, QS_GATE_RZ = 0, 1, 2, 3
 QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_OUT_DEVICE, QS_FLAG_MASKED, QS_FLAG_JIT, QS_FLAG_ADJOINT = 1, 2, 4, 8, 16, 32
 

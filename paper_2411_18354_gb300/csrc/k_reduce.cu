@@ -272,6 +272,7 @@ size_t reduce_scratch_doubles(int n) { return (size_t)kRedMaxBlocks * (size_t)(n
 
 cudaError_t launch_expect_z(int dtype, const void *psi, int n, double *scratch, double *out_z,
                             double *out_norm2, cudaStream_t st) {
+    if (dtype == QS_Q30) return launch_expect_z_q30(psi, n, scratch, out_z, out_norm2, st);
     return dtype == QS_C64 ? expect_z_impl<float>(psi, n, scratch, out_z, out_norm2, st)
                            : expect_z_impl<double>(psi, n, scratch, out_z, out_norm2, st);
 }

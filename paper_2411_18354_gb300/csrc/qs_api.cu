@@ -37,7 +37,7 @@ qs_status cuda_fail(cudaError_t e, const char *what) {
     return fail(QS_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-size_t elem_bytes(int dtype) { return dtype == QS_C64 ? 8 : 16; }
+size_t elem_bytes(int dtype) { return dtype == QS_C128 ? 16 : 8; }
 
 // L2 fetch size for DRAM misses (cudaLimitMaxL2FetchGranularity of this process's context).
 // A gate with controls on low qubits selects runs of 8-64 bytes; with the device's default
@@ -97,7 +97,8 @@ using namespace qs;
 // ------------------------------------------------------------------------------------
 namespace {
 __global__ void k_set_one(void *psi, uint64_t k, int dtype) {
-    if (dtype == QS_C64) reinterpret_cast<float2 *>(psi)[k] = make_float2(1.0f, 0.0f);
+    if (dtype == QS_Q30) reinterpret_cast<int2 *>(psi)[k] = make_int2(1 << 30, 0);
+    else if (dtype == QS_C64) reinterpret_cast<float2 *>(psi)[k] = make_float2(1.0f, 0.0f);
     else reinterpret_cast<double2 *>(psi)[k] = make_double2(1.0, 0.0);
 }
 
@@ -132,7 +133,7 @@ qs_status qs_state_alloc(int n, qs_dtype dtype, void *stream, qs_state **out) {
     if (!out) return fail(QS_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n=%d out of range [1, %d]", n, kMaxQubits);
-    if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "bad dtype %d", (int)dtype);
+    if (dtype != QS_C64 && dtype != QS_C128 && dtype != QS_Q30) return fail(QS_EINVAL, "bad dtype %d", (int)dtype);
     const size_t bytes = (size_t(1) << n) * elem_bytes(dtype);
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
@@ -166,7 +167,7 @@ qs_status qs_state_wrap(void *dev_ptr, size_t bytes, int n, qs_dtype dtype, void
     if (!out) return fail(QS_EINVAL, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n=%d out of range [1, %d]", n, kMaxQubits);
-    if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "bad dtype %d", (int)dtype);
+    if (dtype != QS_C64 && dtype != QS_C128 && dtype != QS_Q30) return fail(QS_EINVAL, "bad dtype %d", (int)dtype);
     if (!dev_ptr) return fail(QS_EINVAL, "dev_ptr is NULL");
     if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0) return fail(QS_EINVAL, "dev_ptr is not 256-byte aligned");
     const size_t need = (size_t(1) << n) * elem_bytes(dtype);

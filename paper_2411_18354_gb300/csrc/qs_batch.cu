@@ -273,6 +273,7 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
     *out = nullptr;
     if (num_states < 1 || !n_qubits || !gate_offsets || !param_offsets)
         return set_error(QS_EINVAL, "qs_batch_create: need num_states >= 1 and the size / offset arrays");
+    if (dtype == QS_Q30) return set_error(QS_EUNSUPPORTED, "qs_batch_create: batches are not built for QS_Q30 states");
     if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_batch_create: bad dtype");
     const int es = (int)elem_bytes(dtype);
     if (small_bits <= 0) small_bits = dtype == QS_C64 ? 12 : 11;

@@ -474,7 +474,10 @@ static qs_status adjoint_schedule(const qs_state *shape, const qs_gate *gates, s
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count, const double *theta,
                               size_t n_theta, int flags, qs_schedule *out) {
     if (!out) return set_error(QS_EINVAL, "qs_circuit_schedule: out is NULL");
-    if (dtype != QS_C64 && dtype != QS_C128) return set_error(QS_EINVAL, "qs_circuit_schedule: bad dtype");
+    if (dtype != QS_C64 && dtype != QS_C128 && dtype != QS_Q30)
+        return set_error(QS_EINVAL, "qs_circuit_schedule: bad dtype");
+    if (dtype == QS_Q30 && (flags & (QS_FLAG_FUSE | QS_FLAG_ADJOINT)))
+        return set_error(QS_EUNSUPPORTED, "qs_circuit_schedule: fused passes and gradients are not built for QS_Q30");
     if (n < 1 || n > kMaxQubits) return set_error(QS_EINVAL, "qs_circuit_schedule: n out of range");
     if (count > 0 && !gates) return set_error(QS_EINVAL, "qs_circuit_schedule: gates is NULL");
     if (flags & ~(QS_FLAG_FUSE | QS_FLAG_GRAPH | QS_FLAG_MASKED | QS_FLAG_JIT | QS_FLAG_ADJOINT))
@@ -493,7 +496,7 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
         if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     const bool masked = (flags & QS_FLAG_MASKED) != 0;
-    if (!masked) merge_runs(&shape, plans);
+    if (!masked && dtype != QS_Q30) merge_runs(&shape, plans);
     qs_schedule r;
     std::memset(&r, 0, sizeof(r));
     r.gates = (int32_t)plans.size();
@@ -598,6 +601,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_MASKED cannot be combined with QS_FLAG_FUSE");
     if ((flags & QS_FLAG_JIT) && !(flags & QS_FLAG_FUSE))
         return set_error(QS_EINVAL, "qs_apply_circuit: QS_FLAG_JIT needs QS_FLAG_FUSE");
+    if (s->dtype == QS_Q30 && (flags & QS_FLAG_FUSE))
+        return set_error(QS_EUNSUPPORTED, "qs_apply_circuit: fused passes are not built for QS_Q30 states");
     // CUDA graph: one per distinct (gates, theta, flags, buffer, tile size). A recorded one is
     // launched before any validation or planning (its gates passed both when it was recorded):
     // the hash picks the candidate, the stored key bytes must then match exactly.
@@ -619,7 +624,8 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
         if (!plan_record(s, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     const bool masked = (flags & QS_FLAG_MASKED) != 0;
-    if (!masked) merge_runs(s, plans);
+    // (fixed point rounds every gate: a merged product would round once and differ)
+    if (!masked && s->dtype != QS_Q30) merge_runs(s, plans);
     if (masked) {
         // baseline schedule: every pair iteration launched, the controls tested per unit,
         // the general update with the full matrix (as the Section III-A kernel does)
@@ -731,6 +737,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
         return set_error(QS_EINVAL, "qs_adjoint_grad: unknown flags");
     if ((flags & QS_FLAG_JIT) && !(flags & QS_FLAG_FUSE))
         return set_error(QS_EINVAL, "qs_adjoint_grad: QS_FLAG_JIT needs QS_FLAG_FUSE");
+    if (s->dtype == QS_Q30) return set_error(QS_EUNSUPPORTED, "qs_adjoint_grad: not built for QS_Q30 states");
     if (n_theta > 0 && !grad) return set_error(QS_EINVAL, "qs_adjoint_grad: grad is NULL");
     if (n_theta > (size_t)(1 << 24)) return set_error(QS_EINVAL, "qs_adjoint_grad: n_theta too large");
     const bool on_dev = (flags & QS_FLAG_OUT_DEVICE) != 0;

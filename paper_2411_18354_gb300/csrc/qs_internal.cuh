@@ -80,6 +80,12 @@ cudaError_t launch_gate_masked(int dtype, void *psi, const GatePlan &p, uint64_t
                                uint64_t ctrl_vals, cudaStream_t st);
 cudaError_t launch_set_basis(int dtype, void *psi, int n, uint64_t k, cudaStream_t st);
 
+// Fixed-point (QS_Q30) gate kernel: matrix from p.Ufull rounded to Q1.30 (k_gate_q30.cu).
+cudaError_t launch_gate_q30(void *psi, const GatePlan &p, bool masked, uint64_t cmask, uint64_t cvals,
+                            cudaStream_t st);
+cudaError_t launch_expect_z_q30(const void *psi, int n, double *scratch, double *out_z, double *out_norm2,
+                                cudaStream_t st);
+
 // Reductions: partial sums per block, then a fixed-order final pass (deterministic).
 // `scratch` must hold reduce_scratch_doubles(n) doubles.
 size_t reduce_scratch_doubles(int n);

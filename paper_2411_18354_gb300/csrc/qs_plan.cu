@@ -147,6 +147,11 @@ bool plan_gate(int n, int dtype, int target, uint64_t ctrl_mask, uint64_t ctrl_v
         return false;
     }
 
+    // Fixed point: one update form for every matrix (exchanges stay exchanges, an exact move
+    // that gives the same integers as the general form of [[0, 1], [1, 0]]; the identity, left
+    // out above, leaves every integer unchanged under the general form too).
+    if (dtype == QS_Q30 && p->op != OP_SWAP) p->op = OP_GEN;
+
     // Inserted positions: the target (value 0) and the controls (their values), ascending.
     int pos[64];
     int m = 0;
@@ -164,7 +169,7 @@ bool plan_gate(int n, int dtype, int target, uint64_t ctrl_mask, uint64_t ctrl_v
     // units of two adjacent vectors per side made every warp instruction stride over memory and
     // capped an in-place update at ~88 % of a copy's bandwidth (measured on GB300: 5.8-5.9
     // against 6.3-6.7 TB/s for the uncontrolled update at n = 30).
-    const bool c64 = dtype == QS_C64;
+    const bool c64 = dtype == QS_C64 || dtype == QS_Q30;  // 8-byte amplitudes
     if (target == 0 && p->op != OP_SIDE) {
         p->layout = LAY_ADJ;
         p->r = 0;
@@ -188,12 +193,14 @@ void plan_masked(const GatePlan &compact, GatePlan *out) {
 }
 
 cudaError_t launch_gate(int dtype, void *psi, const GatePlan &p, cudaStream_t st) {
+    if (dtype == QS_Q30) return launch_gate_q30(psi, p, false, 0, 0, st);
     return dtype == QS_C64 ? launch_gate_c64(psi, p, false, 0, 0, st)
                            : launch_gate_c128(psi, p, false, 0, 0, st);
 }
 
 cudaError_t launch_gate_masked(int dtype, void *psi, const GatePlan &p, uint64_t ctrl_mask,
                                uint64_t ctrl_vals, cudaStream_t st) {
+    if (dtype == QS_Q30) return launch_gate_q30(psi, p, true, ctrl_mask, ctrl_vals, st);
     return dtype == QS_C64 ? launch_gate_c64(psi, p, true, ctrl_mask, ctrl_vals, st)
                            : launch_gate_c128(psi, p, true, ctrl_mask, ctrl_vals, st);
 }

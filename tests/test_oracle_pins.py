@@ -404,3 +404,127 @@ def test_parameter_shift_rejects_controlled_rotations():
     tm[3] -= np.pi / 2
     two_term = 0.5 * (oracle.energy(n, gates, tp) - oracle.energy(n, gates, tm))
     assert abs(two_term - fd[3]) > 1e-2  # 0.220 against 0.159
+
+
+# ---------------------------------------------------------------------------------------
+# Fixed-point amplitudes (Q1.30): the format's rounding rules, exactness of exchanges, the
+# index arithmetic (dense brute force), and agreement with the float64 oracle within the
+# rounding the format implies
+# ---------------------------------------------------------------------------------------
+
+def test_q30_quantisation_rule():
+    """Matrix entries: nearest Q1.30 integer, halves away from zero, clamped to int32."""
+    q = oracle.quantize_q30
+    assert q(0.5) == 1 << 29 and q(-0.5) == -(1 << 29) and q(1.0) == 1 << 30
+    assert q(2.0 ** -31) == 1 and q(-(2.0 ** -31)) == -1          # exactly half a step: away from 0
+    assert q(3 * 2.0 ** -32) == 1 and q(2.0 ** -32) == 0          # 0.75 and 0.25 of a step
+    assert q(1 / np.sqrt(2)) == 759250125                         # 759250124.9919... rounds up
+    assert q(2.5) == 2 ** 31 - 1 and q(-3.0) == -(2 ** 31)        # clamped
+
+
+def test_q30_rounding_of_the_update():
+    """One output component is floor((S + 2^29) / 2^30) of its exact 64-bit sum S, clamped:
+    ties go toward +infinity, and the sum of two full-scale terms saturates."""
+    one = 1 << 30
+    # n = 1, target 0, U = [[a, 0], [0, 1]]: x' = round(a x)
+    for a_raw, x_raw, want in ((1, 1 << 29, 1),      # S = 2^29: exactly half -> up to 1
+                               (1, -(1 << 29), 0),   # S = -2^29: half -> up to 0
+                               (3, 1 << 29, 2),      # S = 1.5 * 2^30 -> 2
+                               (-3, 1 << 29, -1),    # S = -1.5 * 2^30 -> -1
+                               (1, (1 << 29) - 1, 0)):
+        psi = np.zeros((2, 2), dtype=np.int32)
+        psi[0, 0] = x_raw
+        U = np.zeros(8)
+        U[0] = a_raw / one
+        U[6] = 1.0
+        oracle.apply_gate_q30(psi, 1, 0, 0, 0, U)
+        assert psi[0, 0] == want, (a_raw, x_raw, psi[0, 0])
+    psi = np.full((2, 2), 0, dtype=np.int32)
+    psi[0, 0] = psi[1, 0] = one
+    oracle.apply_gate_q30(psi, 1, 0, 0, 0, np.array([[1.0, 1.0], [1.0, -1.0]]))  # x + y = 2 saturates
+    assert psi[0, 0] == 2 ** 31 - 1 and psi[1, 0] == 0
+
+
+def test_q30_exchanges_and_hadamard_exact_values():
+    """X on Q1.30 amplitudes moves the integers unchanged (Section II-A, bit-exact); H on
+    |0> gives round(2^30 * q(1/sqrt 2) / 2^30) = q(1/sqrt 2) on both amplitudes."""
+    rng = np.random.default_rng(3)
+    n = 5
+    psi = rng.integers(-(1 << 30), 1 << 30, size=(1 << n, 2)).astype(np.int32)
+    ref = psi.copy()
+    oracle.apply_gate_q30(psi, n, 2, 0b1001, 0b0001, W.X_MATRIX)
+    for k in range(1 << n):
+        if (k & 0b1001) == 0b0001:
+            assert np.array_equal(psi[k], ref[k ^ 0b100])
+        else:
+            assert np.array_equal(psi[k], ref[k])
+    psi = np.zeros((2, 2), dtype=np.int32)
+    psi[0, 0] = 1 << 30
+    oracle.apply_gate_q30(psi, 1, 0, 0, 0, W.H_MATRIX)
+    assert psi[0, 0] == 759250125 and psi[1, 0] == 759250125 and psi[0, 1] == 0 and psi[1, 1] == 0
+
+
+def _dense_q30(n, t, mask, vals, Uq, psi):
+    """Brute force: the full 2^n x 2^n integer matrix of the gate (P_sat (x) U + rest (x) I,
+    entries as Q1.30 integers), each output component's exact sum rounded by the format's
+    rule."""
+    N = 1 << n
+    u = [(int(Uq[2 * i]), int(Uq[2 * i + 1])) for i in range(4)]  # a, b, c, d
+    M = {}  # (row, column) -> complex integer entry as (re, im)
+    for k in range(N):
+        if (k & mask) != vals:
+            M[(k, k)] = (1 << 30, 0)
+            continue
+        bit = (k >> t) & 1
+        k0 = k & ~(1 << t)
+        M[(k, k0)] = u[0] if bit == 0 else u[2]
+        M[(k, k0 | (1 << t))] = u[1] if bit == 0 else u[3]
+    out = np.zeros((N, 2), dtype=np.int64)
+    for k in range(N):
+        sr = si = 0
+        for j in range(N):
+            mr, mi = M.get((k, j), (0, 0))
+            xr, xi = int(psi[j, 0]), int(psi[j, 1])
+            sr += mr * xr - mi * xi
+            si += mr * xi + mi * xr
+        for c, S in ((0, sr), (1, si)):
+            r = (S + (1 << 29)) >> 30  # Python's >> floors
+            out[k, c] = max(-(2 ** 31), min(2 ** 31 - 1, r))
+    return out.astype(np.int32)
+
+
+def test_q30_gate_against_dense_brute_force():
+    """Every target, control subset and control value at n <= 4: the Q1.30 gate equals the
+    dense integer matrix product with the same rounding, bit for bit."""
+    rng = np.random.default_rng(30)
+    for n in (1, 2, 3, 4):
+        for t in range(n):
+            others = [q for q in range(n) if q != t]
+            for m in range(1 << len(others)):
+                mask = sum(1 << others[i] for i in range(len(others)) if (m >> i) & 1)
+                vals = mask & int(rng.integers(0, 1 << n))
+                U = W.haar_2x2(rng)
+                psi = rng.integers(-(1 << 29), 1 << 29, size=(1 << n, 2)).astype(np.int32)
+                want = _dense_q30(n, t, mask, vals, oracle.q30_matrix(U), psi)
+                got = psi.copy()
+                oracle.apply_gate_q30(got, n, t, mask, vals, U)
+                assert np.array_equal(got, want), (n, t, mask, vals)
+
+
+def test_q30_circuit_tracks_float64_within_rounding():
+    """A random 200-gate circuit (0-3 controls) on a random normalised 8-qubit state: the
+    Q1.30 result differs from the float64 oracle by at most the format's rounding: per gate
+    each output component gains <= 2^-31 from its rounding plus <= 4 * 2^-31 from the
+    quantised matrix (entries within 2^-31, |inputs| <= 1), so 200 gates stay below
+    1000 * 2^-31 = 4.7e-7; and <Z_i> of the Q1.30 state equals the float64 <Z_i> of its
+    dequantised vector."""
+    n = 8
+    gates = W.random_circuit(n, 200, 3, seed=31)
+    psi0 = W.random_state(n, 32)
+    ref = psi0.copy()
+    oracle.run_circuit(ref, n, gates)
+    q = oracle.to_q30(psi0)
+    oracle.run_circuit_q30(q, n, gates)
+    deq = (q[:, 0].astype(np.float64) + 1j * q[:, 1].astype(np.float64)) / (1 << 30)
+    assert np.max(np.abs(deq - ref)) <= 1000 * 2.0 ** -31
+    assert np.max(np.abs(oracle.expect_z_q30(q, n) - oracle.expect_z(deq.astype(np.complex128), n))) <= 1e-12
