@@ -392,8 +392,10 @@ static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, 
             seq[i] = (int)(count - 1 - i);
             if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
         }
+        // compiled sweep passes keep psi and lambda rows of 4 group qubits in registers (the
+        // interpreter holds 3: its dispatch leaves fewer registers free)
         plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &ap->dusp, &slot_of, &ap->pa, kPassMaxGates,
-                   true, 0, jit);
+                   true, jit ? kGroupBits : 0, jit);
     }
     return true;
 }
