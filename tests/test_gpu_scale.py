@@ -5,8 +5,8 @@ The workload: a 30-qubit state, 1000 Haar-random 2x2 gates on uniformly random t
 The start state is a product state with distinct amplitudes (RY(alpha_q) then RZ(beta_q) on
 every qubit from |0...0>), prepared by the same gate records on both sides. The oracle applies
 all 1060 gates to a complex128 vector on the host (17.2 GB, Eq. 2 per selected pair); the GPU
-runs complex64 and complex128, one launch per gate and fused, and the whole output vector is
-compared chunk by chunk on the device.
+runs complex64 and complex128, one launch per gate, fused with interpreted passes and fused with
+compiled passes, and the whole output vector is compared chunk by chunk on the device.
 
 Bounds: the stated targets (complex64 max-abs <= 3e-5 and norm drift <= 1e-5; complex128
 max-abs <= 1e-12), and because the amplitudes of a 30-qubit state are only ~3e-5 in size, a
@@ -68,12 +68,12 @@ def scale_case():
 
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-@pytest.mark.parametrize("fuse", [False, True])
+@pytest.mark.parametrize("fuse", [False, True, "compiled"])
 def test_scale_circuit_n30_whole_vector(qs, scale_case, dtype, fuse):
     import torch
 
     prefix, gates, ref = scale_case
-    flags = qs.QS_FLAG_FUSE if fuse else 0
+    flags = (qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT) if fuse == "compiled" else (qs.QS_FLAG_FUSE if fuse else 0)
     tdt = torch.complex64 if dtype == "c64" else torch.complex128
     buf = torch.empty(1 << N, dtype=tdt, device="cuda")
     st = qs.State.wrap(buf, N)
