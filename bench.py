@@ -58,6 +58,9 @@ def parse_args():
                     help="small profiling case: <Z_i> + norm of an n=27 state, twice")
     ap.add_argument("--tile-costs", action="store_true",
                     help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
+    ap.add_argument("--gate-patterns", action="store_true",
+                    help="cold-L2 device time of single sweep gates with c = 6..8 controls at n = 30 (general and "
+                         "exchange) against the same control count on the top qubits (contiguous runs)")
     ap.add_argument("--ncu-qft", action="store_true",
                     help="profiling case: the fused QFT (29 qubits, or --n), twice (diagonal-run passes)")
     ap.add_argument("--jit", action="store_true",
@@ -975,6 +978,63 @@ def run_tile_costs(args):
     print(json.dumps({"tile_costs_n24_c64": out}), flush=True)
 
 
+def run_gate_patterns(args):
+    """Per gate: median device time over 10 launches, each after a read-only pass over a 256 MB
+    buffer (the L2 then holds clean lines of that buffer, none of the state); the general 2x2
+    and the exchange (same amplitudes moved, no arithmetic) on the sweep's first 12 control
+    sets of c = 6, 7, 8, and the same c with the controls on the top qubits."""
+    import numpy as np
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    n = 30
+    peak, _ = load_peaks()
+    sched = sweep_schedule(n)
+    st = qs.State(n, "c64")
+    for q in range(n):
+        st.apply_gate(q, W.H_MATRIX)
+    flush = torch.empty(1 << 28, dtype=torch.uint8, device="cuda")
+
+    def t_us(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(reps):
+            flush.max()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return sorted(x.elapsed_time(y) for x, y in ev)[reps // 2] * 1e3
+
+    rng = np.random.default_rng(5)
+    out = []
+    for c in (6, 7, 8):
+        rows = [r for s in range(SETS) for r in sched[s] if r[0] == c][:12]
+        alg = alg_bytes(n, c, 8)
+        for (_, t, m, v, U) in rows:
+            ins = m | (1 << t)
+            tg = t_us(lambda: qs._lib.qs_apply_gate(st.h, t, m, v, U))
+            tx = t_us(lambda: qs._lib.qs_apply_x(st.h, t, m, v))
+            out.append({"c": c, "t": t, "p0": (ins & -ins).bit_length() - 1, "mask": hex(m), "gate_us": round(tg, 2),
+                        "exchange_us": round(tx, 2), "frac": round(alg / (tg * 1e-6) / 1e9 / peak, 3),
+                        "frac_sector_adjusted": round(sector_bytes(n, m, 8) / (tg * 1e-6) / 1e9 / peak, 3)})
+        m = sum(1 << q for q in range(n - c, n))
+        t = n - c - 1
+        U = W.pack_u(W.haar_2x2(rng))
+        tg = t_us(lambda: qs._lib.qs_apply_gate(st.h, t, m, m, U))
+        out.append({"c": c, "t": t, "p0": t, "mask": hex(m), "gate_us": round(tg, 2), "contiguous": True,
+                    "frac": round(alg / (tg * 1e-6) / 1e9 / peak, 3)})
+    st.close()
+    print(json.dumps({"gate_patterns_n30_c64": out}), flush=True)
+
+
 def run_ncu_qft(args):
     """Profiling case: the QFT (29 qubits unless --n is given) with QS_FLAG_FUSE, twice; no timing."""
     import torch
@@ -1008,6 +1068,9 @@ def main():
         return
     if args.ncu_qft:
         run_ncu_qft(args)
+        return
+    if args.gate_patterns:
+        run_gate_patterns(args)
         return
     if args.ncu_batch:
         run_ncu_batch(args)
