@@ -58,6 +58,8 @@ def parse_args():
                     help="small profiling case: <Z_i> + norm of an n=27 state, twice")
     ap.add_argument("--tile-costs", action="store_true",
                     help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
+    ap.add_argument("--ncu-scale", action="store_true",
+                    help="profiling case: the 1000-gate scale circuit at n = 30 with compiled passes, twice")
     ap.add_argument("--gate-patterns", action="store_true",
                     help="cold-L2 device time of single sweep gates with c = 6..8 controls at n = 30 (general and "
                          "exchange) against the same control count on the top qubits (contiguous runs)")
@@ -978,6 +980,25 @@ def run_tile_costs(args):
     print(json.dumps({"tile_costs_n24_c64": out}), flush=True)
 
 
+def run_ncu_scale(args):
+    """Profiling case: compile, then the 1000-gate scale circuit (n = 30, 0-8 controls) with
+    QS_FLAG_FUSE | QS_FLAG_JIT twice; no timing."""
+    import torch
+
+    import paper_2411_18354_gb300 as qs
+    import workloads as W
+
+    qs.build()
+    n = 30
+    g = W.scale_circuit(n, 1000, seed=1)
+    _compile(qs, n, g, None, "c64")
+    with qs.State(n, "c64") as st:
+        for _ in range(2):
+            st.apply_circuit(g, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)
+        torch.cuda.synchronize()
+    print("ncu scale case done")
+
+
 def run_gate_patterns(args):
     """Per gate: median device time over 10 launches, each after a read-only pass over a 256 MB
     buffer (the L2 then holds clean lines of that buffer, none of the state); the general 2x2
@@ -1071,6 +1092,9 @@ def main():
         return
     if args.gate_patterns:
         run_gate_patterns(args)
+        return
+    if args.ncu_scale:
+        run_ncu_scale(args)
         return
     if args.ncu_batch:
         run_ncu_batch(args)
