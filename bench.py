@@ -516,7 +516,7 @@ def measure_precision(qs, W):
     return out
 
 
-def measure_batch(qs, W):
+def measure_batch(qs, W, peak):
     """Batching workload: 4096 states, n uniform in 10..20, 8 ansatz layers, complex64: one
     graph-launched persistent kernel for energies and gradients; settings from the autotuner."""
     import numpy as np
@@ -541,11 +541,14 @@ def measure_batch(qs, W):
         gr = torch.empty(b.num_params, dtype=torch.float64, device="cuda")
         ms = _events_ms(lambda: b.run(th, en, gr, qs.QS_FLAG_GRAPH), 2)
         info = b.info()
+        bbytes = b.algorithmic_bytes()
     finally:
         b.close()
     out = {"states": len(ns), "ms_per_launch": round(ms, 2), "states_per_s": round(len(ns) / (ms * 1e-3), 1),
            "gradient_entries_per_s": round(sum(nparams) / (ms * 1e-3), 1), "config": cfg,
            "grid": info["grid"], "smem_bytes": info["smem_bytes"],
+           "algorithmic_GB": round(bbytes / 1e9, 2), "achieved_GBps": round(bbytes / (ms * 1e-3) / 1e9, 1),
+           "frac_hbm": round(bbytes / (ms * 1e-3) / 1e9 / peak, 3),
            "workload": "4096 states, n~U{10..20} (seed 4), HEA 8 layers, energies + adjoint gradients, complex64"}
     # pass-major path: states above small_bits side by side, every pass compiled for its shape and
     # run over all states of one size per launch (first run compiles: untimed)
@@ -554,6 +557,7 @@ def measure_batch(qs, W):
                  {"small_bits": 12, "tile_bits": 11, "max_pass_gates": 64}):
         b = qs.Batch(ns, circuits, nparams, "c64", **jcfg)
         try:
+            jbytes = b.algorithmic_bytes()
             t0 = time.perf_counter()
             b.run(th, en, gr, qs.QS_FLAG_GRAPH | qs.QS_FLAG_JIT)
             torch.cuda.synchronize()
@@ -562,11 +566,14 @@ def measure_batch(qs, W):
         finally:
             b.close()
         if best is None or msj < best[0]:
-            best = (msj, jcfg, first_s)
-    msj, jcfg, first_s = best
+            best = (msj, jcfg, first_s, jbytes)
+    msj, jcfg, first_s, jbytes = best
     out["pass_major_compiled"] = {"ms_per_run": round(msj, 2), "states_per_s": round(len(ns) / (msj * 1e-3), 1),
                                   "gradient_entries_per_s": round(sum(nparams) / (msj * 1e-3), 1), "config": jcfg,
                                   "first_run_s_with_compile": round(first_s, 2),
+                                  "algorithmic_GB": round(jbytes / 1e9, 2),
+                                  "achieved_GBps": round(jbytes / (msj * 1e-3) / 1e9, 1),
+                                  "frac_hbm": round(jbytes / (msj * 1e-3) / 1e9 / peak, 3),
                                   "speedup_vs_persistent": round(ms / msj, 2)}
     return out
 
@@ -846,7 +853,7 @@ def run_ours(args, rank, world, local_rank):
         if want("masked"):
             result["masked_over_reduced_time_by_c"] = measure_masked(qs, n, sched)
         if want("batch"):
-            result["batch"] = measure_batch(qs, W)
+            result["batch"] = measure_batch(qs, W, peak)
         if want("paper"):
             result["paper_circuits"] = measure_paper_circuits(qs, W, peak)
         if want("precision"):

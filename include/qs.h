@@ -358,6 +358,12 @@ qs_status qs_batch_run(qs_batch *b, const double *theta, double *energy, double 
 qs_status qs_batch_info(const qs_batch *b, int *grid, int *small_bits, int *tile_bits,
                         int *max_pass_gates, size_t *smem_bytes, size_t *workspace_bytes);
 
+/* Bytes one run of the batch must move through device memory (its states above small_bits:
+ * |0...0> written, each forward pass reading and writing the tiles its gates select, lambda =
+ * O psi, each sweep pass reading and writing the selected tiles of psi and lambda; states in
+ * shared memory move none): the numerator of the batch's roofline. Host only. */
+qs_status qs_batch_bytes(const qs_batch *b, double *algorithmic_bytes);
+
 /* Release a batch (synchronises its stream first). NULL is accepted. */
 qs_status qs_batch_free(qs_batch *b);
 

@@ -18,7 +18,7 @@ from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_compile, qs_circuit_schedule,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
     qs_measure_fma_peak, qs_debug_build, qs_debug_configure, qs_debug_status,
-    qs_state_alloc, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
+    qs_state_alloc, qs_batch_bytes, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
     qs_set_l2_fetch_bytes, qs_set_tile_bits,
     qs_state_copy_from_host, qs_state_copy_from_host_async, qs_state_copy_to_host, qs_state_copy_to_host_async,
     qs_state_free, qs_state_info, qs_state_set_basis, qs_state_set_stream, qs_state_synchronize, qs_state_wrap,
@@ -171,6 +171,9 @@ class Batch:
 
     def info(self) -> dict:
         return qs_batch_info(self.h)
+
+    def algorithmic_bytes(self) -> float:
+        return qs_batch_bytes(self.h)
 
     def run(self, theta, energy, grad, flags: int = QS_FLAG_GRAPH):
         """theta / energy / grad: torch float64 CUDA tensors (or device addresses)."""

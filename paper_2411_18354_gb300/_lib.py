@@ -70,6 +70,7 @@ _SIGNATURES = [
     ("qs_batch_info", ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    ("qs_batch_bytes", ctypes.c_int, [_vp, _dp]),
     ("qs_batch_free", ctypes.c_int, [_vp]),
     ("qs_set_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("qs_get_tile_bits", ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
@@ -341,6 +342,13 @@ def qs_batch_create(n_qubits, gates, gate_offsets, param_offsets, dtype: int, sm
                                  _vp(go.ctypes.data), _vp(po.ctypes.data), dtype, small_bits, tile_bits,
                                  max_pass_gates, _vp(stream or None), ctypes.byref(h)))
     return h.value
+
+
+def qs_batch_bytes(b: int) -> float:
+    """Algorithmic bytes of one run of the batch (host only)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().qs_batch_bytes(_vp(b), ctypes.byref(out)))
+    return out.value
 
 
 def qs_batch_run(b: int, theta_dev: int, energy_dev: int, grad_dev: int, flags: int = QS_FLAG_GRAPH) -> None:

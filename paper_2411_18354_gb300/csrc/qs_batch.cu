@@ -599,6 +599,25 @@ qs_status qs_batch_info(const qs_batch *b, int *grid, int *small_bits, int *tile
     return QS_OK;
 }
 
+qs_status qs_batch_bytes(const qs_batch *b, double *algorithmic_bytes) {
+    if (!b || b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_bytes: batch is NULL or not valid");
+    if (!algorithmic_bytes) return set_error(QS_EINVAL, "qs_batch_bytes: output is NULL");
+    // states in shared memory move nothing through HBM; a larger state: |0...0> written, every
+    // forward pass reads and writes the tiles its gates select, lambda = O psi reads psi and
+    // writes lambda, every sweep pass reads and writes the selected tiles of psi and lambda
+    double total = 0.0;
+    const double es = (double)elem_bytes(b->dtype);
+    for (const BatchJitProg &jp : b->jprogs) {
+        const double state = std::ldexp(es, jp.n);
+        double per = 3.0 * state;
+        for (size_t i = 0; i < jp.pf.passes.size(); ++i) per += 2.0 * state * pass_touched_fraction(jp.pf, (int)i);
+        for (size_t i = 0; i < jp.pa.passes.size(); ++i) per += 4.0 * state * pass_touched_fraction(jp.pa, (int)i);
+        total += per * (double)jp.states.size();
+    }
+    *algorithmic_bytes = total;
+    return QS_OK;
+}
+
 qs_status qs_batch_free(qs_batch *b) {
     if (!b) return QS_OK;
     if (b->magic != kBatchMagic) return set_error(QS_EINVAL, "qs_batch_free: batch is not valid");
