@@ -528,3 +528,18 @@ def test_q30_circuit_tracks_float64_within_rounding():
     deq = (q[:, 0].astype(np.float64) + 1j * q[:, 1].astype(np.float64)) / (1 << 30)
     assert np.max(np.abs(deq - ref)) <= 1000 * 2.0 ** -31
     assert np.max(np.abs(oracle.expect_z_q30(q, n) - oracle.expect_z(deq.astype(np.complex128), n))) <= 1e-12
+
+
+def test_q30_gate_output_matches_whole_vector_update():
+    """The one-amplitude Q1.30 update (used by sampled checks at full size) equals the whole
+    vector update element by element, for targets and controls of both polarities."""
+    rng = np.random.default_rng(33)
+    n = 7
+    for t, mask, vals in ((0, 0, 0), (6, 0b11, 0b01), (3, 0b1000001, 0b1000000), (2, 0b10, 0)):
+        psi = rng.integers(-(1 << 30), 1 << 30, size=(1 << n, 2)).astype(np.int32)
+        U = W.haar_2x2(rng)
+        ref = psi.copy()
+        oracle.apply_gate_q30(ref, n, t, mask, vals, U)
+        for k in range(1 << n):
+            got = oracle.gate_output_q30(k, t, mask, vals, U, psi[k], psi[k ^ (1 << t)])
+            assert got == (int(ref[k, 0]), int(ref[k, 1])), (t, mask, k)
