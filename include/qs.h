@@ -171,7 +171,10 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
  * All gates are validated before anything is launched. flags: QS_FLAG_FUSE runs runs of
  * consecutive gates whose targets fit in one shared-memory tile in one HBM round trip (a tile
  * pass; controls outside the tile select the tiles a gate changes) and runs of diagonal
- * gates in one pass each, as qs_circuit_schedule plans them; QS_FLAG_GRAPH records the
+ * gates in one pass each, as qs_circuit_schedule plans them. Such a plan may apply gates that
+ * commute in another order than the given one (qs_circuit_order returns it): two gates keep
+ * their order unless every qubit they share is, in both, a control or a qubit of a diagonal
+ * gate. QS_FLAG_GRAPH records the
  * launches into a CUDA graph and launches it. Each state keeps up to 16 recorded graphs; a
  * call whose gate records, theta, flags, state buffer and tile size equal a recorded graph's
  * byte for byte replays it without validating or planning again (the hash that finds the
@@ -212,6 +215,21 @@ typedef struct {
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
                               const double *theta, size_t n_theta, int flags,
                               qs_schedule *out);
+
+/* The order in which the plan of qs_circuit_schedule (same arguments) applies the gates:
+ * order[0..count-1] receives a permutation of 0..count-1, gate indices as given, first
+ * applied first; with QS_FLAG_ADJOINT the order of the reverse sweep (first un-applied
+ * first). Host only, like qs_circuit_schedule. With QS_FLAG_FUSE the planner may apply gates
+ * that commute in another order than the given one (Section III applies them serially; any
+ * order that keeps each pair of gates that might not commute gives the same state): it
+ * fills each tile pass with every gate whose predecessors have run and whose target is
+ * local, adding the local qubit that releases the most gates, and keeps that order where its
+ * modelled cost is lower. Gates merged with their same-target neighbours stay consecutive;
+ * gates that change nothing (identity matrices) come last. Without QS_FLAG_FUSE the order is
+ * the given one (reversed for the sweep). Errors as qs_circuit_schedule; order must hold
+ * `count` entries (QS_EINVAL if NULL with count > 0). */
+qs_status qs_circuit_order(int n, qs_dtype dtype, const qs_gate *gates, size_t count,
+                           const double *theta, size_t n_theta, int flags, int32_t *order);
 
 /* Measured FMA rate of the current device in the arithmetic of `dtype` (QS_C64: float32,
  * QS_C128: float64), in flop/s (2 per FMA): one launch of independent FMA chains on every SM

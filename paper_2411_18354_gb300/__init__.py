@@ -15,7 +15,8 @@ import numpy as np
 from . import _lib
 from ._lib import (  # noqa: F401  (re-exported C-ABI names)
     QS_C64, QS_C128, QS_Q30, QS_FLAG_ADJOINT, QS_FLAG_FUSE, QS_FLAG_GRAPH, QS_FLAG_JIT, QS_FLAG_MASKED, QS_FLAG_OUT_DEVICE, QS_GATE_U,
-    QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_compile, qs_circuit_schedule,
+    QS_GATE_X, QS_GATE_RY, QS_GATE_RZ, QsError, qs_adjoint_grad, qs_apply_circuit, qs_apply_gate, qs_circuit_compile, qs_circuit_order,
+    qs_circuit_schedule,
     qs_apply_gate_masked, qs_apply_x, qs_build_info, qs_expect_z, qs_expect_z_noalloc, qs_last_error,
     qs_measure_fma_peak, qs_debug_build, qs_debug_configure, qs_debug_status,
     qs_state_alloc, qs_batch_bytes, qs_batch_create, qs_batch_free, qs_batch_info, qs_batch_run, qs_get_l2_fetch_bytes, qs_get_tile_bits,
@@ -33,6 +34,12 @@ def circuit_schedule(n: int, gates, theta=None, flags: int = QS_FLAG_FUSE, dtype
     """Launch schedule of ``State(n, dtype).apply_circuit(gates, theta, flags)``: launches,
     single gates, tile passes, diagonal runs and the planner's modelled cost (host only)."""
     return qs_circuit_schedule(n, _DT[dtype], gates, theta, flags)
+
+
+def circuit_order(n: int, gates, theta=None, flags: int = QS_FLAG_FUSE, dtype="c64") -> np.ndarray:
+    """Gate indices in the order that schedule applies them (first applied first; with
+    QS_FLAG_ADJOINT the reverse sweep's order); host only."""
+    return qs_circuit_order(n, _DT[dtype], gates, theta, flags)
 
 
 def _current_stream() -> int:

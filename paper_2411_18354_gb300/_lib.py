@@ -55,6 +55,8 @@ _SIGNATURES = [
     ("qs_apply_circuit", ctypes.c_int, [_c_state_p, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, ctypes.c_int]),
     ("qs_circuit_schedule", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
                                            ctypes.c_int, _vp]),
+    ("qs_circuit_order", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
+                                        ctypes.c_int, _vp]),
     ("qs_circuit_compile", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t,
                                           ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int)]),
     ("qs_measure_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _dp]),
@@ -249,6 +251,18 @@ def qs_circuit_schedule(n: int, dtype: int, gates, theta=None, flags: int = 0) -
     out = QsSchedule()
     _check(lib().qs_circuit_schedule(n, dtype, gp, g.size, tp, nt, flags, _vp(ctypes.addressof(out))))
     return {name: getattr(out, name) for name, _ in QsSchedule._fields_}
+
+
+def qs_circuit_order(n: int, dtype: int, gates, theta=None, flags: int = 0):
+    """The order (gate indices, first applied first) in which the plan of qs_circuit_schedule
+    applies the gates; with QS_FLAG_ADJOINT the reverse sweep's order (host only)."""
+    import numpy as np
+
+    g, gp = _gates_arg(gates)
+    t, tp, nt = _theta_arg(theta)
+    out = np.zeros(max(1, g.size), dtype=np.int32)
+    _check(lib().qs_circuit_order(n, dtype, gp, g.size, tp, nt, flags, _vp(out.ctypes.data)))
+    return out[: g.size].copy()
 
 
 def qs_circuit_compile(n: int, dtype: int, gates, theta=None, flags: int = QS_FLAG_FUSE | QS_FLAG_JIT,

@@ -181,9 +181,10 @@ static void cmatmul2(const double *A, const double *B, double *C) {  // C = A B,
         }
 }
 
-static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans) {
+static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans, std::vector<int> *first_rec = nullptr) {
     std::vector<GatePlan> out;
     out.reserve(plans.size());
+    if (first_rec) first_rec->clear();
     size_t i = 0;
     while (i < plans.size()) {
         size_t j = i + 1;
@@ -191,6 +192,7 @@ static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans) {
                plans[j].ctrl_vals == plans[i].ctrl_vals)
             ++j;
         if (j == i + 1) {
+            if (first_rec) first_rec->push_back((int)i);
             out.push_back(plans[i]);
         } else {
             double U[8], T[8];
@@ -204,13 +206,17 @@ static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans) {
             // an exact exchange product stays an exchange (bit-exact), else the planner
             // classifies the product's structure
             if (plan_gate(s->n, s->dtype, plans[i].t, plans[i].ctrl_mask, plans[i].ctrl_vals, U, QS_GATE_U, -1, &m, e2,
-                          sizeof(e2)))
+                          sizeof(e2))) {
+                if (first_rec) first_rec->push_back((int)i);
                 out.push_back(m);
-            else
+            } else {
+                for (size_t q = i; q < j && first_rec; ++q) first_rec->push_back((int)q);
                 out.insert(out.end(), plans.begin() + i, plans.begin() + j);  // not finite: keep the run
+            }
         }
         i = j;
     }
+    if (first_rec) first_rec->push_back((int)plans.size());
     plans.swap(out);
 }
 
@@ -537,6 +543,58 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
     }
     r.launches = r.single_gates + r.tile_passes + r.diag_runs;
     *out = r;
+    return QS_OK;
+}
+
+qs_status qs_circuit_order(int n, qs_dtype dtype, const qs_gate *gates, size_t count, const double *theta,
+                           size_t n_theta, int flags, int32_t *order) {
+    if (count > 0 && !order) return set_error(QS_EINVAL, "qs_circuit_order: order is NULL");
+    qs_schedule sched;  // the same validation as the schedule
+    const qs_status st = qs_circuit_schedule(n, dtype, gates, count, theta, n_theta, flags, &sched);
+    if (st != QS_OK) return st;
+    qs_state shape;
+    shape.n = n;
+    shape.dtype = dtype;
+    std::vector<int> out;
+    out.reserve(count);
+    std::vector<char> placed(count, 0);
+    auto put = [&](int r) {
+        if (r >= 0 && (size_t)r < count && !placed[r]) {
+            placed[r] = 1;
+            out.push_back(r);
+        }
+    };
+    char err[256];
+    const bool fuse = (flags & QS_FLAG_FUSE) != 0;
+    if (flags & QS_FLAG_ADJOINT) {
+        AdjPlan ap;
+        if (fuse) {
+            if (!plan_adjoint(&shape, gates, count, theta, n_theta, flags, &ap, err, sizeof(err)))
+                return set_error(QS_EINVAL, err);
+            for (int g : ap.pa.order) put(g);  // sweep plans are one per gate record
+        }
+        for (size_t i = count; i-- > 0;) put((int)i);
+    } else {
+        if (fuse) {
+            std::vector<GatePlan> plans(count);
+            for (size_t i = 0; i < count; ++i)
+                if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
+                    return set_error(QS_EINVAL, err);
+            std::vector<int> first_rec;
+            merge_runs(&shape, plans, &first_rec);
+            std::vector<int> seq(plans.size());
+            for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
+            FusedProgram prog;
+            plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true, 0,
+                       (flags & QS_FLAG_JIT) != 0);
+            for (int pl : prog.order)
+                for (int r = first_rec[pl]; r < first_rec[pl + 1]; ++r) put(r);
+        }
+        for (size_t i = 0; i < count; ++i) {  // identities (and everything, unfused) in the given order
+            if (!placed[i]) put((int)i);
+        }
+    }
+    for (size_t i = 0; i < count; ++i) order[i] = out[i];
     return QS_OK;
 }
 

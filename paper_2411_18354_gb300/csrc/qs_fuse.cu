@@ -16,6 +16,7 @@
 // The local set is finally padded with the lowest free qubits up to k.
 #include <algorithm>
 #include <cstdio>
+#include <iterator>
 #include <cstring>
 #include <vector>
 
@@ -73,6 +74,145 @@ static LocalGate make_local_gate(const GatePlan &p, uint64_t Lmask, const int *l
     return g;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Gate order
+// ---------------------------------------------------------------------------------------------
+// A circuit may run in any order that keeps every pair of gates that might not commute in its
+// given order. Sufficient for two gates to commute: each qubit they share is, in both of them,
+// a control or a qubit of a diagonal gate. In the computational basis of the shared qubits both
+// are then block diagonal, and the blocks act on disjoint qubits. (The rule is structural: it
+// holds for every value of a rotation angle, since a rotation's kind fixes which qubits it is
+// diagonal on.) Per qubit this gives the dependencies: a gate that is not diagonal on the
+// qubit follows the last such gate and every gate that used the qubit since; any other use
+// follows the last gate that is not diagonal on it.
+struct OrderItem {
+    int t;        // target position; -1: the gate changes nothing (no dependencies)
+    uint64_t q;   // positions the gate uses (target and controls)
+    uint64_t nd;  // positions on which it is not diagonal (its target, unless it is diagonal)
+    bool param;   // counts against the parameter limit of a block
+};
+
+// List scheduling into blocks of at most K target positions (always those in `forced`),
+// max_items items and max_param parameterised items. A block takes every item that is ready
+// (all its predecessors placed) and has its target in the block, repeatedly; when none is
+// left it adds the position whose closure (the items adding it would make takeable, directly
+// or through the items they release) is largest, ties to the position whose closure holds the
+// earliest item, until the block is full or nothing more can join. Items keep their given
+// order as the priority. Returns the items in execution order.
+static std::vector<int> block_schedule(const std::vector<OrderItem> &it, int npos, int K, uint64_t forced,
+                                       int max_items, int max_param) {
+    const int N = (int)it.size();
+    std::vector<std::vector<int>> succ(N);
+    std::vector<int> indeg(N, 0), stamp(N, -1), last_nd(npos, -1);
+    std::vector<std::vector<int>> since(npos);
+    for (int i = 0; i < N; ++i) {
+        auto dep = [&](int d) {
+            if (d >= 0 && stamp[d] != i) {
+                stamp[d] = i;
+                succ[d].push_back(i);
+                ++indeg[i];
+            }
+        };
+        for (uint64_t m = it[i].q; m; m &= m - 1) {
+            const int b = __builtin_ctzll(m);
+            dep(last_nd[b]);
+            if ((it[i].nd >> b) & 1ull)
+                for (int d : since[b]) dep(d);
+        }
+        for (uint64_t m = it[i].q; m; m &= m - 1) {
+            const int b = __builtin_ctzll(m);
+            if ((it[i].nd >> b) & 1ull) {
+                last_nd[b] = i;
+                since[b].clear();
+            } else {
+                since[b].push_back(i);
+            }
+        }
+    }
+    auto fits = [&](int i, uint64_t S) { return it[i].t < 0 || ((S >> it[i].t) & 1ull); };
+    std::vector<int> ready;  // sorted ascending (priority = given order)
+    for (int i = 0; i < N; ++i)
+        if (indeg[i] == 0) ready.push_back(i);
+    std::vector<int> order, released, dec(N, 0), touched, stack;
+    order.reserve(N);
+    while (!ready.empty()) {
+        uint64_t S = forced;
+        int count = 0, np = 0;
+        while (true) {
+            // take every ready item that fits, until none is left (taking releases others)
+            bool progress = true;
+            while (progress && count < max_items) {
+                progress = false;
+                released.clear();
+                std::vector<int> keep;
+                keep.reserve(ready.size());
+                for (int i : ready) {
+                    if (count < max_items && fits(i, S) && !(it[i].param && np >= max_param)) {
+                        order.push_back(i);
+                        ++count;
+                        np += it[i].param;
+                        for (int s : succ[i])
+                            if (--indeg[s] == 0) released.push_back(s);
+                        progress = true;
+                    } else {
+                        keep.push_back(i);
+                    }
+                }
+                std::sort(released.begin(), released.end());
+                ready.clear();
+                std::merge(keep.begin(), keep.end(), released.begin(), released.end(), std::back_inserter(ready));
+            }
+            if (count >= max_items || popc(S) >= K) break;
+            uint64_t cand = 0;
+            for (int i : ready)
+                if (it[i].t >= 0 && !((S >> it[i].t) & 1ull)) cand |= 1ull << it[i].t;
+            int best = -1, best_got = 0, best_first = N;
+            for (uint64_t m = cand; m; m &= m - 1) {
+                const int b = __builtin_ctzll(m);
+                const uint64_t S2 = S | (1ull << b);
+                int got = 0, gp = np, first = N;
+                stack.clear();
+                for (int i : ready)
+                    if (fits(i, S2)) stack.push_back(i);
+                while (!stack.empty() && count + got < max_items) {
+                    const int i = stack.back();
+                    stack.pop_back();
+                    if (it[i].param && gp >= max_param) continue;
+                    ++got;
+                    gp += it[i].param;
+                    first = std::min(first, i);
+                    for (int s : succ[i]) {
+                        if (dec[s]++ == 0) touched.push_back(s);
+                        if (dec[s] == indeg[s] && fits(s, S2)) stack.push_back(s);
+                    }
+                }
+                for (int s : touched) dec[s] = 0;
+                touched.clear();
+                if (got > best_got || (got == best_got && got > 0 && first < best_first)) {
+                    best = b;
+                    best_got = got;
+                    best_first = first;
+                }
+            }
+            if (best < 0) break;
+            S |= 1ull << best;
+        }
+        if (count == 0) {  // nothing could join (limits below one item): place the first alone
+            const int i = ready.front();
+            ready.erase(ready.begin());
+            order.push_back(i);
+            released.clear();
+            for (int s : succ[i])
+                if (--indeg[s] == 0) released.push_back(s);
+            std::sort(released.begin(), released.end());
+            std::vector<int> merged;
+            std::merge(ready.begin(), ready.end(), released.begin(), released.end(), std::back_inserter(merged));
+            ready.swap(merged);
+        }
+    }
+    return order;
+}
+
 // Choose the group qubits Q (r of them, containing the targets S): the rows of a warp vary
 // the lowest local qubits outside Q, and for shared-memory accesses without bank conflicts
 // the lowest `sw` of those must land on distinct low bits after the swizzle (qubit b lands on
@@ -122,10 +262,54 @@ static uint32_t choose_group(uint32_t S, int k, int r, int sw) {
 }
 
 // Split a pass's gates into register groups and append them to the program.
-static void add_groups(const std::vector<LocalGate> &lg, const std::vector<int> &slots, const std::vector<const double *> &ds,
-                       const std::vector<int> &src, int k, int dtype, int group_bits, FusedProgram *prog, TilePass *P) {
+// Register groups a pass's gates form in this order: runs of consecutive gates with at most r
+// distinct targets.
+static int count_groups(const std::vector<LocalGate> &lg, int r) {
+    int groups = 0;
+    size_t i = 0;
+    while (i < lg.size()) {
+        uint32_t S = 0;
+        while (i < lg.size() && popc(S | (1u << lg[i].t)) <= r) S |= 1u << lg[i++].t;
+        ++groups;
+    }
+    return groups;
+}
+
+// The pass's gates in an order of fewer register groups where the gate order allows it (the
+// commutation rule of block_schedule on the local positions: non-local controls are controls
+// of every gate that has them, so they never order two gates).
+static void order_for_groups(std::vector<LocalGate> &lg, std::vector<int> &slots, std::vector<const double *> &ds,
+                             std::vector<int> &src, int k, int r) {
+    if (lg.size() < 3) return;
+    std::vector<OrderItem> items(lg.size());
+    for (size_t i = 0; i < lg.size(); ++i) {
+        const LocalGate &g = lg[i];
+        const bool diag = g.op == OP_DIAG || g.op == OP_SIDE;
+        items[i] = {g.t, (1ull << g.t) | (uint64_t)g.cm, diag ? 0ull : (1ull << g.t), false};
+    }
+    const std::vector<int> ord = block_schedule(items, k, r, 0, (int)lg.size(), (int)lg.size());
+    std::vector<LocalGate> lg2(lg.size());
+    for (size_t i = 0; i < ord.size(); ++i) lg2[i] = lg[ord[i]];
+    if (count_groups(lg2, r) >= count_groups(lg, r)) return;
+    std::vector<int> slots2(lg.size()), src2(lg.size());
+    std::vector<const double *> ds2(lg.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+        slots2[i] = slots[ord[i]];
+        src2[i] = src[ord[i]];
+        ds2[i] = ds[ord[i]];
+    }
+    lg.swap(lg2);
+    slots.swap(slots2);
+    src.swap(src2);
+    ds.swap(ds2);
+}
+
+static void add_groups(std::vector<LocalGate> lg, std::vector<int> slots, std::vector<const double *> ds,
+                       std::vector<int> src, int k, int dtype, int group_bits, FusedProgram *prog, TilePass *P) {
     const int r = std::min(group_bits, k);
     const int sw = dtype == QS_C64 ? 4 : 3;
+    order_for_groups(lg, slots, ds, src, k, r);
+    prog->order.insert(prog->order.end(), src.begin(), src.end());  // the executed order
     P->group_begin = (int)prog->groups.size();
     P->gate_begin = (int)prog->gates.size();
     bool folded = false;
@@ -302,9 +486,11 @@ static double pass_gate_cost(int dtype, const GatePlan &p, bool jit) {
 // chunk of 8 amplitudes, or once per warp): small against the launch's state read + write.
 static double diag_run_gate_cost(int dtype) { return dtype == QS_C64 ? 0.005 : 0.02; }
 
-bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
-                const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                int max_gates, bool allow_single, int group_bits, bool jit) {
+// The planner proper: gates in the order seq gives.
+static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
+                          const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
+                          int max_gates, bool allow_single, int group_bits, bool jit) {
+    prog->order.clear();
     prog->ops.clear();
     prog->passes.clear();
     prog->gates.clear();
@@ -388,9 +574,11 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     // kDiagMaxGates gates; lead >= 0: that uncontrolled gate goes first in the first launch.
     auto emit_diag = [&](size_t a, size_t b, int lead) {
         std::vector<DiagGate> run;
+        if (lead >= 0) prog->order.push_back(lead);
         for (size_t q = a; q < b; ++q) {
             const GatePlan &p = plans[seq[q]];
             if (p.units == 0) continue;
+            prog->order.push_back(seq[q]);
             DiagGate dg;
             make_diag_gate(p, &dg);
             run.push_back(dg);
@@ -426,7 +614,7 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             }
             i = e + 1;
         }
-        return true;
+        return;
     }
     // Least modelled cost of gates [j, N): best[j]. The first segment is [j, cut[j]) of kind
     // kind[j]: a single launch, a tile pass, a diagonal run, or an uncontrolled gate leading a
@@ -520,9 +708,48 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
             emit_diag(i + 1, cut[i], seq[i]);
             break;
         default:
-            if (plans[seq[i]].units != 0 || is_param(seq[i])) prog->ops.push_back({-1, seq[i]});
+            if (plans[seq[i]].units != 0 || is_param(seq[i])) {
+                prog->ops.push_back({-1, seq[i]});
+                prog->order.push_back(seq[i]);
+            }
         }
     }
+}
+
+bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
+                const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
+                int max_gates, bool allow_single, int group_bits, bool jit) {
+    plan_in_order(n, dtype, k, seq, plans, dus, gslots, prog, max_gates, allow_single, group_bits, jit);
+    // The same gates in the order block_schedule gives for passes of k local qubits (the same
+    // limits as plan_in_order's passes); kept where the modelled cost is lower.
+    const int N = (int)seq.size();
+    if (N < 3) return true;
+    const int b0 = dtype == QS_C64 ? 4 : 3;
+    const int kk = std::min(std::min(std::max(k, b0 + 1), kTileMaxBits), n);
+    const int b = std::min(kk, b0);
+    const uint64_t low = (1ull << b) - 1ull;
+    const int mg = std::max(1, std::min(max_gates, kPassMaxGates));
+    std::vector<OrderItem> items(N);
+    for (int i = 0; i < N; ++i) {
+        const int g = seq[i];
+        const GatePlan &p = plans[g];
+        const bool param = dus != nullptr && (*dus)[g] != nullptr;
+        if (p.units == 0 && !param) {
+            items[i] = {-1, 0ull, 0ull, false};
+            continue;
+        }
+        const bool diag = p.op == OP_DIAG || p.op == OP_SIDE;
+        items[i] = {p.t, (1ull << p.t) | p.ctrl_mask, diag ? 0ull : (1ull << p.t), param};
+    }
+    const std::vector<int> ord = block_schedule(items, n, kk, low, mg, dus ? kTileMaxParam : N);
+    bool same = true;
+    for (int i = 0; i < N && same; ++i) same = ord[i] == i;
+    if (same) return true;
+    std::vector<int> seq2(N);
+    for (int i = 0; i < N; ++i) seq2[i] = seq[ord[i]];
+    FusedProgram alt;
+    plan_in_order(n, dtype, k, seq2, plans, dus, gslots, &alt, max_gates, allow_single, group_bits, jit);
+    if (alt.model_cost < prog->model_cost - 1e-9) *prog = std::move(alt);
     return true;
 }
 

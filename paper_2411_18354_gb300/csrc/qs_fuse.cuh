@@ -25,6 +25,7 @@ struct FusedProgram {
     std::vector<TileGroup> groups;  // all passes' register groups
     std::vector<RegGate> gates;     // all groups' gates
     std::vector<int> gate_src;      // plan index each RegGate came from
+    std::vector<int> order;         // plan indices in the order the program applies them
     std::vector<DiagRun> druns;
     std::vector<DiagGate> dgates;   // all diagonal runs' gates
     double model_cost = 0.0;        // planner's cost estimate (units of one state read + write)
@@ -48,7 +49,8 @@ const TileGroup *table_groups(const FusedProgram &p, const void *dev_base);
 const RegGate *table_gates(const FusedProgram &p, const void *dev_base);
 const DiagGate *table_dgates(const FusedProgram &p, const void *dev_base);
 
-// Plan the gates plans[seq[0]], plans[seq[1]], ... (execution order). For the adjoint
+// Plan the gates plans[seq[0]], plans[seq[1]], ... (the circuit's order; the program may apply
+// gates that commute in another order, see `order`). For the adjoint
 // sweep, `dus[g]` is dU/dtheta of gate g (nullptr when g has no parameter) and `gslots[g]` its
 // gradient slot; pass nullptr for both in forward mode. k = local qubits per tile.
 // max_gates bounds the gates of one pass (fusion depth); with allow_single == false every gate
