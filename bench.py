@@ -58,6 +58,7 @@ def parse_args():
                     help="small profiling case: <Z_i> + norm of an n=27 state, twice")
     ap.add_argument("--tile-costs", action="store_true",
                     help="per-gate cost of fused tile passes by gate kind (n = 24, 2^12-amplitude tiles)")
+    ap.add_argument("--layers", type=int, default=2, help="ansatz layers of the --ncu-fused case")
     ap.add_argument("--ncu-scale", action="store_true",
                     help="profiling case: the 1000-gate scale circuit at n = 30 with compiled passes, twice")
     ap.add_argument("--gate-patterns", action="store_true",
@@ -889,7 +890,7 @@ def run_ncu_fused(args):
     import workloads as W
 
     qs.build()
-    n, layers = 24, 2
+    n, layers = 24, args.layers
     g = W.hea_circuit(n, layers)
     th = W.hea_params(n, layers, seed=3)
     flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if args.jit else 0)

@@ -269,12 +269,13 @@ qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t
 
 /* Tile size of the fused passes (QS_FLAG_FUSE) for one precision, forward (adjoint = 0) or
  * adjoint sweep (adjoint = 1): `bits` local qubits per shared-memory tile, or 0 for the
- * library default (complex64: 12; complex128: 11 forward, 10 adjoint). Valid: 5 up to the
+ * library default (complex64: 12, and 11 for a sweep compiled with QS_FLAG_JIT; complex128:
+ * 11 forward, 10 adjoint). Valid: 5 up to the
  * largest tile whose block fits one SM's shared memory (complex64 14 forward / 13 adjoint,
  * complex128 13 / 12); EINVAL otherwise. Process-wide; normally set from the autotuner's
  * cache. The QS_TILE_BITS environment variable overrides it (capped at that largest tile). */
 qs_status qs_set_tile_bits(qs_dtype dtype, int adjoint, int bits);
-/* The tile size the next fused call will use. */
+/* The tile size the next fused call without QS_FLAG_JIT will use. */
 int qs_get_tile_bits(qs_dtype dtype, int adjoint);
 
 /* DRAM fetch size of the L2 (the context limit cudaLimitMaxL2FetchGranularity of this

@@ -412,27 +412,6 @@ qs_status qs_batch_create(int num_states, const int *n_qubits, const qs_gate *ga
             pid = (int)progs.size();
             progs.push_back(bp);
             prog_of.emplace(key, pid);
-            if (!small) {
-                // the pass-major path's compiled sweep passes hold psi and lambda rows of
-                // kGroupBits qubits (the persistent kernel's interpreter holds kGroupBitsAdjoint)
-                FusedProgram pa4;
-                plan_fused(n, dtype, k, seq, adj, &dus, &slots, &pa4, max_pass_gates, false, kGroupBits);
-                for (size_t gi = 0; gi < pa4.gates.size(); ++gi) {
-                    RegGate &G = pa4.gates[gi];
-                    const qs_gate &src = gs[pa4.gate_src[gi]];
-                    G.pkind2 = 0;
-                    G.pidx2 = 0;
-                    if (src.kind == QS_GATE_RY || src.kind == QS_GATE_RZ) {
-                        G.pkind = src.kind;
-                        G.pidx = src.param;
-                        G.slot = src.param;
-                    } else {
-                        G.slot = -1;
-                        G.pkind = 0;
-                    }
-                }
-                pa = std::move(pa4);
-            }
             host_progs.push_back({std::move(pf), std::move(pa)});
         }
         states[s].n = n;

@@ -130,7 +130,7 @@ static double gate_algorithmic_bytes(const GatePlan &p, int dtype) {
     return p.op == OP_SIDE ? 0.5 * b : b;
 }
 
-static int tile_bits(int dtype, bool adjoint);
+static int tile_bits(int dtype, bool adjoint, bool jit = false);
 
 // The bytes a recorded graph depends on: the gate records, the parameters, the flags, the
 // state buffer and the tile size, each run preceded by its length so that different splits
@@ -250,7 +250,9 @@ static int max_tile_bits(int dtype, bool adjoint) {
 // Local qubits per tile of a fused pass (shared memory per CTA: 2^k amplitudes, twice that
 // for the adjoint's psi and lambda tiles): QS_TILE_BITS if set (at most the largest tile that
 // fits), else the tuned value, else the default.
-static int tile_bits(int dtype, bool adjoint) {
+// jit: the sweep's passes will be compiled for their shape; their default tile is smaller
+// (2^11 amplitudes of psi and lambda: two tile buffers and two blocks fit one SM).
+static int tile_bits(int dtype, bool adjoint, bool jit) {
     const char *env = std::getenv("QS_TILE_BITS");
     if (env && *env) {
         const int v = std::atoi(env);
@@ -258,7 +260,8 @@ static int tile_bits(int dtype, bool adjoint) {
     }
     const int tuned = g_tile_bits[dtype == QS_C64 ? 0 : 1][adjoint ? 1 : 0].load();
     if (tuned > 0) return tuned;
-    return dtype == QS_C64 ? 12 : (adjoint ? 10 : 11);
+    if (dtype == QS_C64) return adjoint && jit ? 11 : 12;
+    return adjoint ? 10 : 11;
 }
 
 // Make sure `*buf` (device) holds `bytes`; grow-only. The old buffer may still be read by
@@ -398,10 +401,10 @@ static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, 
             seq[i] = (int)(count - 1 - i);
             if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
         }
-        // compiled sweep passes keep psi and lambda rows of 4 group qubits in registers (the
-        // interpreter holds 3: its dispatch leaves fewer registers free)
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true), seq, adj, &ap->dusp, &slot_of, &ap->pa, kPassMaxGates,
-                   true, jit ? kGroupBits : 0, jit);
+        // sweep passes keep psi and lambda rows of kGroupBitsAdjoint group qubits in registers
+        // (compiled passes too: with 4, their long straight-line groups spill registers)
+        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true, jit), seq, adj, &ap->dusp, &slot_of, &ap->pa, kPassMaxGates,
+                   true, 0, jit);
     }
     return true;
 }

@@ -153,9 +153,14 @@ struct Refs {
 };
 
 // The pair updates of one gate on row registers v (and, adjoint, w with the derivative dot
-// when the gate has a parameter).
-void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, bool param, const char *v, const char *w,
-                     const Refs &refs) {
+// when the gate has a parameter). A rotation U = exp(-i theta P / 2) about the Pauli P = Y or Z
+// (pauli 'Y' / 'Z') has dU/dtheta = (-i/2) P U, so with psi' = U^dagger psi (the amplitudes
+// after the un-apply) Re <lambda| dU psi'> = Re <lambda| (-i/2) P psi> = Im <lambda| P psi> / 2:
+// it is taken from the pair before the un-apply, 4 products per pair, no derivative matrix
+// (the caller halves the sum). pauli == 0: the derivative matrix is applied to a copy of the
+// un-applied pair and dotted with lambda.
+void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, bool param, char pauli, const char *v,
+                     const char *w, const Refs &refs) {
     const char *M = refs.m[gi].c_str();
     const int p = G.p;
     int dop = G.op == OP_DIAG ? OP_DIAG : (G.op == OP_REAL ? OP_REAL : OP_GEN);
@@ -173,9 +178,15 @@ void emit_gate_pairs(Out &o, const RegGate &G, int gi, int E, bool adjoint, bool
             default: break;
             }
         };
+        if (adjoint && param && pauli == 'Y')  // Im <l|Y p> = (l1 . p0) - (l0 . p1), real dot products
+            o.f("dot += (%s[%d].x * %s[%d].x + %s[%d].y * %s[%d].y) - (%s[%d].x * %s[%d].x + %s[%d].y * %s[%d].y);\n", w, e2, v,
+                e, w, e2, v, e, w, e, v, e2, w, e, v, e2);
+        else if (adjoint && param && pauli == 'Z')  // Im <l|Z p> = Im(conj(l0) p0) - Im(conj(l1) p1)
+            o.f("dot += (%s[%d].x * %s[%d].y - %s[%d].y * %s[%d].x) - (%s[%d].x * %s[%d].y - %s[%d].y * %s[%d].x);\n", w, e, v,
+                e, w, e, v, e, w, e2, v, e2, w, e2, v, e2);
         op(v);
         if (adjoint) {
-            if (param) {
+            if (param && !pauli) {
                 o.f("{ T2 mx = %s[%d], my = %s[%d]; ", v, e, v, e2);
                 o.f("%s(mx, my, %s); ", dop == OP_DIAG ? "u_diag" : (dop == OP_REAL ? "u_real" : "u_gen"),
                     refs.d[gi].c_str());
@@ -254,6 +265,13 @@ void emit_diag_run(Out &o, const RegGate *gs, int gi0, int count, int E, bool ad
         }
     }
     o.f("      }\n");
+}
+
+// The Pauli of a parameterised gate of the sweep: its rotation kind (batch), or the structure
+// the planner forces on rotations (RY: real, RZ: diagonal); 0 when neither.
+char pauli_of(const RegGate &R, bool batched) {
+    if (batched) return R.pkind == QS_GATE_RY ? 'Y' : R.pkind == QS_GATE_RZ ? 'Z' : 0;
+    return R.op == OP_REAL ? 'Y' : R.op == OP_DIAG ? 'Z' : 0;
 }
 
 }  // namespace
@@ -444,7 +462,7 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                     R.pkind2, i, i, 8 * pj[i]);
             else
                 o.f(" for (int q_ = 0; q_ < 8; ++q_) pm_[%d + q_] = u1[q_];", 8 * pj[i]);
-            if (adjoint) o.f(" for (int q_ = 0; q_ < 8; ++q_) pd_[%d + q_] = d1[q_];", 8 * pj[i]);
+            if (adjoint && !pauli_of(R, true)) o.f(" for (int q_ = 0; q_ < 8; ++q_) pd_[%d + q_] = d1[q_];", 8 * pj[i]);
             o.f(" }\n");
         }
         o.f("    }\n");
@@ -554,8 +572,10 @@ std::string jit_pass_source(int dtype, bool adjoint, const TilePass &P, const Ti
                 }
                 const bool need_rc = guard || R.crm;
                 if (need_rc) o.f("        if (%s) {\n", rc.c_str());
-                emit_gate_pairs(o, R, gi, E, adjoint, slot >= 0, "v", "w", refs);
+                const char pauli = slot >= 0 ? pauli_of(R, batched) : 0;
+                emit_gate_pairs(o, R, gi, E, adjoint, slot >= 0, pauli, "v", "w", refs);
                 if (need_rc) o.f("        }\n");
+                if (slot >= 0 && pauli) o.f("        dot *= (R)0.5;\n");
                 if (slot >= 0) {
                     o.f("        for (int of = 16; of > 0; of >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, of);\n");
                     o.f("        if (lane == 0) { R *s_ = acc_s + %d * %d + warp, *c_ = acc_c + %d * %d + warp; "
