@@ -336,15 +336,29 @@ def measure_adjoint(qs, W, peak, reps=3):
     return out
 
 
+# Measured FMA rates (TFLOP/s, 2 flops per FMA) of this device, filled in by main before the
+# measurements that quote an arithmetic roofline.
+FMA_PEAKS = {}
+
+
 def program_roofline(qs, n, gates, theta, flags, dtype, ms, peak):
-    """Algorithmic bytes of the launches qs_apply_circuit (or, with QS_FLAG_ADJOINT,
-    qs_adjoint_grad) makes for these flags (per single gate its selected amplitudes, per tile
-    pass the tiles its gates select, per diagonal run the chunks it can change; read + write),
-    divided by the measured time: achieved GB/s and the fraction of the HBM peak."""
+    """Both rooflines of the launches qs_apply_circuit (or, with QS_FLAG_ADJOINT,
+    qs_adjoint_grad) makes for these flags. Memory: algorithmic bytes (per single gate its
+    selected amplitudes, per tile pass the tiles its gates select, per diagonal run the chunks
+    it can change; read + write) / time, against the HBM peak. Arithmetic: the circuit's
+    algorithmic flops (qs_schedule.algorithmic_flops) / time, against the measured FMA rate of
+    the state's precision (which counts an FMA as 2 flops: a multiplication or addition alone
+    costs an issue slot for 1, so 1.0 is out of reach for updates with plain multiplies)."""
     sch = qs.circuit_schedule(n, gates, theta, flags=flags & ~qs.QS_FLAG_GRAPH, dtype=dtype)
     gbs = sch["algorithmic_bytes"] / (ms * 1e-3) / 1e9
-    return {"algorithmic_GB": round(sch["algorithmic_bytes"] / 1e9, 3), "achieved_GBps": round(gbs, 1),
-            "frac_hbm": round(gbs / peak, 3), "launches": sch["launches"], "tile_passes": sch["tile_passes"]}
+    out = {"algorithmic_GB": round(sch["algorithmic_bytes"] / 1e9, 3), "achieved_GBps": round(gbs, 1),
+           "frac_hbm": round(gbs / peak, 3), "launches": sch["launches"], "tile_passes": sch["tile_passes"]}
+    fp = FMA_PEAKS.get("fp32" if dtype == "c64" else "fp64")
+    if fp:
+        tf = sch["algorithmic_flops"] / (ms * 1e-3) / 1e12
+        out.update({"algorithmic_GFLOP": round(sch["algorithmic_flops"] / 1e9, 2), "achieved_TFLOPs": round(tf, 2),
+                    "frac_fma_peak": round(tf / fp, 3)})
+    return out
 
 
 def _compile(qs, n, gates, theta, dtype, adjoint=False):
@@ -459,7 +473,8 @@ def measure_paper_circuits(qs, W, peak, reps=3):
                 if label != "masked":  # the comparator reads the pairs it skips too: no algorithmic roofline
                     rf = program_roofline(qs, n, gates, None, flags, "c64", ms, peak)
                     r[f"{label}_roofline"] = {k: rf[k] for k in ("algorithmic_GB", "achieved_GBps", "frac_hbm",
-                                                                 "launches")}
+                                                                 "launches", "achieved_TFLOPs", "frac_fma_peak")
+                                              if k in rf}
             r["masked_over_reduced"] = round(r["masked_ms"] / r["reduced_ms"], 2)
             r["paper_s"] = PAPER_TIMES_S[name]
             out[name] = r
@@ -569,13 +584,29 @@ def measure_batch(qs, W, peak):
         if best is None or msj < best[0]:
             best = (msj, jcfg, first_s, jbytes)
     msj, jcfg, first_s, jbytes = best
+    # the batch's arithmetic: per state that of its circuit's gradient (forward, energy and
+    # lambda, sweep), from the planner's schedule of one state of each size
+    first = {}
+    for i, k in enumerate(ns):
+        first.setdefault(k, i)
+    flops = sum(ns.count(k) * qs.circuit_schedule(k, circ[k], thetas[first[k]],
+                                                   qs.QS_FLAG_FUSE | qs.QS_FLAG_ADJOINT)["algorithmic_flops"]
+                for k in first)
+    def arith(t_ms):
+        if not FMA_PEAKS.get("fp32"):
+            return {}
+        tf = flops / (t_ms * 1e-3) / 1e12
+        return {"algorithmic_GFLOP": round(flops / 1e9, 1), "achieved_TFLOPs": round(tf, 2),
+                "frac_fma_peak": round(tf / FMA_PEAKS["fp32"], 3)}
+
+    out.update(arith(ms))
     out["pass_major_compiled"] = {"ms_per_run": round(msj, 2), "states_per_s": round(len(ns) / (msj * 1e-3), 1),
                                   "gradient_entries_per_s": round(sum(nparams) / (msj * 1e-3), 1), "config": jcfg,
                                   "first_run_s_with_compile": round(first_s, 2),
                                   "algorithmic_GB": round(jbytes / 1e9, 2),
                                   "achieved_GBps": round(jbytes / (msj * 1e-3) / 1e9, 1),
                                   "frac_hbm": round(jbytes / (msj * 1e-3) / 1e9 / peak, 3),
-                                  "speedup_vs_persistent": round(ms / msj, 2)}
+                                  "speedup_vs_persistent": round(ms / msj, 2), **arith(msj)}
     return out
 
 
@@ -845,6 +876,9 @@ def run_ours(args, rank, world, local_rank):
                                "frac_hbm": round(b3 / (ms3 * 1e-3) / 1e9 / peak, 3),
                                "format": "Q1.30 int32 (re, im), exact 64-bit products, one rounding per output"}
     if rank == 0:
+        if any(want(p) for p in ("adjoint", "fused", "batch", "paper", "precision")):
+            FMA_PEAKS.update(measure_fma_peaks(qs))
+            result.setdefault("fma_peaks_tflops", dict(FMA_PEAKS))
         if want("adjoint"):
             result["adjoint"] = measure_adjoint(qs, W, peak)
         if want("fused"):

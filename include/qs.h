@@ -210,6 +210,16 @@ typedef struct {
                                  selected amplitudes (2 * 2^(n-c) * s), per tile pass the
                                  tiles one of its gates selects (2 * fraction * 2^n * s),
                                  per diagonal run the chunks it can change */
+    double algorithmic_flops; /* floating-point operations of the gate updates, in the state's
+                                 precision: per selected pair 28 for a general 2x2 (16
+                                 multiplications, 12 additions), 12 for a real or a diagonal
+                                 matrix, 6 for a one-sided phase, 0 for an exchange; with
+                                 QS_FLAG_ADJOINT also the sweep's un-apply of each gate on psi
+                                 and on lambda, 8 per pair for each parameterised gate's
+                                 derivative product Im <lambda|P psi> / 2 (P = Y or Z), and 8
+                                 per amplitude for the energy and lambda = O psi. The same with
+                                 and without QS_FLAG_FUSE (the circuit's arithmetic, not a
+                                 kernel's). */
 } qs_schedule;
 
 qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_t count,

@@ -241,7 +241,8 @@ class QsSchedule(ctypes.Structure):
 
     _fields_ = [("launches", ctypes.c_int32), ("single_gates", ctypes.c_int32), ("tile_passes", ctypes.c_int32),
                 ("diag_runs", ctypes.c_int32), ("gates", ctypes.c_int32), ("pass_gates", ctypes.c_int32),
-                ("model_cost", ctypes.c_double), ("algorithmic_bytes", ctypes.c_double)]
+                ("model_cost", ctypes.c_double), ("algorithmic_bytes", ctypes.c_double),
+                ("algorithmic_flops", ctypes.c_double)]
 
 
 def qs_circuit_schedule(n: int, dtype: int, gates, theta=None, flags: int = 0) -> dict:

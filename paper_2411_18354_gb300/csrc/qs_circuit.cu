@@ -130,6 +130,14 @@ static double gate_algorithmic_bytes(const GatePlan &p, int dtype) {
     return p.op == OP_SIDE ? 0.5 * b : b;
 }
 
+// Floating-point operations of one gate's update (per selected pair: general 28, real or
+// diagonal 12, one-sided 6, exchange 0), and of a sweep's derivative product (8 per pair).
+static double gate_algorithmic_flops(const GatePlan &p) {
+    if (p.units == 0) return 0.0;
+    const double per = p.op == OP_GEN ? 28.0 : (p.op == OP_REAL || p.op == OP_DIAG) ? 12.0 : p.op == OP_SIDE ? 6.0 : 0.0;
+    return per * std::ldexp(1.0, p.n - 1 - __builtin_popcountll(p.ctrl_mask));
+}
+
 static int tile_bits(int dtype, bool adjoint, bool jit = false);
 
 // The bytes a recorded graph depends on: the gate records, the parameters, the flags, the
@@ -459,6 +467,13 @@ static qs_status adjoint_schedule(const qs_state *shape, const qs_gate *gates, s
             }
         }
     };
+    for (const GatePlan &p : ap.fwd) r.algorithmic_flops += gate_algorithmic_flops(p);
+    for (size_t i = 0; i < ap.adj.size(); ++i) {
+        const GatePlan &p = ap.adj[i];
+        r.algorithmic_flops += 2.0 * gate_algorithmic_flops(p);
+        if (ap.slot_of[i] >= 0) r.algorithmic_flops += 8.0 * std::ldexp(1.0, n - 1 - __builtin_popcountll(p.ctrl_mask));
+    }
+    r.algorithmic_flops += 8.0 * std::ldexp(1.0, n);
     if (flags & QS_FLAG_FUSE) {
         add_program(ap.pf, ap.fwd, 1.0);
         add_program(ap.pa, ap.adj, 2.0);
@@ -511,6 +526,7 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
     qs_schedule r;
     std::memset(&r, 0, sizeof(r));
     r.gates = (int32_t)plans.size();
+    for (const GatePlan &p : plans) r.algorithmic_flops += gate_algorithmic_flops(p);
     const double state_bytes = std::ldexp(dtype == QS_C64 ? 8.0 : 16.0, n);
     if (flags & QS_FLAG_FUSE) {
         std::vector<int> seq(plans.size());
