@@ -216,3 +216,37 @@ def test_jit_adjoint_many_tiles_per_block(qs, dtype, tile_bits, monkeypatch):
         tm[p] -= h
         fd = (oracle.energy(n, gates, tp) - oracle.energy(n, gates, tm)) / (2 * h)
         assert abs(g[p] - fd) <= (1e-4 if dtype == "c64" else 1e-6), p
+
+
+@pytest.mark.parametrize("jit", [False, True])
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-6), ("c64", 1e-4)])
+def test_reordered_plans_match_oracle(qs, dtype, tol, jit, monkeypatch):
+    """Plans that apply commuting gates out of the given order (tile passes of 2^7 amplitudes:
+    the ansatz's layers interleave across passes): checked to be reordered on the host, then the
+    forward state against the oracle's in-order run and the gradient (its sweep in its own
+    order) against the oracle's finite differences, interpreted and compiled passes."""
+    monkeypatch.setenv("QS_TILE_BITS", "7")
+    n, layers = 12, 6
+    gl = list(W.hea_circuit(n, layers))
+    npar = 2 * n * layers
+    for q in range(0, n - 2, 3):  # controlled phases and controlled rotations between layers
+        gl.append(W.make_gate(q + 2, np.diag([1.0, np.exp(0.7j)]), [q], [1]))
+        gl.append(W.make_gate(q + 1, None, [q + 2], [0], kind=W.KIND_RY, param=npar))
+        npar += 1
+    tail = W.hea_circuit(n, 2)
+    tail["param"] += npar
+    gates = W.gate_list(gl + list(tail))
+    th = np.random.default_rng(9).uniform(0.0, 2.0 * np.pi, size=npar + 4 * n)
+    flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if jit else 0)
+    order = qs.circuit_order(n, gates, th, flags, dtype=dtype)
+    assert (order != np.arange(len(gates))).any()
+    ref = W.basis_state(n, 0)
+    oracle.run_circuit(ref, n, gates, th)
+    with qs.State(n, dtype) as st:
+        st.apply_circuit(gates, th, flags=flags)
+        got = c128_of(st.to_numpy())
+        assert np.max(np.abs(got - ref)) <= ATOL_CIRCUIT[dtype]
+        st.set_basis(0)
+        e, g = st.adjoint_grad(gates, th, flags)
+    assert abs(e - oracle.energy(n, gates, th)) <= tol
+    assert np.max(np.abs(g - oracle.fd_grad(n, gates, th))) <= tol
