@@ -179,6 +179,11 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
  * call whose gate records, theta, flags, state buffer and tile size equal a recorded graph's
  * byte for byte replays it without validating or planning again (the hash that finds the
  * candidate is always confirmed by comparing the stored bytes).
+ * Fused plans (of this call and of qs_adjoint_grad) are kept process-wide, the last 8: a call
+ * with the same n, precision, flags, tile sizes and gate records whose gates keep their
+ * structure for the new theta (the same operation class per gate: an angle that makes a
+ * rotation the identity changes it) reuses the plan with its own matrices instead of planning
+ * again; plans with diagonal-run passes are not kept.
  * QS_FLAG_MASKED runs every gate with the baseline schedule of Section III-A instead (all
  * 2^(n-1) pair iterations, controls tested per pair, the general 2x2 update), the
  * comparator of qs_apply_gate_masked for whole circuits; QS_EINVAL with QS_FLAG_FUSE. */
@@ -346,8 +351,10 @@ qs_status qs_expect_z_noalloc(const void *psi, int n, qs_dtype dtype, void *stre
  * grad += 2 Re <lambda| dU_g/dtheta psi> for every RY/RZ gate. On return the state holds
  * psi_in recomputed by the sweep (up to rounding). A second vector (lambda) is allocated
  * on first use and kept with the state. Inner products accumulate in float64.
- * QS_FLAG_FUSE groups low-target gates into tile passes; QS_FLAG_OUT_DEVICE makes energy
- * and grad device pointers (asynchronous); otherwise host pointers (synchronous). */
+ * QS_FLAG_FUSE groups low-target gates into tile passes (and may apply commuting gates in
+ * another order, forward and in the sweep; see qs_circuit_order); QS_FLAG_OUT_DEVICE makes
+ * energy and grad device pointers (asynchronous); otherwise host pointers (synchronous).
+ * Fused plans are kept as for qs_apply_circuit. */
 qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count,
                           const double *theta, size_t n_theta, double *energy,
                           double *grad, int flags);

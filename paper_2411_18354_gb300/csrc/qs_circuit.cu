@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "qs_fuse.cuh"
@@ -349,8 +350,10 @@ struct AdjPlan {
     FusedProgram pf, pa;
 };
 
-static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
-                         int flags, AdjPlan *ap, char *err, size_t errlen) {
+// The per-gate plans of a gradient: forward (then merged), sweep (U^dagger), the parameter
+// slots and derivative matrices.
+static bool plan_adjoint_gates(const qs_state *s, const qs_gate *gates, size_t count, const double *theta,
+                               size_t n_theta, AdjPlan *ap, char *err, size_t errlen) {
     std::vector<GatePlan> &fwd = ap->fwd, &adj = ap->adj;
     fwd.assign(count, GatePlan{});
     adj.assign(count, GatePlan{});
@@ -395,27 +398,151 @@ static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, 
             dus.insert(dus.end(), D, D + 8);
         }
     }
-    const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     ap->dusp.assign(count, nullptr);
+    for (size_t i = 0; i < count; ++i)
+        if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
     merge_runs(s, fwd);  // the forward pass needs no per-gate state
-    if (fuse) {
-        std::vector<int> seq(fwd.size());
-        for (size_t i = 0; i < fwd.size(); ++i) seq[i] = (int)i;
-        const bool jit = (flags & QS_FLAG_JIT) != 0;
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, fwd, nullptr, nullptr, &ap->pf, kPassMaxGates, true,
-                   0, jit);
-        seq.resize(count);
-        for (size_t i = 0; i < count; ++i) {
-            seq[i] = (int)(count - 1 - i);
-            if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
-        }
-        // sweep passes keep psi and lambda rows of kGroupBitsAdjoint group qubits in registers
-        // (compiled passes too: with 4, their long straight-line groups spill registers)
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, true, jit), seq, adj, &ap->dusp, &slot_of, &ap->pa, kPassMaxGates,
-                   true, 0, jit);
-    }
     return true;
 }
+
+// The fused forward and sweep programs of a gradient whose per-gate plans ap holds.
+static void plan_adjoint_programs(const qs_state *s, int flags, AdjPlan *ap) {
+    const size_t count = ap->adj.size();
+    std::vector<int> seq(ap->fwd.size());
+    for (size_t i = 0; i < ap->fwd.size(); ++i) seq[i] = (int)i;
+    const bool jit = (flags & QS_FLAG_JIT) != 0;
+    plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, ap->fwd, nullptr, nullptr, &ap->pf, kPassMaxGates, true,
+               0, jit);
+    seq.resize(count);
+    for (size_t i = 0; i < count; ++i) seq[i] = (int)(count - 1 - i);
+    // sweep passes keep psi and lambda rows of kGroupBitsAdjoint group qubits in registers
+    // (compiled passes too: with 4, their long straight-line groups spill registers)
+    plan_fused(s->n, s->dtype, tile_bits(s->dtype, true, jit), seq, ap->adj, &ap->dusp, &ap->slot_of, &ap->pa,
+               kPassMaxGates, true, 0, jit);
+}
+
+static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
+                         int flags, AdjPlan *ap, char *err, size_t errlen) {
+    if (!plan_adjoint_gates(s, gates, count, theta, n_theta, ap, err, errlen)) return false;
+    if (flags & QS_FLAG_FUSE) plan_adjoint_programs(s, flags, ap);
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Plan cache
+// ---------------------------------------------------------------------------------------------
+// A training loop applies or differentiates the same circuit with new angles again and again.
+// A fused program depends on the angles only through the gates' matrices, as long as every
+// gate keeps its structure (operation class, one-sided side, identity or not): the last
+// kPlanCacheEntries programs (of qs_apply_circuit: one; of qs_adjoint_grad: forward and sweep)
+// are kept process-wide, keyed by everything else they depend on (entry point, size,
+// precision, flags, tile sizes, the gate records), and a call whose per-gate structure equals
+// the cached one takes them and copies its own matrices in. Programs with diagonal-run
+// launches (whose factor classes follow the values) are not kept.
+namespace {
+
+constexpr size_t kPlanCacheEntries = 8;
+
+struct PlanCacheEntry {
+    std::vector<unsigned char> key;
+    std::vector<uint64_t> sig;
+    FusedProgram pf, pa;
+    std::vector<JitPass> jf, ja;
+    uint64_t used = 0;
+};
+
+std::mutex g_plan_mu;
+std::vector<PlanCacheEntry> g_plan_cache;
+uint64_t g_plan_clock = 0;
+
+std::vector<unsigned char> plan_cache_key(char entry, const qs_state *s, const qs_gate *gates, size_t count,
+                                          size_t n_theta, int flags) {
+    std::vector<unsigned char> k(1, (unsigned char)entry);
+    auto put = [&k](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        k.insert(k.end(), b, b + n);
+    };
+    const bool jit = (flags & QS_FLAG_JIT) != 0;
+    const int64_t hdr[7] = {s->n, (int64_t)s->dtype, flags & (QS_FLAG_FUSE | QS_FLAG_JIT), tile_bits(s->dtype, false),
+                            tile_bits(s->dtype, true, jit), (int64_t)count, (int64_t)n_theta};
+    put(hdr, sizeof(hdr));
+    if (count > 0) put(gates, count * sizeof(qs_gate));
+    return k;
+}
+
+// The structure of per-gate plans (what a program built from them depends on besides values).
+void plans_signature(const std::vector<GatePlan> &plans, std::vector<uint64_t> *sig) {
+    sig->push_back(plans.size());
+    for (const GatePlan &p : plans) {
+        sig->push_back((uint64_t)(uint32_t)p.op | ((uint64_t)(uint32_t)p.side << 8) | ((uint64_t)(p.units == 0) << 16) |
+                       ((uint64_t)(uint32_t)p.t << 24));
+        sig->push_back(p.ctrl_mask);
+        sig->push_back(p.ctrl_vals);
+    }
+}
+
+std::vector<uint64_t> adj_signature(const AdjPlan &ap) {
+    std::vector<uint64_t> sig;
+    plans_signature(ap.fwd, &sig);
+    plans_signature(ap.adj, &sig);
+    for (int x : ap.slot_of) sig.push_back((uint64_t)(int64_t)x);
+    return sig;
+}
+
+// The matrices of a program's gates from the current plans (and derivative matrices).
+void refresh_matrices(FusedProgram &prog, const std::vector<GatePlan> &plans, const std::vector<const double *> *dusp) {
+    for (size_t gi = 0; gi < prog.gates.size(); ++gi) {
+        RegGate &R = prog.gates[gi];
+        const int src = prog.gate_src[gi];
+        std::memcpy(R.U, plans[src].U, sizeof(R.U));
+        for (int q = 0; q < 8; ++q) R.Uf[q] = (float)R.U[q];
+        if (dusp && R.slot >= 0 && (*dusp)[src]) {
+            std::memcpy(R.D, (*dusp)[src], sizeof(R.D));
+            for (int q = 0; q < 8; ++q) R.Df[q] = (float)R.D[q];
+        }
+    }
+}
+
+// Copies of the kept programs for this key and structure (pa / ja may be null for an entry
+// with one program).
+bool plan_cache_take(const std::vector<unsigned char> &key, const std::vector<uint64_t> &sig, FusedProgram *pf,
+                     FusedProgram *pa, std::vector<JitPass> *jf, std::vector<JitPass> *ja) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    for (PlanCacheEntry &e : g_plan_cache) {
+        if (e.key != key || e.sig != sig) continue;
+        e.used = ++g_plan_clock;
+        *pf = e.pf;
+        *jf = e.jf;
+        if (pa) *pa = e.pa;
+        if (ja) *ja = e.ja;
+        return true;
+    }
+    return false;
+}
+
+void plan_cache_put(std::vector<unsigned char> key, std::vector<uint64_t> sig, const FusedProgram &pf,
+                    const FusedProgram *pa, const std::vector<JitPass> &jf, const std::vector<JitPass> *ja) {
+    if (!pf.druns.empty() || (pa && !pa->druns.empty())) return;
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    PlanCacheEntry *slot = nullptr;
+    if (g_plan_cache.size() < kPlanCacheEntries) {
+        g_plan_cache.emplace_back();
+        slot = &g_plan_cache.back();
+    } else {
+        slot = &g_plan_cache[0];
+        for (PlanCacheEntry &e : g_plan_cache)
+            if (e.used < slot->used) slot = &e;
+    }
+    slot->key = std::move(key);
+    slot->sig = std::move(sig);
+    slot->pf = pf;
+    slot->pa = pa ? *pa : FusedProgram{};
+    slot->jf = jf;
+    slot->ja = ja ? *ja : std::vector<JitPass>{};
+    slot->used = ++g_plan_clock;
+}
+
+}  // namespace
 
 }  // namespace qs
 
@@ -717,17 +844,27 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
     }
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     FusedProgram prog;
-    if (fuse) {
-        std::vector<int> seq(plans.size());  // after merging: fewer plans than records
-        for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
-        plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true,
-                   0, (flags & QS_FLAG_JIT) != 0);
-    }
     std::vector<JitPass> jit;
+    if (fuse) {
+        std::vector<unsigned char> pkey = plan_cache_key('F', s, gates, count, n_theta, flags);
+        std::vector<uint64_t> sig;
+        plans_signature(plans, &sig);
+        if (plan_cache_take(pkey, sig, &prog, nullptr, &jit, nullptr)) {
+            refresh_matrices(prog, plans, nullptr);
+        } else {
+            std::vector<int> seq(plans.size());  // after merging: fewer plans than records
+            for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
+            plan_fused(s->n, s->dtype, tile_bits(s->dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates,
+                       true, 0, (flags & QS_FLAG_JIT) != 0);
+            if (flags & QS_FLAG_JIT) {
+                std::string jerr;
+                if (!jit_prepare_program(s->dtype, false, prog, &jit, &jerr))
+                    return set_error(QS_ECUDA, ("qs_apply_circuit: " + jerr).c_str());
+            }
+            plan_cache_put(std::move(pkey), std::move(sig), prog, nullptr, jit, nullptr);
+        }
+    }
     if (flags & QS_FLAG_JIT) {
-        std::string jerr;
-        if (!jit_prepare_program(s->dtype, false, prog, &jit, &jerr))
-            return set_error(QS_ECUDA, ("qs_apply_circuit: " + jerr).c_str());
         cudaError_t e = jit_load(jit);  // before any stream capture below
         if (e != cudaSuccess) return cuda_fail(e, "qs_apply_circuit: loading compiled passes");
     }
@@ -823,7 +960,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     AdjPlan ap;
     {
         char err[256];
-        if (!plan_adjoint(s, gates, count, theta, n_theta, flags, &ap, err, sizeof(err)))
+        if (!plan_adjoint_gates(s, gates, count, theta, n_theta, &ap, err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     }
     std::vector<GatePlan> &fwd = ap.fwd, &adj = ap.adj;
@@ -835,10 +972,22 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     const bool fuse = (flags & QS_FLAG_FUSE) != 0;
     std::vector<JitPass> jf, ja;
     const bool use_jit = (flags & QS_FLAG_JIT) != 0;
-    if (use_jit) {
-        std::string jerr;
-        if (!jit_prepare_program(s->dtype, false, pf, &jf, &jerr) || !jit_prepare_program(s->dtype, true, pa, &ja, &jerr))
-            return set_error(QS_ECUDA, ("qs_adjoint_grad: " + jerr).c_str());
+    if (fuse) {
+        std::vector<unsigned char> key = plan_cache_key('A', s, gates, count, n_theta, flags);
+        std::vector<uint64_t> sig = adj_signature(ap);
+        if (plan_cache_take(key, sig, &pf, &pa, &jf, &ja)) {
+            refresh_matrices(pf, fwd, nullptr);
+            refresh_matrices(pa, adj, &dusp);
+        } else {
+            plan_adjoint_programs(s, flags, &ap);
+            if (use_jit) {
+                std::string jerr;
+                if (!jit_prepare_program(s->dtype, false, pf, &jf, &jerr) ||
+                    !jit_prepare_program(s->dtype, true, pa, &ja, &jerr))
+                    return set_error(QS_ECUDA, ("qs_adjoint_grad: " + jerr).c_str());
+            }
+            plan_cache_put(std::move(key), std::move(sig), pf, &pa, jf, &ja);
+        }
     }
 
     // Buffers: lambda, partials [nslots][P], slot sums, slot->param map, outputs.

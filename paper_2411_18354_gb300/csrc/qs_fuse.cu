@@ -281,6 +281,10 @@ static int count_groups(const std::vector<LocalGate> &lg, int r) {
 static void order_for_groups(std::vector<LocalGate> &lg, std::vector<int> &slots, std::vector<const double *> &ds,
                              std::vector<int> &src, int k, int r) {
     if (lg.size() < 3) return;
+    uint32_t targets = 0;
+    for (const LocalGate &g : lg) targets |= 1u << g.t;
+    const int in_order = count_groups(lg, r);
+    if (in_order <= (popc(targets) + r - 1) / r) return;  // no order needs fewer groups
     std::vector<OrderItem> items(lg.size());
     for (size_t i = 0; i < lg.size(); ++i) {
         const LocalGate &g = lg[i];
@@ -290,7 +294,7 @@ static void order_for_groups(std::vector<LocalGate> &lg, std::vector<int> &slots
     const std::vector<int> ord = block_schedule(items, k, r, 0, (int)lg.size(), (int)lg.size());
     std::vector<LocalGate> lg2(lg.size());
     for (size_t i = 0; i < ord.size(); ++i) lg2[i] = lg[ord[i]];
-    if (count_groups(lg2, r) >= count_groups(lg, r)) return;
+    if (count_groups(lg2, r) >= in_order) return;
     std::vector<int> slots2(lg.size()), src2(lg.size());
     std::vector<const double *> ds2(lg.size());
     for (size_t i = 0; i < ord.size(); ++i) {
@@ -486,19 +490,33 @@ static double pass_gate_cost(int dtype, const GatePlan &p, bool jit) {
 // chunk of 8 amplitudes, or once per warp): small against the launch's state read + write.
 static double diag_run_gate_cost(int dtype) { return dtype == QS_C64 ? 0.005 : 0.02; }
 
-// The planner proper: gates in the order seq gives.
+enum { SEG_SINGLE, SEG_PASS, SEG_DIAG, SEG_LEAD_DIAG, SEG_NONE };
+
+// A cut of the gate sequence into segments: [i, cut[i]) of kind kind[i], from i = 0 on, and
+// the modelled cost of the whole.
+struct Segments {
+    bool done = false;
+    double cost = 0.0;
+    std::vector<size_t> cut;
+    std::vector<char> kind;
+};
+
+// The planner proper, gates in the order seq gives: cuts the sequence (into `sg`, unless it is
+// already cut) and, with `prog`, emits the program.
 static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                           const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
-                          int max_gates, bool allow_single, int group_bits, bool jit) {
-    prog->order.clear();
-    prog->ops.clear();
-    prog->passes.clear();
-    prog->gates.clear();
-    prog->groups.clear();
-    prog->gate_src.clear();
-    prog->druns.clear();
-    prog->dgates.clear();
-    prog->model_cost = 0.0;
+                          int max_gates, bool allow_single, int group_bits, bool jit, Segments *sg) {
+    if (prog) {
+        prog->order.clear();
+        prog->ops.clear();
+        prog->passes.clear();
+        prog->gates.clear();
+        prog->groups.clear();
+        prog->gate_src.clear();
+        prog->druns.clear();
+        prog->dgates.clear();
+        prog->model_cost = 0.0;
+    }
     max_gates = std::max(1, std::min(max_gates, kPassMaxGates));
     // k >= b0 + 1 so that any single target fits next to the b0 low qubits (n permitting)
     const int b0 = dtype == QS_C64 ? 4 : 3;
@@ -508,6 +526,20 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
     const bool adjoint = dus != nullptr;
     const bool diag_runs = !adjoint && allow_single && n >= kDiagChunkBits;
     auto is_param = [&](int g) { return adjoint && (*dus)[g] != nullptr; };
+    const size_t N = seq.size();
+    // per position: target bit (0: changes nothing), controls, parameter, per-gate pass cost
+    std::vector<uint64_t> tbit_of(N), ctrl_of(N);
+    std::vector<char> param_of(N);
+    std::vector<double> cost_of(N);
+    for (size_t j = 0; j < N; ++j) {
+        const GatePlan &p = plans[seq[j]];
+        const bool param = is_param(seq[j]);
+        const bool real = p.units != 0 || param;
+        tbit_of[j] = real ? (1ull << p.t) : 0ull;
+        ctrl_of[j] = p.ctrl_mask;
+        param_of[j] = param;
+        cost_of[j] = real ? pass_gate_cost(dtype, p, jit) * (param && jit ? 1.5 : 1.0) : 0.0;
+    }
     // Take gates seq[i], seq[i + 1], ... (before `end`) into one pass while its targets fit in
     // k local qubits and the gate and parameter limits allow; visit(j, frac, compute, real)
     // after gate j joined: frac = fraction of tiles touched (union bound over the gates' tile
@@ -516,17 +548,16 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
         uint64_t L = low;
         double frac = 0.0, compute = 0.0;
         int nparam = 0, real = 0, count = 0;
-        for (size_t j = i0; j < end && count < max_gates; ++j) {
-            const GatePlan &p = plans[seq[j]];
-            const bool param = is_param(seq[j]);
-            if (p.units != 0 || param) {
-                const uint64_t L2 = L | (1ull << p.t);
-                if (popc(L2) > k) break;
-                if (param && nparam >= kTileMaxParam) break;
-                frac = std::min(1.0, frac + std::ldexp(1.0, -popc(p.ctrl_mask & ~L2)));
-                compute += pass_gate_cost(dtype, p, jit) * (param && jit ? 1.5 : 1.0);
+        const size_t stop = std::min(end, i0 + (size_t)max_gates);
+        for (size_t j = i0; j < stop; ++j) {
+            if (tbit_of[j]) {
+                const uint64_t L2 = L | tbit_of[j];
+                if (L2 != L && popc(L2) > k) break;
+                if (param_of[j] && nparam >= kTileMaxParam) break;
+                if (frac < 1.0) frac = std::min(1.0, frac + std::ldexp(1.0, -popc(ctrl_of[j] & ~L2)));
+                compute += cost_of[j];
                 L = L2;
-                nparam += param;
+                nparam += param_of[j];
                 ++real;
             }
             ++count;
@@ -596,7 +627,38 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
             prog->druns.push_back(r);
         }
     };
-    const size_t N = seq.size();
+    // emit the program of a cut sequence
+    auto emit_all = [&](const Segments &S) {
+        prog->model_cost = S.cost;
+        for (size_t i = 0; i < N; i = S.cut[i]) {
+            switch (S.kind[i]) {
+            case SEG_PASS:
+                emit_pass(i, S.cut[i]);
+                break;
+            case SEG_DIAG:
+                emit_diag(i, S.cut[i], -1);
+                break;
+            case SEG_LEAD_DIAG:
+                emit_diag(i + 1, S.cut[i], seq[i]);
+                break;
+            case SEG_SINGLE:
+                if (plans[seq[i]].units != 0 || is_param(seq[i])) {
+                    prog->ops.push_back({-1, seq[i]});
+                    prog->order.push_back(seq[i]);
+                }
+                break;
+            default:
+                break;
+            }
+        }
+    };
+    if (sg->done) {
+        if (prog) emit_all(*sg);
+        return;
+    }
+    sg->cut.assign(N + 1, N);
+    sg->kind.assign(N + 1, SEG_NONE);
+    sg->cost = 0.0;
     if (!allow_single) {  // every gate goes into a pass: each pass takes as many as fit
         size_t i = 0;
         while (i < N) {
@@ -608,12 +670,15 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
                 cost = frac + compute;
                 nreal = real;
             });
+            sg->cut[i] = e + 1;
             if (nreal > 0) {  // identity gates alone need no pass
-                emit_pass(i, e + 1);
-                prog->model_cost += cost;
+                sg->kind[i] = SEG_PASS;
+                sg->cost += cost;
             }
             i = e + 1;
         }
+        sg->done = true;
+        if (prog) emit_all(*sg);
         return;
     }
     // Least modelled cost of gates [j, N): best[j]. The first segment is [j, cut[j]) of kind
@@ -622,11 +687,10 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
     // kDiagMaxGates gates costs one read + write of the chunks it can change (all of them with
     // a leading gate; else those whose bits >= 3 match the controls every gate of the run
     // shares).
-    enum { SEG_SINGLE, SEG_PASS, SEG_DIAG, SEG_LEAD_DIAG };
     const double launch_cost = launch_latency_cost(n, dtype);
     std::vector<double> best(N + 1, 0.0);
-    std::vector<size_t> cut(N + 1, N);
-    std::vector<char> kind(N + 1, SEG_SINGLE);
+    std::vector<size_t> &cut = sg->cut;
+    std::vector<char> &kind = sg->kind;
     const uint64_t chunk_low = (1ull << kDiagChunkBits) - 1ull;
     // fraction of the state a diagonal run over seq[a, e] changes (no leading gate)
     auto diag_span = [&](size_t a, size_t end, bool lead, auto &&visit) {
@@ -695,35 +759,24 @@ static void plan_in_order(int n, int dtype, int k, const std::vector<int> &seq, 
         cut[j] = bc;
         kind[j] = bk;
     }
-    prog->model_cost = best[0];
-    for (size_t i = 0; i < N; i = cut[i]) {
-        switch (kind[i]) {
-        case SEG_PASS:
-            emit_pass(i, cut[i]);
-            break;
-        case SEG_DIAG:
-            emit_diag(i, cut[i], -1);
-            break;
-        case SEG_LEAD_DIAG:
-            emit_diag(i + 1, cut[i], seq[i]);
-            break;
-        default:
-            if (plans[seq[i]].units != 0 || is_param(seq[i])) {
-                prog->ops.push_back({-1, seq[i]});
-                prog->order.push_back(seq[i]);
-            }
-        }
-    }
+    sg->cost = best[0];
+    sg->done = true;
+    if (prog) emit_all(*sg);
 }
 
 bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std::vector<GatePlan> &plans,
                 const std::vector<const double *> *dus, const std::vector<int> *gslots, FusedProgram *prog,
                 int max_gates, bool allow_single, int group_bits, bool jit) {
-    plan_in_order(n, dtype, k, seq, plans, dus, gslots, prog, max_gates, allow_single, group_bits, jit);
-    // The same gates in the order block_schedule gives for passes of k local qubits (the same
-    // limits as plan_in_order's passes); kept where the modelled cost is lower.
+    // The gates in the given order and in the order block_schedule gives for passes of k local
+    // qubits (the same limits as plan_in_order's passes): both are cut, and the program of the
+    // one of lower modelled cost is emitted.
+    Segments s1;
     const int N = (int)seq.size();
-    if (N < 3) return true;
+    if (N < 3) {
+        plan_in_order(n, dtype, k, seq, plans, dus, gslots, prog, max_gates, allow_single, group_bits, jit, &s1);
+        return true;
+    }
+    plan_in_order(n, dtype, k, seq, plans, dus, gslots, nullptr, max_gates, allow_single, group_bits, jit, &s1);
     const int b0 = dtype == QS_C64 ? 4 : 3;
     const int kk = std::min(std::min(std::max(k, b0 + 1), kTileMaxBits), n);
     const int b = std::min(kk, b0);
@@ -744,12 +797,17 @@ bool plan_fused(int n, int dtype, int k, const std::vector<int> &seq, const std:
     const std::vector<int> ord = block_schedule(items, n, kk, low, mg, dus ? kTileMaxParam : N);
     bool same = true;
     for (int i = 0; i < N && same; ++i) same = ord[i] == i;
-    if (same) return true;
-    std::vector<int> seq2(N);
-    for (int i = 0; i < N; ++i) seq2[i] = seq[ord[i]];
-    FusedProgram alt;
-    plan_in_order(n, dtype, k, seq2, plans, dus, gslots, &alt, max_gates, allow_single, group_bits, jit);
-    if (alt.model_cost < prog->model_cost - 1e-9) *prog = std::move(alt);
+    if (!same) {
+        std::vector<int> seq2(N);
+        for (int i = 0; i < N; ++i) seq2[i] = seq[ord[i]];
+        Segments s2;
+        plan_in_order(n, dtype, k, seq2, plans, dus, gslots, nullptr, max_gates, allow_single, group_bits, jit, &s2);
+        if (s2.cost < s1.cost - 1e-9) {
+            plan_in_order(n, dtype, k, seq2, plans, dus, gslots, prog, max_gates, allow_single, group_bits, jit, &s2);
+            return true;
+        }
+    }
+    plan_in_order(n, dtype, k, seq, plans, dus, gslots, prog, max_gates, allow_single, group_bits, jit, &s1);
     return true;
 }
 

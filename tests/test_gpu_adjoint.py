@@ -207,3 +207,30 @@ def test_autograd_reuses_its_state_across_steps(qs):
         with torch.no_grad():
             theta -= 0.1 * theta.grad
     assert len(ag._STATES) <= before + 1
+
+
+@pytest.mark.parametrize("flags_name", ["fuse", "fuse_jit"])
+def test_plan_cache_new_angles_and_structure_changes(qs, flags_name):
+    """Repeated gradients of one circuit with new angles reuse the kept plan with the new
+    matrices: every call matches the oracle's parameter shift, also after another circuit was
+    differentiated in between and when an angle of 0 turns a rotation into the identity (its
+    structure changes, so the call plans again)."""
+    flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if flags_name == "fuse_jit" else 0)
+    n, layers = 10, 6
+    gates = W.hea_circuit(n, layers)
+    other = W.hea_circuit(n, 2)
+    rng = np.random.default_rng(21)
+    thetas = [rng.uniform(0.1, 6.2, 2 * n * layers) for _ in range(3)]
+    zero = thetas[0].copy()
+    zero[[0, 5, 17]] = 0.0  # RY(0), RZ(0), RZ(0): identities
+    with qs.State(n, "c128") as st:
+        for th in (thetas[0], thetas[1], None, thetas[2], zero, thetas[0]):
+            st.set_basis(0)
+            if th is None:
+                t2 = rng.uniform(0.1, 6.2, 2 * n * 2)
+                e, g = st.adjoint_grad(other, t2, flags)
+                assert np.max(np.abs(g - oracle.param_shift_grad(n, other, t2))) <= 1e-10
+                continue
+            e, g = st.adjoint_grad(gates, th, flags)
+            assert abs(e - oracle.energy(n, gates, th)) <= 1e-10
+            assert np.max(np.abs(g - oracle.param_shift_grad(n, gates, th))) <= 1e-10

@@ -250,3 +250,28 @@ def test_reordered_plans_match_oracle(qs, dtype, tol, jit, monkeypatch):
         e, g = st.adjoint_grad(gates, th, flags)
     assert abs(e - oracle.energy(n, gates, th)) <= tol
     assert np.max(np.abs(g - oracle.fd_grad(n, gates, th))) <= tol
+
+
+@pytest.mark.parametrize("jit", [False, True])
+def test_kept_plans_take_new_angles(qs, jit):
+    """qs_apply_circuit keeps fused plans by structure: the same circuit with new angles (plain
+    and recorded into graphs), another circuit in between and an angle of 0 (a rotation
+    becomes the identity: planned again) all match the oracle."""
+    flags = qs.QS_FLAG_FUSE | (qs.QS_FLAG_JIT if jit else 0)
+    n, layers = 14, 5
+    gates = W.hea_circuit(n, layers)
+    rng = np.random.default_rng(31)
+    thetas = [rng.uniform(0.1, 6.2, 2 * n * layers) for _ in range(3)]
+    zero = thetas[1].copy()
+    zero[[2, 9]] = 0.0
+    other = _random_gates(rng, n, 80)
+    psi0 = random_state(n, "c128", 7)
+    with qs.State(n, "c128") as st:
+        for th, extra in ((thetas[0], 0), (thetas[1], qs.QS_FLAG_GRAPH), (None, 0), (thetas[2], 0), (zero, 0),
+                          (thetas[0], qs.QS_FLAG_GRAPH)):
+            st.from_numpy(psi0)
+            g, t = (other, None) if th is None else (gates, th)
+            st.apply_circuit(g, t, flags=flags | extra)
+            ref = psi0.copy()
+            oracle.run_circuit(ref, n, g, t)
+            assert np.max(np.abs(st.to_numpy() - ref)) <= ATOL_CIRCUIT["c128"]
