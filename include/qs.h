@@ -183,7 +183,7 @@ qs_status qs_apply_gate_masked(qs_state *s, int target, uint64_t ctrl_mask,
  * with the same n, precision, flags, tile sizes and gate records whose gates keep their
  * structure for the new theta (the same operation class per gate: an angle that makes a
  * rotation the identity changes it) reuses the plan with its own matrices instead of planning
- * again; plans with diagonal-run passes are not kept.
+ * again; plans with diagonal-run passes or more than 65536 gates are not kept.
  * QS_FLAG_MASKED runs every gate with the baseline schedule of Section III-A instead (all
  * 2^(n-1) pair iterations, controls tested per pair, the general 2x2 update), the
  * comparator of qs_apply_gate_masked for whole circuits; QS_EINVAL with QS_FLAG_FUSE. */
@@ -275,7 +275,11 @@ qs_status qs_debug_status(unsigned int *status, uint64_t *first_bad);
  * text. Circuits with the same structure (e.g. the layers of a parameterised ansatz at other
  * angles) reuse the compiled kernels; the first call that needs a new shape compiles it,
  * which takes a fraction of a second to seconds. This call moves that cost out of the timed
- * or latency-critical path. *compile_seconds (may be NULL) receives the compile time of this
+ * or latency-critical path. With the environment variable QS_JIT_CACHE_DIR set to a writable
+ * directory (created if its parent exists), every compiled kernel is also kept there (one file per kernel: its full source and
+ * cubin, keyed by a hash of the source, the compile options and the NVRTC version; used only
+ * when the stored source equals the wanted one), so that later processes load instead of
+ * compiling. *compile_seconds (may be NULL) receives the compile (or load) time of this
  * call (0 when everything was cached), *passes (may be NULL) the number of tile passes.
  * QS_EINVAL for invalid gates (as qs_apply_circuit), QS_ECUDA if compilation fails. */
 qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t count,

@@ -442,6 +442,7 @@ static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, 
 namespace {
 
 constexpr size_t kPlanCacheEntries = 8;
+constexpr size_t kPlanCacheMaxGates = 65536;  // gates of a kept entry's programs
 
 struct PlanCacheEntry {
     std::vector<unsigned char> key;
@@ -523,6 +524,8 @@ bool plan_cache_take(const std::vector<unsigned char> &key, const std::vector<ui
 void plan_cache_put(std::vector<unsigned char> key, std::vector<uint64_t> sig, const FusedProgram &pf,
                     const FusedProgram *pa, const std::vector<JitPass> &jf, const std::vector<JitPass> *ja) {
     if (!pf.druns.empty() || (pa && !pa->druns.empty())) return;
+    // at most ~15 MB of gate tables per entry (larger programs are planned on every call)
+    if (pf.gates.size() + (pa ? pa->gates.size() : 0) > kPlanCacheMaxGates) return;
     std::lock_guard<std::mutex> lock(g_plan_mu);
     PlanCacheEntry *slot = nullptr;
     if (g_plan_cache.size() < kPlanCacheEntries) {

@@ -5,6 +5,7 @@
 // pair updates, Section III Eq. 2 per selected pair); only the per-gate interpretation is
 // gone. See qs_jit.cuh.
 #include <nvrtc.h>
+#include <sys/stat.h>
 
 #include <algorithm>
 #include <atomic>
@@ -13,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -749,6 +751,71 @@ bool compile_cubin(const std::string &src, std::vector<char> *cubin, std::string
     return true;
 }
 
+// ---------------------------------------------------------------------------------------------
+// On-disk kernel cache (QS_JIT_CACHE_DIR)
+// ---------------------------------------------------------------------------------------------
+// With QS_JIT_CACHE_DIR=<directory> every compiled kernel is also written there, one file per
+// kernel source, and a later process loads it instead of compiling. A file holds a header, the
+// kernel's full source and its cubin; it is used only when the stored source equals the
+// wanted one byte for byte (so neither a name collision nor a stale file can give another
+// kernel), and written under a temporary name then renamed (readers never see a partial one).
+constexpr char kDiskMagic[8] = {'Q', 'S', 'J', 'I', 'T', 'C', '1', '\n'};
+
+std::string disk_cache_dir() {
+    const char *d = std::getenv("QS_JIT_CACHE_DIR");
+    return (d && *d) ? std::string(d) : std::string();
+}
+
+// File of a kernel source: FNV-1a of the source, the compile options and the NVRTC version.
+std::string disk_path(const std::string &dir, const std::string &src) {
+    int major = 0, minor = 0;
+    nvrtcVersion(&major, &minor);
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const char *p, size_t n) {
+        for (size_t i = 0; i < n; ++i) {
+            h ^= (unsigned char)p[i];
+            h *= 1099511628211ull;
+        }
+    };
+    char v[64];
+    const int m = std::snprintf(v, sizeof(v), "sm_103a;c++17;fmad;nvrtc %d.%d;", major, minor);
+    mix(v, (size_t)m);
+    mix(src.data(), src.size());
+    char name[64];
+    std::snprintf(name, sizeof(name), "/qs_jit_%016llx.bin", (unsigned long long)h);
+    return dir + name;
+}
+
+bool disk_load(const std::string &path, const std::string &src, std::vector<char> *cubin) {
+    FILE *f = std::fopen(path.c_str(), "rb");
+    if (!f) return false;
+    std::vector<char> all;
+    char buf[1 << 16];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) all.insert(all.end(), buf, buf + got);
+    std::fclose(f);
+    const size_t hdr = sizeof(kDiskMagic) + sizeof(uint64_t);
+    if (all.size() < hdr || std::memcmp(all.data(), kDiskMagic, sizeof(kDiskMagic)) != 0) return false;
+    uint64_t len = 0;
+    std::memcpy(&len, all.data() + sizeof(kDiskMagic), sizeof(len));
+    if (len != src.size() || all.size() <= hdr + len || std::memcmp(all.data() + hdr, src.data(), len) != 0) return false;
+    cubin->assign(all.begin() + (ptrdiff_t)(hdr + len), all.end());
+    return true;
+}
+
+void disk_store(const std::string &path, const std::string &src, const std::vector<char> &cubin) {
+    const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)std::hash<std::thread::id>()(
+                                                std::this_thread::get_id()));
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return;  // not writable: the cache is an optimisation only
+    const uint64_t len = src.size();
+    bool ok = std::fwrite(kDiskMagic, 1, sizeof(kDiskMagic), f) == sizeof(kDiskMagic) &&
+              std::fwrite(&len, 1, sizeof(len), f) == sizeof(len) && std::fwrite(src.data(), 1, src.size(), f) == src.size() &&
+              std::fwrite(cubin.data(), 1, cubin.size(), f) == cubin.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
 }  // namespace
 
 bool jit_prepare_programs(int dtype, const std::vector<JitRequest> &reqs, std::string *err, double *compile_seconds,
@@ -793,6 +860,51 @@ bool jit_prepare_programs(int dtype, const std::vector<JitRequest> &reqs, std::s
         if (first_of.count(srcs[p])) continue;
         first_of[srcs[p]] = (int)p;
         missing.push_back((int)p);
+    }
+    const std::string dir = disk_cache_dir();
+    if (!missing.empty() && !dir.empty()) {
+        ::mkdir(dir.c_str(), 0755);  // if missing (one level; an error leaves the cache unused)
+        // one module per kernel: loaded from the directory where present, else compiled
+        // (concurrently) and written there
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<std::unique_ptr<Module>> mods(missing.size());
+        std::vector<size_t> todo;
+        for (size_t i = 0; i < missing.size(); ++i) {
+            mods[i] = std::make_unique<Module>();
+            mods[i]->source = srcs[missing[i]];
+            mods[i]->names.push_back("qs_pass");
+            if (!disk_load(disk_path(dir, mods[i]->source), mods[i]->source, &mods[i]->cubin)) todo.push_back(i);
+        }
+        std::vector<std::string> errs(mods.size());
+        std::vector<char> ok(mods.size(), 1);
+        unsigned hw = std::thread::hardware_concurrency();
+        if (hw == 0) hw = 4;
+        std::atomic<size_t> next{0};
+        {
+            std::vector<std::thread> th;
+            for (unsigned w = 0; w < std::min<size_t>(hw, todo.size()); ++w)
+                th.emplace_back([&] {
+                    for (size_t q; (q = next.fetch_add(1)) < todo.size();) {
+                        Module &m = *mods[todo[q]];
+                        ok[todo[q]] = compile_cubin(m.source, &m.cubin, &errs[todo[q]]) ? 1 : 0;
+                        if (ok[todo[q]]) disk_store(disk_path(dir, m.source), m.source, m.cubin);
+                    }
+                });
+            for (auto &t : th) t.join();
+        }
+        for (size_t i = 0; i < mods.size(); ++i)
+            if (!ok[i]) {
+                *err = errs[i];
+                return false;
+            }
+        for (size_t i = 0; i < mods.size(); ++i) {
+            g_by_source[srcs[missing[i]]] = {(int)g_modules.size(), 0};
+            g_modules.push_back(std::move(mods[i]));
+        }
+        if (compile_seconds)
+            *compile_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (compiled_modules) *compiled_modules = (int)todo.size();
+        missing.clear();
     }
     if (!missing.empty()) {
         auto t0 = std::chrono::steady_clock::now();

@@ -275,3 +275,31 @@ def test_kept_plans_take_new_angles(qs, jit):
             ref = psi0.copy()
             oracle.run_circuit(ref, n, g, t)
             assert np.max(np.abs(st.to_numpy() - ref)) <= ATOL_CIRCUIT["c128"]
+
+
+def test_kernels_loaded_from_disk_match_oracle(tmp_path):
+    """QS_JIT_CACHE_DIR: a process that loads the compiled passes from the directory (written by
+    an earlier process) runs them correctly: both processes' states against the oracle."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out_files = [tmp_path / "psi0.npy", tmp_path / "psi1.npy"]
+    code = ("import sys, numpy as np\n"
+            "import paper_2411_18354_gb300 as qs, workloads as W\n"
+            "n = 14\n"
+            "g = W.hea_circuit(n, 4)\n"
+            "th = W.hea_params(n, 4, seed=2)\n"
+            "with qs.State(n, 'c128') as st:\n"
+            "    st.apply_circuit(g, th, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_JIT)\n"
+            "    np.save(sys.argv[1], st.to_numpy())\n")
+    env = dict(os.environ, QS_JIT_CACHE_DIR=str(tmp_path / "kernels"), PYTHONPATH=root)
+    n = 14
+    ref = W.basis_state(n, 0)
+    oracle.run_circuit(ref, n, W.hea_circuit(n, 4), W.hea_params(n, 4, seed=2))
+    for f in out_files:
+        r = subprocess.run([sys.executable, "-c", code, str(f)], env=env, capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stderr
+        assert np.max(np.abs(np.load(f) - ref)) <= ATOL_CIRCUIT["c128"]
+    assert list((tmp_path / "kernels").glob("qs_jit_*.bin"))

@@ -273,3 +273,34 @@ def test_fused_order_fills_passes_across_layers(qs):
         assert (order != np.arange(len(g))).any()
     s = qs.circuit_schedule(n, g, th, qs.QS_FLAG_FUSE | qs.QS_FLAG_ADJOINT)
     assert s["tile_passes"] + s["single_gates"] <= 3 * layers + 4  # forward + sweep, was 5 + 5 per layer
+
+
+def test_compiled_kernels_kept_on_disk(qs, tmp_path):
+    """QS_JIT_CACHE_DIR: a second process loads the compiled pass kernels from the directory
+    instead of compiling them (host only: compilation needs no device); a file whose stored
+    source differs from the wanted kernel is not used but compiled again and rewritten."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import paper_2411_18354_gb300 as qs, workloads as W\n"
+            "g = W.hea_circuit(12, 3)\n"
+            "th = W.hea_params(12, 3, seed=1)\n"
+            "print(qs.qs_circuit_compile(12, qs.QS_C64, g, th)['compile_seconds'])\n")
+    env = dict(os.environ, QS_JIT_CACHE_DIR=str(tmp_path), PYTHONPATH=root)
+
+    def run():
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr
+        return float(out.stdout.strip().splitlines()[-1])
+
+    first = run()
+    files = sorted(tmp_path.glob("qs_jit_*.bin"))
+    assert files and first > 0.05
+    assert run() < first / 5  # loaded, not compiled
+    for f in files:  # another source under the same name: ignored
+        f.write_bytes(b"QSJITC1\n" + (5).to_bytes(8, "little") + b"other" + b"\0" * 64)
+    assert run() > first / 5  # compiled again
+    assert all(f.read_bytes().count(b"qs_pass") > 0 for f in files)  # and rewritten
+    assert run() < first / 5
