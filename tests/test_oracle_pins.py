@@ -337,6 +337,29 @@ def test_expect_z_closed_forms():
     assert abs(oracle.inner_re(psi, psi, n) - 1.0) < 1e-14
 
 
+def test_inner_re_pins():
+    """Re <a|b> = sum over amplitudes of Re(conj(a_k) b_k): basis states are orthonormal, purely
+    imaginary amplitudes count like real ones (a dropped or sign-flipped imaginary term fails),
+    a relative phase gives its cosine, and the polarisation identity
+    Re <a|b> = (|a + b|^2 - |a - b|^2) / 4 holds with the oracle's own norm2 (pinned above)."""
+    n = 5
+    for j in (0, 7, 31):
+        for k in (0, 7, 31):
+            assert oracle.inner_re(W.basis_state(n, j), W.basis_state(n, k), n) == (1.0 if j == k else 0.0)
+    a = 1j * W.basis_state(n, 9)
+    assert oracle.inner_re(a, a, n) == 1.0
+    for al, be in ((0.3, 1.1), (2.0, -0.7), (0.0, np.pi)):
+        x = np.exp(1j * al) * W.basis_state(n, 4)
+        y = np.exp(1j * be) * W.basis_state(n, 4)
+        assert abs(oracle.inner_re(x, y, n) - np.cos(be - al)) < 1e-15
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        u = rng.normal(size=2**n) + 1j * rng.normal(size=2**n)
+        v = rng.normal(size=2**n) + 1j * rng.normal(size=2**n)
+        pol = (oracle.norm2(u + v, n) - oracle.norm2(u - v, n)) / 4.0
+        assert abs(oracle.inner_re(u, v, n) - pol) < 1e-12 * (1.0 + abs(pol))
+
+
 def test_rotation_definitions():
     """RY(theta) = exp(-i theta Y/2), RZ(theta) = exp(-i theta Z/2): compare with the matrix
     exponential series of the Pauli generators."""
