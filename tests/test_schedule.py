@@ -304,3 +304,21 @@ def test_compiled_kernels_kept_on_disk(qs, tmp_path):
     assert run() > first / 5  # compiled again
     assert all(f.read_bytes().count(b"qs_pass") > 0 for f in files)  # and rewritten
     assert run() < first / 5
+
+
+def test_order_validates_arguments(qs):
+    """qs_circuit_order rejects what qs_circuit_schedule rejects, and a NULL output, before
+    planning; without QS_FLAG_FUSE the order is the given one (reversed for the sweep)."""
+    import ctypes
+
+    g = W.random_circuit(8, 10, 2, seed=1)
+    with pytest.raises(qs.QsError):
+        qs.circuit_order(8, W.gate_list([W.make_gate(9, W.H_MATRIX, ())]))
+    with pytest.raises(qs.QsError):
+        qs.circuit_order(8, g, flags=qs.QS_FLAG_FUSE | qs.QS_FLAG_MASKED)
+    with pytest.raises(qs.QsError):
+        qs.circuit_order(0, g)
+    gp = g.ctypes.data_as(ctypes.c_void_p)
+    assert qs._lib.lib().qs_circuit_order(8, qs.QS_C64, gp, g.size, None, 0, qs.QS_FLAG_FUSE, None) != 0
+    assert (qs.circuit_order(8, g, flags=0) == np.arange(g.size)).all()
+    assert (qs.circuit_order(8, g, flags=qs.QS_FLAG_ADJOINT) == np.arange(g.size)[::-1]).all()
