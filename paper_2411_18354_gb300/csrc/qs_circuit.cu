@@ -190,7 +190,26 @@ static void cmatmul2(const double *A, const double *B, double *C) {  // C = A B,
         }
 }
 
-static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans, std::vector<int> *first_rec = nullptr) {
+// Float32 instructions per selected pair of one gate's update inside a compiled complex64 pass
+// (general 16; real 4, as packed two-lane instructions; diagonal 8; one-sided 4; exchange and
+// identity 0).
+static int compiled_update_cost(const GatePlan &p) {
+    if (p.units == 0) return 0;
+    switch (p.op) {
+    case OP_GEN: return 16;
+    case OP_REAL: return 4;
+    case OP_DIAG: return 8;
+    case OP_SIDE: return 4;
+    default: return 0;
+    }
+}
+
+// flags: with QS_FLAG_FUSE | QS_FLAG_JIT on complex64 states a run is merged only where its
+// product costs a compiled pass fewer instructions than its gates apart (RY then RZ: a general
+// product, 16 per pair, against 4 + 8 apart; two diagonal or two real gates: merged).
+static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans, std::vector<int> *first_rec = nullptr,
+                       int flags = 0) {
+    const bool compiled = (flags & QS_FLAG_FUSE) && (flags & QS_FLAG_JIT) && s->dtype == QS_C64;
     std::vector<GatePlan> out;
     out.reserve(plans.size());
     if (first_rec) first_rec->clear();
@@ -214,8 +233,14 @@ static void merge_runs(const qs_state *s, std::vector<GatePlan> &plans, std::vec
             char e2[200];
             // an exact exchange product stays an exchange (bit-exact), else the planner
             // classifies the product's structure
-            if (plan_gate(s->n, s->dtype, plans[i].t, plans[i].ctrl_mask, plans[i].ctrl_vals, U, QS_GATE_U, -1, &m, e2,
-                          sizeof(e2))) {
+            bool merge = plan_gate(s->n, s->dtype, plans[i].t, plans[i].ctrl_mask, plans[i].ctrl_vals, U, QS_GATE_U, -1,
+                                   &m, e2, sizeof(e2));
+            if (merge && compiled) {
+                int apart = 0;
+                for (size_t q = i; q < j; ++q) apart += compiled_update_cost(plans[q]);
+                merge = compiled_update_cost(m) < apart;
+            }
+            if (merge) {
                 if (first_rec) first_rec->push_back((int)i);
                 out.push_back(m);
             } else {
@@ -353,7 +378,7 @@ struct AdjPlan {
 // The per-gate plans of a gradient: forward (then merged), sweep (U^dagger), the parameter
 // slots and derivative matrices.
 static bool plan_adjoint_gates(const qs_state *s, const qs_gate *gates, size_t count, const double *theta,
-                               size_t n_theta, AdjPlan *ap, char *err, size_t errlen) {
+                               size_t n_theta, int flags, AdjPlan *ap, char *err, size_t errlen) {
     std::vector<GatePlan> &fwd = ap->fwd, &adj = ap->adj;
     fwd.assign(count, GatePlan{});
     adj.assign(count, GatePlan{});
@@ -401,7 +426,7 @@ static bool plan_adjoint_gates(const qs_state *s, const qs_gate *gates, size_t c
     ap->dusp.assign(count, nullptr);
     for (size_t i = 0; i < count; ++i)
         if (slot_of[i] >= 0) ap->dusp[i] = &dus[8 * slot_of[i]];
-    merge_runs(s, fwd);  // the forward pass needs no per-gate state
+    merge_runs(s, fwd, nullptr, flags);  // the forward pass needs no per-gate state
     return true;
 }
 
@@ -423,7 +448,7 @@ static void plan_adjoint_programs(const qs_state *s, int flags, AdjPlan *ap) {
 
 static bool plan_adjoint(const qs_state *s, const qs_gate *gates, size_t count, const double *theta, size_t n_theta,
                          int flags, AdjPlan *ap, char *err, size_t errlen) {
-    if (!plan_adjoint_gates(s, gates, count, theta, n_theta, ap, err, errlen)) return false;
+    if (!plan_adjoint_gates(s, gates, count, theta, n_theta, flags, ap, err, errlen)) return false;
     if (flags & QS_FLAG_FUSE) plan_adjoint_programs(s, flags, ap);
     return true;
 }
@@ -652,7 +677,7 @@ qs_status qs_circuit_schedule(int n, qs_dtype dtype, const qs_gate *gates, size_
         if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     const bool masked = (flags & QS_FLAG_MASKED) != 0;
-    if (!masked && dtype != QS_Q30) merge_runs(&shape, plans);
+    if (!masked && dtype != QS_Q30) merge_runs(&shape, plans, nullptr, flags);
     qs_schedule r;
     std::memset(&r, 0, sizeof(r));
     r.gates = (int32_t)plans.size();
@@ -730,7 +755,7 @@ qs_status qs_circuit_order(int n, qs_dtype dtype, const qs_gate *gates, size_t c
                 if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
                     return set_error(QS_EINVAL, err);
             std::vector<int> first_rec;
-            merge_runs(&shape, plans, &first_rec);
+            merge_runs(&shape, plans, &first_rec, flags);
             std::vector<int> seq(plans.size());
             for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
             FusedProgram prog;
@@ -769,7 +794,7 @@ qs_status qs_circuit_compile(int n, qs_dtype dtype, const qs_gate *gates, size_t
         for (size_t i = 0; i < count; ++i)
             if (!plan_record(&shape, gates[i], theta, n_theta, i, &plans[i], err, sizeof(err)))
                 return set_error(QS_EINVAL, err);
-        merge_runs(&shape, plans);
+        merge_runs(&shape, plans, nullptr, fl);
         std::vector<int> seq(plans.size());
         for (size_t i = 0; i < plans.size(); ++i) seq[i] = (int)i;
         plan_fused(n, dtype, tile_bits(dtype, false), seq, plans, nullptr, nullptr, &prog, kPassMaxGates, true, 0,
@@ -834,7 +859,7 @@ qs_status qs_apply_circuit(qs_state *s, const qs_gate *gates, size_t count, cons
             return set_error(QS_EINVAL, err);
     const bool masked = (flags & QS_FLAG_MASKED) != 0;
     // (fixed point rounds every gate: a merged product would round once and differ)
-    if (!masked && s->dtype != QS_Q30) merge_runs(s, plans);
+    if (!masked && s->dtype != QS_Q30) merge_runs(s, plans, nullptr, flags);
     if (masked) {
         // baseline schedule: every pair iteration launched, the controls tested per unit,
         // the general update with the full matrix (as the Section III-A kernel does)
@@ -963,7 +988,7 @@ qs_status qs_adjoint_grad(qs_state *s, const qs_gate *gates, size_t count, const
     AdjPlan ap;
     {
         char err[256];
-        if (!plan_adjoint_gates(s, gates, count, theta, n_theta, &ap, err, sizeof(err)))
+        if (!plan_adjoint_gates(s, gates, count, theta, n_theta, flags, &ap, err, sizeof(err)))
             return set_error(QS_EINVAL, err);
     }
     std::vector<GatePlan> &fwd = ap.fwd, &adj = ap.adj;
